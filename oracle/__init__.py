@@ -1,0 +1,43 @@
+"""FP64 CPU oracle for the ppRPA hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+timed CPU-baseline leg of the benchmark may import this package; the product
+path (the CUDA library and its Python binding) never does, and this package
+imports nothing from the product.
+
+Every function cites the passage of the LibppRPA paper (arXiv 2512.12515) it
+follows.  Matrix elements are built element by element from their
+definitions and diagonalised densely, so a reader can check each step
+against the equations by eye.
+
+Parity status per function (what pins it; see tests/test_oracle_pins.py):
+
+* ao_to_mo, eri_phys, build_matrix, solve_full, solve_full_shifted,
+  correlation_energy: pinned by the spin-orbital brute force, the
+  two-electron determinant CI, the B = 0 limit, root counting, the
+  correlation-energy identity, the uniform-shift identity and the
+  second-order (MP2-type) limit.
+* grad_omega: pinned by central finite differences and by the trace rule of
+  the two-electron density matrix.
+* ri_sigma / davidson: pinned by the explicit matrix (sigma) and by full
+  diagonalisation (Davidson roots).
+* eigenvector phase: fixed by convention (largest-magnitude component
+  positive); parity unpinned beyond that convention.
+"""
+from .pprpa_ref import (  # noqa: F401
+    active_orbitals,
+    ao_to_mo,
+    pair_list,
+    eri_phys,
+    build_matrix,
+    matrix_blocks,
+    solve_full,
+    solve_full_shifted,
+    correlation_energy,
+    grad_omega,
+    two_e_density_diag,
+    nto_weights,
+    diag_of_matrix,
+)
+from .brute import spinorb_matrix, two_electron_ci, mp2_pair_energy  # noqa: F401
+from .davidson_ref import ri_sigma, ri_sigma_rows, davidson  # noqa: F401

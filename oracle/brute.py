@@ -1,0 +1,99 @@
+"""Brute-force references that do not use the spin adaptation.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+* ``spinorb_matrix``: the ppRPA matrix over spin orbitals with the
+  antisymmetrised interaction (Sec. ppRPA Equation, general A, B, C with
+  a < b, i < j).  Its spectrum is the union of the singlet roots and three
+  copies of the triplet roots.
+* ``two_electron_ci``: the Hamiltonian of two electrons in the virtual
+  orbitals, in the basis of opposite-spin determinants, from the
+  Slater-Condon rules.  With no occupied orbitals ppRPA is exact for two
+  electrons (Sec. Total Energy results, the two-electron statement).
+* ``mp2_pair_energy``: the second-order energy the ppRPA correlation energy
+  reduces to for weak interaction (ladder-CCD equivalence, Introduction).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .pprpa_ref import eri_phys
+
+
+def _spin_eri(L):
+    """Antisymmetrised <PQ||RS> over spin orbitals P = 2p + sigma."""
+    V = eri_phys(np.asarray(L, dtype=np.float64))
+    n = V.shape[0]
+    spin = np.arange(2 * n) % 2
+    sp = np.arange(2 * n) // 2
+    Vso = V[np.ix_(sp, sp, sp, sp)]
+    mask = (spin[:, None, None, None] == spin[None, None, :, None]) & (
+        spin[None, :, None, None] == spin[None, None, None, :]
+    )
+    Vso = np.where(mask, Vso, 0.0)
+    return Vso - Vso.transpose(0, 1, 3, 2)
+
+
+def spinorb_matrix(eps_act, nocc_act, L_act):
+    """Spin-orbital ppRPA matrix and its block sizes.
+
+    A_{ab,cd} = d_ac d_bd (eps_a + eps_b) + <ab||cd>, B_{ab,kl} = <ab||kl>,
+    C_{ij,kl} = -d_ik d_jl (eps_i + eps_j) + <ij||kl>, a < b, i < j over
+    spin orbitals (Sec. ppRPA Equation).  Returns ``(M, nvv, noo)``.
+    """
+    eps = np.asarray(eps_act, dtype=np.float64)
+    n = eps.shape[0]
+    anti = _spin_eri(L_act)
+    e_so = np.repeat(eps, 2)
+    occ_so = [P for P in range(2 * n) if P // 2 < nocc_act]
+    vir_so = [P for P in range(2 * n) if P // 2 >= nocc_act]
+    vv = [(vir_so[x], vir_so[y]) for x in range(len(vir_so)) for y in range(x + 1, len(vir_so))]
+    oo = [(occ_so[x], occ_so[y]) for x in range(len(occ_so)) for y in range(x + 1, len(occ_so))]
+    allp = vv + oo
+    nvv, noo = len(vv), len(oo)
+    M = np.zeros((nvv + noo, nvv + noo))
+    for I, (p, q) in enumerate(allp):
+        for J, (r, s) in enumerate(allp):
+            M[I, J] = anti[p, q, r, s]
+        if I < nvv:
+            M[I, I] += e_so[p] + e_so[q]
+        else:
+            M[I, I] -= e_so[p] + e_so[q]
+    return M, nvv, noo
+
+
+def two_electron_ci(eps_act, L_act):
+    """Two electrons in all given orbitals: eigenvalues of the determinant CI.
+
+    Basis: |p alpha, q beta> for all p, q (the M_s = 0 space, which holds
+    every singlet and one component of every triplet).  Slater-Condon rules
+    give <p q|H|r s> = d_pr d_qs (eps_p + eps_q) + <pq|rs>; the exchange
+    integral vanishes between opposite spins.  Returns sorted eigenvalues.
+    """
+    eps = np.asarray(eps_act, dtype=np.float64)
+    n = eps.shape[0]
+    V = eri_phys(np.asarray(L_act, dtype=np.float64))
+    H = V.reshape(n * n, n * n).copy()
+    H[np.arange(n * n), np.arange(n * n)] += (eps[:, None] + eps[None, :]).reshape(-1)
+    return np.sort(np.linalg.eigvalsh(0.5 * (H + H.T)))
+
+
+def mp2_pair_energy(eps_act, nocc_act, L_act):
+    """E2 = sum_{a<b, i<j} |<ab||ij>|^2 / (eps_i + eps_j - eps_a - eps_b), spin orbitals.
+
+    The second-order energy that ppRPA (ladder CCD, exact to second order;
+    Introduction) reproduces in the weak-interaction limit.
+    """
+    eps = np.asarray(eps_act, dtype=np.float64)
+    n = eps.shape[0]
+    anti = _spin_eri(L_act)
+    e_so = np.repeat(eps, 2)
+    occ = [P for P in range(2 * n) if P // 2 < nocc_act]
+    vir = [P for P in range(2 * n) if P // 2 >= nocc_act]
+    e2 = 0.0
+    for x, a in enumerate(vir):
+        for b in vir[x + 1:]:
+            for y, i in enumerate(occ):
+                for j in occ[y + 1:]:
+                    e2 += anti[a, b, i, j] ** 2 / (e_so[i] + e_so[j] - e_so[a] - e_so[b])
+    return e2

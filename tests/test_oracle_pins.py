@@ -1,0 +1,287 @@
+"""Pins of the FP64 oracle against facts it does not compute itself.
+
+Each test ties the oracle to the paper or to mathematics: a brute-force
+spin-orbital build, a determinant CI, a closed form, a limit or an identity.
+A plausible slip in the oracle (a dropped 1/sqrt(2), a wrong exchange sign,
+a transposed index, a missing diagonal term) fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small(no, nv, naux, seed, nbasis_extra=3):
+    """A small synthetic system (same generator as the workloads)."""
+    nb = no + nv + nbasis_extra
+    spec = synth.SystemSpec("t", nb, no + 1 if no else 0, naux, no, nv, seed)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], no, nv)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    return s["eps"][orb], L
+
+
+def test_generator_chunked_stream_is_identical():
+    spec = synth.SystemSpec("t", 12, 4, 10, 4, 8, 7)
+    full = synth.make_system(spec)["ao3c"]
+    parts = [blk for _, blk in synth.ao_slices(spec, 3)]
+    assert np.array_equal(np.concatenate(parts), full)
+    assert np.allclose(full, full.transpose(0, 2, 1))
+
+
+def test_ao_to_mo_matches_two_step_transform():
+    spec = synth.SystemSpec("t", 9, 3, 5, 2, 4, 3)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], 2, 4)
+    assert list(orb) == [1, 2, 3, 4, 5, 6]
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    C = s["C"][:, orb]
+    for P in range(spec.naux):
+        ref = C.T @ s["ao3c"][P] @ C
+        assert np.allclose(L[P], ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("no,nv", [(2, 3), (3, 4), (1, 4)])
+def test_spin_adapted_spectrum_equals_spin_orbital(no, nv):
+    """Singlet roots + 3 x triplet roots = spin-orbital roots (general A, B, C)."""
+    eps, L = small(no, nv, 7, 11 + no)
+    Mso, nvv_so, noo_so = oracle.spinorb_matrix(eps, no, L)
+    so = oracle.solve_full(Mso, nvv_so, noo_so)
+    parts = {}
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+        parts[mult] = oracle.solve_full(M, nvv, noo)
+        parts[mult]["Ec"] = oracle.correlation_energy(M, nvv, noo, parts[mult])[0]
+    pp = np.sort(np.concatenate([parts[1]["omega_pp"]] + [parts[3]["omega_pp"]] * 3))
+    hh = np.sort(np.concatenate([parts[1]["omega_hh"]] + [parts[3]["omega_hh"]] * 3))
+    assert np.allclose(np.sort(so["omega_pp"]), pp, atol=1e-11)
+    assert np.allclose(np.sort(so["omega_hh"]), hh, atol=1e-11)
+    ec_so = oracle.correlation_energy(Mso, nvv_so, noo_so, so)[0]
+    assert abs(ec_so - (parts[1]["Ec"] + 3 * parts[3]["Ec"])) < 1e-11
+
+
+@pytest.mark.parametrize("nv", [3, 5])
+def test_two_electrons_are_exact(nv):
+    """No occupied orbitals: ppRPA roots equal the two-electron determinant CI."""
+    eps, L = small(0, nv, 6, 40 + nv, nbasis_extra=2)
+    roots = []
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, 0, L, mult)
+        assert noo == 0
+        roots.append(oracle.solve_full(M, nvv, noo)["omega_pp"])
+    ci = oracle.two_electron_ci(eps, L)
+    assert np.allclose(np.sort(np.concatenate(roots)), ci, atol=1e-12)
+
+
+def test_two_orbital_closed_form():
+    """One occupied (i) and one virtual (a) orbital, one auxiliary function.
+
+    Singlet pairs (a,a) and (i,i): A = 2 eps_a + L_aa^2, B = L_ai^2,
+    C = -2 eps_i + L_ii^2, and det(W M - omega) = 0 gives
+    omega = ((A - C) +- sqrt((A + C)^2 - 4 B^2)) / 2 (worked by hand).
+    """
+    eps = np.array([-0.7, 0.4])
+    L = np.array([[[0.3, 0.2], [0.2, 0.5]]])
+    A = 2 * 0.4 + 0.5 ** 2
+    B = 0.2 ** 2
+    C = -2 * (-0.7) + 0.3 ** 2
+    disc = np.sqrt((A + C) ** 2 - 4 * B ** 2)
+    M, nvv, noo = oracle.build_matrix(eps, 1, L, 1)
+    assert np.allclose(M, [[A, B], [B, C]], atol=1e-15)
+    sol = oracle.solve_full(M, nvv, noo)
+    assert abs(sol["omega_pp"][0] - ((A - C) + disc) / 2) < 1e-14
+    assert abs(sol["omega_hh"][0] - ((A - C) - disc) / 2) < 1e-14
+    M3, nvv3, noo3 = oracle.build_matrix(eps, 1, L, 3)
+    assert M3.shape == (0, 0)
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_b_zero_limit(mult):
+    """With L^P_ai = 0 the coupling B vanishes: omega(N+2) = eig(A),
+    omega(N-2) = -eig(C) (because C Y = -omega Y), and E_c = 0."""
+    eps, L = small(3, 5, 8, 5)
+    L = L.copy()
+    L[:, :3, 3:] = 0.0
+    L[:, 3:, :3] = 0.0
+    M, nvv, noo = oracle.build_matrix(eps, 3, L, mult)
+    assert np.abs(M[:nvv, nvv:]).max() == 0.0
+    sol = oracle.solve_full(M, nvv, noo)
+    assert np.allclose(sol["omega_pp"], np.linalg.eigvalsh(M[:nvv, :nvv]), atol=1e-12)
+    assert np.allclose(sol["omega_hh"], np.sort(-np.linalg.eigvalsh(M[nvv:, nvv:])), atol=1e-12)
+    e1, e2 = oracle.correlation_energy(M, nvv, noo, sol)
+    assert abs(e1) < 1e-12 and abs(e2) < 1e-12
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_root_counting_normalisation_and_ec_identity(mult):
+    """nvv roots of norm +1 and noo of norm -1 (Eq. xy_norm); the two forms
+    of Eq. correlation_energy agree."""
+    eps, L = small(4, 7, 10, 21)
+    M, nvv, noo = oracle.build_matrix(eps, 4, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    assert not sol["unstable"]
+    assert len(sol["omega_pp"]) == nvv and len(sol["omega_hh"]) == noo
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    assert np.allclose(np.einsum("ik,i,ik->k", sol["z_pp"], w, sol["z_pp"]), 1.0, atol=1e-12)
+    assert np.allclose(np.einsum("ik,i,ik->k", sol["z_hh"], w, sol["z_hh"]), -1.0, atol=1e-12)
+    assert sol["omega_pp"].min() > sol["omega_hh"].max()
+    e1, e2 = oracle.correlation_energy(M, nvv, noo, sol)
+    assert abs(e1 - e2) < 1e-12
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_shifted_reduction_equals_dense_eig(mult):
+    eps, L = small(3, 6, 9, 8)
+    M, nvv, noo = oracle.build_matrix(eps, 3, L, mult)
+    a = oracle.solve_full(M, nvv, noo)
+    mu = 0.5 * (a["omega_pp"][0] + a["omega_hh"][-1])
+    b = oracle.solve_full_shifted(M, nvv, noo, mu)
+    assert np.allclose(a["omega_pp"], b["omega_pp"], atol=1e-12)
+    assert np.allclose(a["omega_hh"], b["omega_hh"], atol=1e-12)
+    # non-degenerate roots: same eigenvectors under the phase convention
+    assert np.allclose(a["z_pp"][:, :3], b["z_pp"][:, :3], atol=1e-9)
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_uniform_orbital_shift(mult):
+    """eps_p -> eps_p + delta for all p moves every root by 2 delta; E_c fixed."""
+    eps, L = small(3, 5, 6, 9)
+    d = 0.37
+    M0, nvv, noo = oracle.build_matrix(eps, 3, L, mult)
+    M1, _, _ = oracle.build_matrix(eps + d, 3, L, mult)
+    s0 = oracle.solve_full(M0, nvv, noo)
+    s1 = oracle.solve_full(M1, nvv, noo)
+    assert np.allclose(s1["omega_pp"], s0["omega_pp"] + 2 * d, atol=1e-12)
+    assert np.allclose(s1["omega_hh"], s0["omega_hh"] + 2 * d, atol=1e-12)
+    assert abs(oracle.correlation_energy(M1, nvv, noo, s1)[0]
+               - oracle.correlation_energy(M0, nvv, noo, s0)[0]) < 1e-12
+
+
+def test_second_order_limit_is_mp2():
+    """Scaling L -> lam L, E_c(lam) / E2(lam) -> 1 (ladder CCD is exact to
+    second order), with E_c = E_c(singlet) + 3 E_c(triplet)."""
+    eps, L = small(3, 5, 8, 33)
+    ratios = []
+    for lam in (0.1, 0.01):
+        ec = 0.0
+        for mult, g in ((1, 1.0), (3, 3.0)):
+            M, nvv, noo = oracle.build_matrix(eps, 3, lam * L, mult)
+            ec += g * oracle.correlation_energy(M, nvv, noo)[0]
+        e2 = oracle.mp2_pair_energy(eps, 3, lam * L)
+        ratios.append(ec / e2)
+    assert abs(ratios[0] - 1) < 2e-2
+    assert abs(ratios[1] - 1) < 2e-4
+    assert abs(ratios[1] - 1) < abs(ratios[0] - 1) / 50
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_gradient_matches_finite_differences(mult):
+    """Hellmann-Feynman d omega / d eps and d omega / d L against central FD (h = 1e-4)."""
+    no, nv = 2, 4
+    eps, L = small(no, nv, 5, 17)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    for key, r in (("pp", 0), ("pp", 2), ("hh", -1)):
+        z = sol["z_" + key][:, r]
+        de, dL = oracle.grad_omega(eps, no, L, mult, z)
+        h = 1e-4
+
+        def root(e, LL):
+            Mx, a, b = oracle.build_matrix(e, no, LL, mult)
+            sx = oracle.solve_full(Mx, a, b)
+            return sx["omega_" + key][r]
+
+        for p in (0, 3, 5):
+            ep, em = eps.copy(), eps.copy()
+            ep[p] += h
+            em[p] -= h
+            fd = (root(ep, L) - root(em, L)) / (2 * h)
+            assert abs(fd - de[p]) < 1e-5 * max(1.0, abs(de[p]))
+        rng = np.random.default_rng(3)
+        for _ in range(3):
+            D = rng.standard_normal(L.shape)
+            D = D + D.transpose(0, 2, 1)
+            D /= np.linalg.norm(D)
+            fd = (root(eps, L + h * D) - root(eps, L - h * D)) / (2 * h)
+            an = float(np.sum(dL * D))
+            assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_eps_gradient_is_density_diagonal_and_trace_rule(mult):
+    """d omega / d eps_p = s D^2e_pp and Tr D^2e = +-2 (Sec. Density Matrix),
+    so sum_p d omega / d eps_p = 2."""
+    no, nv = 3, 5
+    eps, L = small(no, nv, 6, 29)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    for key, s in (("pp", 1.0), ("hh", -1.0)):
+        z = sol["z_" + key][:, 0]
+        de, _ = oracle.grad_omega(eps, no, L, mult, z)
+        D = oracle.two_e_density_diag(z, no, nv, mult)
+        assert np.allclose(de, s * D, atol=1e-12)
+        assert abs(D.sum() - 2 * s) < 1e-12
+        assert abs(de.sum() - 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_nto_weight_sum_rule(mult):
+    no, nv = 3, 6
+    eps, L = small(no, nv, 7, 5)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    for key, s in (("pp", 1.0), ("hh", -1.0)):
+        lp, lh = oracle.nto_weights(sol["z_" + key][:, 1], no, nv, mult)
+        assert abs(lp.sum() - lh.sum() - s) < 1e-12
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("no,nv", [(1, 2), (3, 7), (5, 9)])
+def test_ri_sigma_equals_explicit_matrix(mult, no, nv):
+    eps, L = small(no, nv, 11, 3 * no + nv)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    Z = synth.random_trial_vectors(nvv + noo, 4, 99)
+    assert np.allclose(oracle.ri_sigma(eps, no, L, mult, Z), Z @ M.T, atol=1e-13)
+    rows = [0, nvv - 1, nvv + noo - 1]
+    got = oracle.ri_sigma_rows(eps, no, L, mult, Z[1], rows)
+    assert np.allclose(got, (M @ Z[1])[rows], atol=1e-13)
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_davidson_matches_full_on_small_workload(mult):
+    spec = synth.CONFIGS["c0"]
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    eps = s["eps"][orb]
+    M, nvv, noo = oracle.build_matrix(eps, spec.nocc_act, L, mult)
+    full = oracle.solve_full(M, nvv, noo)
+    res = oracle.davidson(lambda Z: oracle.ri_sigma(eps, spec.nocc_act, L, mult, Z),
+                          np.diag(M), nvv, noo, 10, tol=1e-8)
+    assert res["converged"]
+    assert np.allclose(res["omega"], full["omega_pp"][:10], atol=1e-10)
+
+
+def test_small_workload_matches_golden():
+    """Regression of the small full-diagonalisation workload against values
+    written by tests/golden/make_golden.py (oracle only)."""
+    with open(os.path.join(GOLDEN, "c0_roots.json")) as f:
+        g = json.load(f)
+    spec = synth.CONFIGS["c0"]
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    eps = s["eps"][orb]
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, spec.nocc_act, L, mult)
+        sol = oracle.solve_full(M, nvv, noo)
+        ref = g[str(mult)]
+        assert np.allclose(sol["omega_pp"], ref["omega_pp"], atol=1e-10)
+        assert np.allclose(sol["omega_hh"], ref["omega_hh"], atol=1e-10)
+        assert abs(oracle.correlation_energy(M, nvv, noo, sol)[0] - ref["ec"]) < 1e-10
