@@ -1,0 +1,192 @@
+/*
+ * pprpa.h - C ABI of the GB300 (sm_103a) particle-particle RPA hot path.
+ *
+ * The library solves the spin-adapted ppRPA eigenproblem of the LibppRPA
+ * paper (arXiv 2512.12515, Sec. "ppRPA Equation"):
+ *
+ *     [ A   B ] [X]           [ I  0 ] [X]
+ *     [ B^T C ] [Y] = omega * [ 0 -I ] [Y]
+ *
+ * with singlet or triplet matrix elements built from density-fitted
+ * integrals, <pq|rs> = (pr|qs) = sum_P L^P_pr L^P_qs.  The inputs follow the
+ * paper's input set (Sec. "Implementation Details"): occupation numbers,
+ * orbital energies, and either MO coefficients with three-center AO
+ * integrals or the MO-space fitting integrals directly.  The outputs are
+ * the two-electron addition energies omega^{N+2}, the eigenvectors X/Y
+ * (normalised X^T X - Y^T Y = +1, Eq. xy_norm), the correlation energy
+ * (Eq. correlation_energy) and Hellmann-Feynman gradients
+ * (Sec. "Analytic Gradient").
+ *
+ * Conventions (every entry point):
+ *  - Arrays are row-major, float64, C-contiguous.  A pointer argument is a
+ *    HOST pointer unless the call takes a `where` flag equal to
+ *    PPRPA_DEVICE (then it is a device pointer on the context's GPU).
+ *  - The caller owns every buffer it passes.  Inputs are copied (or
+ *    transformed) into library-owned device memory before the call returns;
+ *    outputs are written into caller buffers before the call returns.
+ *  - Every call returns 0 (PPRPA_OK) or a negative error code; no call
+ *    aborts the process or throws.  pprpa_strerror() names a code and
+ *    pprpa_last_error() gives a message for the last failure on the
+ *    calling thread.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Active orbitals are ordered occupied first, then virtual.  Pair
+ *    vectors use the row-major upper triangle: singlet pairs (p <= q),
+ *    triplet pairs (p < q); X (virtual pairs) comes first, then Y
+ *    (occupied pairs): z = [X; Y], length N = nvv + noo.
+ */
+#ifndef PPRPA_H
+#define PPRPA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define PPRPA_OK 0
+#define PPRPA_ERR_ARG (-1)      /* bad shape, null pointer, bad option, wrong call order */
+#define PPRPA_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define PPRPA_ERR_OOM (-3)      /* device allocation failed */
+#define PPRPA_ERR_NOCONV (-4)   /* Davidson hit max_iter; outputs hold the last iterate */
+#define PPRPA_ERR_UNSTABLE (-5) /* no shift makes M - mu W positive definite */
+#define PPRPA_ERR_TIMEOUT (-6)  /* a device-side bounded wait expired */
+#define PPRPA_ERR_STATE (-7)    /* required data not set yet (e.g. no integrals) */
+#define PPRPA_ERR_UNSUPPORTED (-8) /* the GPU lacks sm_103a features */
+
+/* ---- enums ------------------------------------------------------------ */
+#define PPRPA_HOST 0
+#define PPRPA_DEVICE 1
+
+#define PPRPA_SINGLET 1
+#define PPRPA_TRIPLET 3
+
+#define PPRPA_METHOD_FULL 0     /* explicit A/B/C build + dense diagonalisation */
+#define PPRPA_METHOD_DAVIDSON 1 /* density-fitted sigma + Davidson */
+
+#define PPRPA_PREC_FP64 0       /* every contraction in FP64 */
+#define PPRPA_PREC_BF16 1       /* BF16 tensor-core sigma, then BF16x3 split sigma */
+
+#define PPRPA_CHANNEL_PP 0      /* lowest two-electron addition roots */
+
+typedef struct pprpa_ctx pprpa_ctx;
+
+typedef struct pprpa_options {
+    int mult;          /* PPRPA_SINGLET or PPRPA_TRIPLET */
+    int channel;       /* PPRPA_CHANNEL_PP */
+    int method;        /* PPRPA_METHOD_FULL or PPRPA_METHOD_DAVIDSON */
+    int precision;     /* PPRPA_PREC_* (Davidson only; FULL is always FP64) */
+    int nroots;        /* number of lowest N+2 roots wanted (>= 1) */
+    double conv_tol;   /* residual 2-norm ||M z - omega W z|| for converged roots */
+    int max_iter;      /* Davidson iteration cap */
+    int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic */
+    int want_ec;       /* FULL only: also return the correlation energy */
+} pprpa_options;
+
+typedef struct pprpa_info {
+    int iters;            /* Davidson iterations (both stages) */
+    int iters_stage1;     /* iterations spent in the low-precision stage */
+    int n_sigma;          /* single-vector sigma applications */
+    int converged;        /* 1 if every root met conv_tol */
+    double max_resid;     /* largest residual norm of the returned roots */
+    double mu;            /* shift used by the last Rayleigh-Ritz step */
+    double max_imag;      /* FULL: not computed (0); reserved */
+    double t_sigma_ms;    /* device time in sigma (CUDA events) */
+    double t_total_ms;    /* device time of the whole solve */
+    double sigma_flops;   /* algorithmic sigma flops 3*naux*n*(nv^2+no^2) per vector, summed */
+} pprpa_info;
+
+/* ---- context ------------------------------------------------------------
+ * pprpa_create: make a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on, or NULL for a library-owned stream.  Returns
+ * PPRPA_ERR_UNSUPPORTED when the device is not compute capability 10.3.
+ * pprpa_destroy frees every device buffer of the context (NULL is a no-op).
+ */
+int pprpa_create(pprpa_ctx** out, int device, void* cuda_stream);
+void pprpa_destroy(pprpa_ctx* ctx);
+
+/* ---- inputs ---------------------------------------------------------------
+ * pprpa_set_orbitals: occupation numbers occ[nmo] (each 0 or 1; closed
+ * shell) and orbital energies eps[nmo] in Hartree, sorted ascending.
+ * Inputs of Sec. "Implementation Details" (a) and (b).  Host pointers.
+ */
+int pprpa_set_orbitals(pprpa_ctx* ctx, int nmo, const double* occ, const double* eps);
+
+/* pprpa_set_active: active space = the highest nocc_act occupied and the
+ * lowest nvir_act virtual orbitals (the active-space formalism of
+ * Sec. "ppRPA Equation").  Must follow set_orbitals and precede
+ * set_ao / set_mo.  Default: every orbital active.
+ */
+int pprpa_set_active(pprpa_ctx* ctx, int nocc_act, int nvir_act);
+
+/* pprpa_set_ao: three-center AO integrals ao3c[naux][nbasis][nbasis]
+ * (symmetric in the last two indices, already contracted with the fitting
+ * metric) and MO coefficients C[nbasis][nmo].  Runs the AO->MO transform
+ * L^P_pq = sum_{mu,nu} C_{mu p} (P|mu nu) C_{nu q} on the device in FP64
+ * for the active orbitals (input (c) of Sec. "Implementation Details" in
+ * its AO form; Abstract).  `where` = PPRPA_HOST or PPRPA_DEVICE for both
+ * arrays.  Host input is streamed in slices; device input is read in place.
+ */
+int pprpa_set_ao(pprpa_ctx* ctx, int nbasis, int naux, const double* C,
+                 const double* ao3c, int where);
+
+/* pprpa_set_mo: MO-space fitting integrals L[naux][nmo][nmo] (input (c) of
+ * Sec. "Implementation Details").  Only the active block is kept. */
+int pprpa_set_mo(pprpa_ctx* ctx, int naux, const double* L, int where);
+
+/* pprpa_get_L: copy the active-space L^P_pq (naux x n x n, n = nocc_act +
+ * nvir_act, occupied first) into `out` (host or device per `where`). */
+int pprpa_get_L(pprpa_ctx* ctx, double* out, int where);
+
+/* pprpa_dims: sizes of the current problem: n active orbitals, naux, and
+ * the pair counts nvv / noo for multiplicity `mult`.  Any out pointer may
+ * be NULL. */
+int pprpa_dims(pprpa_ctx* ctx, int mult, int* n, int* naux, int* nvv, int* noo);
+
+/* ---- hot-path kernels (also used by pprpa_solve) ------------------------
+ * pprpa_diag: diagonal of the ppRPA matrix M (Sec. "ppRPA Equation"):
+ *   singlet D_(pq) = w (eps_p + eps_q) + ((pp|qq) + (pq|pq)) / (1 + d_pq),
+ *   triplet D_(pq) = w (eps_p + eps_q) + (pp|qq) - (pq|pq),
+ * w = +1 on virtual pairs, -1 on occupied pairs.  out[N]. */
+int pprpa_diag(pprpa_ctx* ctx, int mult, double* out, int where);
+
+/* pprpa_sigma: sigma_k = M z_k for k vectors z[k][N] -> sigma[k][N]
+ * (the Davidson matrix-vector product of Sec. "ppRPA Equation", evaluated
+ * as sum_P L^P Zt L^P with the pair packing of Zt).  precision selects
+ * the contraction arithmetic: PPRPA_PREC_FP64, PPRPA_PREC_BF16 (BF16
+ * operands, FP32 accumulation), or PPRPA_PREC_BF16 + 16 (BF16x3 split:
+ * hi*hi + hi*lo + lo*hi).  Result is FP64.  Device or host per `where`. */
+int pprpa_sigma(pprpa_ctx* ctx, int mult, int precision, int k, const double* z,
+                double* sigma, int where);
+
+/* pprpa_build_matrix: explicit M = [[A, B], [B^T, C]] (N x N, FP64) from
+ * the fitted integrals (Sec. "ppRPA Equation", spin-adapted elements). */
+int pprpa_build_matrix(pprpa_ctx* ctx, int mult, double* M, int where);
+
+/* ---- solve -----------------------------------------------------------------
+ * pprpa_solve: lowest opts->nroots two-electron addition roots.
+ * omega[nroots] ascending; X[nroots][nvv] and Y[nroots][noo] (either may be
+ * NULL) with X^T X - Y^T Y = 1 and the largest-magnitude component positive;
+ * ec (may be NULL, FULL only): correlation energy sum(Omega^{N+2}) - Tr A
+ * of Eq. correlation_energy for this multiplicity; info may be NULL.
+ * Host output pointers.  Returns PPRPA_ERR_NOCONV (outputs filled with the
+ * last iterate) or PPRPA_ERR_UNSTABLE when no positive-definite shift
+ * exists.  The converged eigenvectors stay on the device for pprpa_grad. */
+int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double* X,
+                double* Y, double* ec, pprpa_info* info);
+
+/* pprpa_grad: Hellmann-Feynman gradient (Sec. "Analytic Gradient") of root
+ * `root` of the last pprpa_solve: d omega / d L^P_pq -> dL[naux][n][n]
+ * (entries treated as independent) and d omega / d eps_p -> deps[n]
+ * (active orbitals).  Computed in FP64 on the device.  Either output may
+ * be NULL.  Host or device per `where`. */
+int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+const char* pprpa_strerror(int code);
+const char* pprpa_last_error(void);
+/* Number of kernels this library has launched on the calling process. */
+long long pprpa_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPRPA_H */

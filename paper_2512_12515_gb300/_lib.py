@@ -1,0 +1,269 @@
+"""ctypes binding of libpprpa_gb300.so (argument marshalling only).
+
+Every entry point of include/pprpa.h has a same-named function here.  Array
+arguments are either NumPy float64 arrays (host) or torch CUDA float64
+tensors (device); the binding checks dtype/contiguity, passes raw pointers
+and converts a negative return code into :class:`PprpaError`.  No step of
+the computation runs in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpprpa_gb300.so")
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+HOST, DEVICE = 0, 1
+SINGLET, TRIPLET = 1, 3
+METHOD_FULL, METHOD_DAVIDSON = 0, 1
+PREC_FP64, PREC_BF16 = 0, 1
+PREC_BF16_SPLIT = PREC_BF16 + 16  # sigma only: BF16x3 split products
+CHANNEL_PP = 0
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("mult", ctypes.c_int),
+        ("channel", ctypes.c_int),
+        ("method", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("nroots", ctypes.c_int),
+        ("conv_tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("max_subspace", ctypes.c_int),
+        ("want_ec", ctypes.c_int),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("iters_stage1", ctypes.c_int),
+        ("n_sigma", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("max_resid", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("max_imag", ctypes.c_double),
+        ("t_sigma_ms", ctypes.c_double),
+        ("t_total_ms", ctypes.c_double),
+        ("sigma_flops", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PprpaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> (restype, argtypes); mirrors include/pprpa.h
+SIGNATURES = {
+    "pprpa_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "pprpa_destroy": (None, [_P]),
+    "pprpa_set_orbitals": (_I, [_P, _I, _P, _P]),
+    "pprpa_set_active": (_I, [_P, _I, _I]),
+    "pprpa_set_ao": (_I, [_P, _I, _I, _P, _P, _I]),
+    "pprpa_set_mo": (_I, [_P, _I, _P, _I]),
+    "pprpa_get_L": (_I, [_P, _P, _I]),
+    "pprpa_dims": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                        ctypes.POINTER(_I)]),
+    "pprpa_diag": (_I, [_P, _I, _P, _I]),
+    "pprpa_sigma": (_I, [_P, _I, _I, _I, _P, _P, _I]),
+    "pprpa_build_matrix": (_I, [_P, _I, _P, _I]),
+    "pprpa_solve": (_I, [_P, ctypes.POINTER(Options), _P, _P, _P, _P, ctypes.POINTER(Info)]),
+    "pprpa_grad": (_I, [_P, _I, _P, _P, _I]),
+    "pprpa_strerror": (ctypes.c_char_p, [_I]),
+    "pprpa_last_error": (ctypes.c_char_p, []),
+    "pprpa_kernel_launches": (ctypes.c_longlong, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        lib = load()
+        raise PprpaError(rc, f"{lib.pprpa_strerror(rc).decode()}: {lib.pprpa_last_error().decode()}")
+    return rc
+
+
+def _ptr(a, writable=False):
+    """(pointer, where) of a float64 NumPy array or torch tensor."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        if writable and not a.flags["WRITEABLE"]:
+            raise TypeError("output array is read-only")
+        return a.ctypes.data, HOST
+    # torch tensor
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def kernel_launches() -> int:
+    return int(load().pprpa_kernel_launches())
+
+
+class Context:
+    """Owns one pprpa_ctx (library-owned device memory, one CUDA stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        h = _P()
+        _check(lib.pprpa_create(ctypes.byref(h), int(device), stream))
+        self._h = h
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.pprpa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- inputs ----
+    def set_orbitals(self, occ, eps):
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        if occ.shape != eps.shape or occ.ndim != 1:
+            raise ValueError("occ and eps must be 1-D of equal length")
+        _check(self.lib.pprpa_set_orbitals(self._h, occ.shape[0], occ.ctypes.data, eps.ctypes.data))
+
+    def set_active(self, nocc_act, nvir_act):
+        _check(self.lib.pprpa_set_active(self._h, int(nocc_act), int(nvir_act)))
+
+    def set_ao(self, C, ao3c):
+        pc, wc = _ptr(C)
+        pa, wa = _ptr(ao3c)
+        if wc != wa:
+            raise ValueError("C and ao3c must both be host or both be device arrays")
+        naux, nb, nb2 = ao3c.shape
+        if nb != nb2 or C.shape[0] != nb:
+            raise ValueError("shape mismatch between C and ao3c")
+        _check(self.lib.pprpa_set_ao(self._h, nb, naux, pc, pa, wa))
+
+    def set_mo(self, L):
+        p, w = _ptr(L)
+        _check(self.lib.pprpa_set_mo(self._h, L.shape[0], p, w))
+
+    def dims(self, mult):
+        n, naux, nvv, noo = _I(), _I(), _I(), _I()
+        _check(self.lib.pprpa_dims(self._h, int(mult), ctypes.byref(n), ctypes.byref(naux),
+                                   ctypes.byref(nvv), ctypes.byref(noo)))
+        return n.value, naux.value, nvv.value, noo.value
+
+    def get_L(self, out=None):
+        n, naux, _, _ = self.dims(1)
+        if out is None:
+            out = np.empty((naux, n, n))
+        p, w = _ptr(out, True)
+        _check(self.lib.pprpa_get_L(self._h, p, w))
+        return out
+
+    # ---- kernels ----
+    def diag(self, mult, out=None):
+        _, _, nvv, noo = self.dims(mult)
+        if out is None:
+            out = np.empty(nvv + noo)
+        p, w = _ptr(out, True)
+        _check(self.lib.pprpa_diag(self._h, int(mult), p, w))
+        return out
+
+    def sigma(self, mult, z, precision=PREC_FP64, out=None):
+        pz, wz = _ptr(z)
+        k = z.shape[0] if z.ndim == 2 else 1
+        if out is None:
+            out = np.empty_like(z) if isinstance(z, np.ndarray) else z.new_empty(z.shape)
+        po, wo = _ptr(out, True)
+        if wz != wo:
+            raise ValueError("z and out must live on the same side")
+        _check(self.lib.pprpa_sigma(self._h, int(mult), int(precision), int(k), pz, po, wz))
+        return out
+
+    def build_matrix(self, mult, out=None):
+        _, _, nvv, noo = self.dims(mult)
+        N = nvv + noo
+        if out is None:
+            out = np.empty((N, N))
+        p, w = _ptr(out, True)
+        _check(self.lib.pprpa_build_matrix(self._h, int(mult), p, w))
+        return out
+
+    # ---- solve / gradient ----
+    def solve(self, mult=SINGLET, nroots=10, method=METHOD_DAVIDSON, precision=PREC_FP64,
+              conv_tol=1e-6, max_iter=200, max_subspace=0, want_ec=False, raise_noconv=True):
+        _, _, nvv, noo = self.dims(mult)
+        o = Options(mult, CHANNEL_PP, method, precision, nroots, conv_tol, max_iter, max_subspace,
+                    int(want_ec))
+        omega = np.empty(nroots)
+        X = np.empty((nroots, nvv))
+        Y = np.empty((nroots, max(noo, 1)))
+        ec = np.full(1, np.nan)
+        info = Info()
+        rc = self.lib.pprpa_solve(self._h, ctypes.byref(o), omega.ctypes.data, X.ctypes.data,
+                                  Y.ctypes.data, ec.ctypes.data if want_ec else None,
+                                  ctypes.byref(info))
+        if rc != OK and not (rc == ERR_NOCONV and not raise_noconv):
+            _check(rc)
+        return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
+                "info": info.as_dict(), "rc": rc}
+
+    def grad(self, root, dL=None, deps=None):
+        n, naux, _, _ = self.dims(1)
+        if dL is None:
+            dL = np.empty((naux, n, n))
+        if deps is None:
+            deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        p1, w1 = _ptr(dL, True)
+        p2, w2 = _ptr(deps, True)
+        if w1 != w2:
+            raise ValueError("dL and deps must live on the same side")
+        _check(self.lib.pprpa_grad(self._h, int(root), p1, p2, w1))
+        return dL, deps

@@ -1,0 +1,440 @@
+// C ABI entry points: context, inputs (with the AO->MO transform), kernels, gradient.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.h"
+
+namespace pprpa {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+void count_launch(long long n) { g_launches += n; }
+
+static int check_ctx(pprpa_ctx* c) {
+    if (!c) return set_error(PPRPA_ERR_ARG, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return set_error(PPRPA_ERR_CUDA, cudaGetErrorString(e));
+    return PPRPA_OK;
+}
+
+static int need_L(pprpa_ctx* c) {
+    if (!c->have_L) return set_error(PPRPA_ERR_STATE, "integrals not set (call pprpa_set_ao or pprpa_set_mo)");
+    return PPRPA_OK;
+}
+
+int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out) {
+    if (mult != 1 && mult != 3) return set_error(PPRPA_ERR_ARG, "mult must be 1 or 3");
+    PairTable& t = c->pairs[mult == 1 ? 0 : 1];
+    if (!t.ready) {
+        t.pp.clear();
+        t.pq.clear();
+        const int no = c->no, nv = c->nv;
+        for (int a = 0; a < nv; ++a)
+            for (int b = (mult == 1 ? a : a + 1); b < nv; ++b) {
+                t.pp.push_back(no + a);
+                t.pq.push_back(no + b);
+            }
+        t.nvv = (int)t.pp.size();
+        for (int i = 0; i < no; ++i)
+            for (int j = (mult == 1 ? i : i + 1); j < no; ++j) {
+                t.pp.push_back(i);
+                t.pq.push_back(j);
+            }
+        t.N = (int)t.pp.size();
+        t.noo = t.N - t.nvv;
+        if (t.d_pp) cudaFree(t.d_pp);
+        if (t.d_pq) cudaFree(t.d_pq);
+        t.d_pp = t.d_pq = nullptr;
+        if (t.N > 0) {
+            PP_CUDA(cudaMalloc(&t.d_pp, sizeof(int) * t.N));
+            PP_CUDA(cudaMalloc(&t.d_pq, sizeof(int) * t.N));
+            PP_CUDA(cudaMemcpyAsync(t.d_pp, t.pp.data(), sizeof(int) * t.N, cudaMemcpyHostToDevice, c->stream));
+            PP_CUDA(cudaMemcpyAsync(t.d_pq, t.pq.data(), sizeof(int) * t.N, cudaMemcpyHostToDevice, c->stream));
+            PP_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        t.ready = true;
+    }
+    *out = &t;
+    return PPRPA_OK;
+}
+
+static void reset_integrals(pprpa_ctx* c) {
+    if (c->d_L) cudaFree(c->d_L);
+    if (c->d_Lhi) cudaFree(c->d_Lhi);
+    if (c->d_Llo) cudaFree(c->d_Llo);
+    if (c->d_lastZ) cudaFree(c->d_lastZ);
+    c->d_L = nullptr;
+    c->d_Lhi = c->d_Llo = nullptr;
+    c->d_lastZ = nullptr;
+    c->bf16_ready = false;
+    c->have_L = false;
+    c->last_nroots = 0;
+    for (auto& t : c->pairs) t.ready = false;
+}
+
+static int upload_eps(pprpa_ctx* c) {
+    const int n = c->n();
+    if (c->d_eps) cudaFree(c->d_eps);
+    c->d_eps = nullptr;
+    if (n == 0) return PPRPA_OK;
+    std::vector<double> e(n);
+    const int first = c->nocc - c->no;
+    for (int p = 0; p < n; ++p) e[p] = c->eps[first + p];
+    PP_CUDA(cudaMalloc(&c->d_eps, sizeof(double) * n));
+    PP_CUDA(cudaMemcpy(c->d_eps, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa
+
+using namespace pprpa;
+
+extern "C" {
+
+const char* pprpa_strerror(int code) {
+    switch (code) {
+        case PPRPA_OK: return "ok";
+        case PPRPA_ERR_ARG: return "invalid argument";
+        case PPRPA_ERR_CUDA: return "CUDA error";
+        case PPRPA_ERR_OOM: return "out of device memory";
+        case PPRPA_ERR_NOCONV: return "Davidson did not converge";
+        case PPRPA_ERR_UNSTABLE: return "no positive-definite shift (unstable ppRPA problem)";
+        case PPRPA_ERR_TIMEOUT: return "device-side wait timed out";
+        case PPRPA_ERR_STATE: return "required input not set";
+        case PPRPA_ERR_UNSUPPORTED: return "GPU is not sm_103 (GB300)";
+        default: return "unknown error";
+    }
+}
+
+const char* pprpa_last_error(void) { return g_last_error.c_str(); }
+
+long long pprpa_kernel_launches(void) { return g_launches.load(); }
+
+int pprpa_create(pprpa_ctx** out, int device, void* cuda_stream) {
+    if (!out) return set_error(PPRPA_ERR_ARG, "null out pointer");
+    *out = nullptr;
+    int ndev = 0;
+    PP_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_error(PPRPA_ERR_ARG, "bad device index");
+    PP_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    PP_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return set_error(PPRPA_ERR_UNSUPPORTED, std::string("device is sm_") + std::to_string(prop.major) +
+                                                    std::to_string(prop.minor) + ", need sm_103");
+    pprpa_ctx* c = new pprpa_ctx();
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return set_error(PPRPA_ERR_CUDA, cudaGetErrorString(e)); }
+        c->own_stream = true;
+    }
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) {
+        pprpa_destroy(c);
+        return set_error(PPRPA_ERR_OOM, "status word");
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    *out = c;
+    return PPRPA_OK;
+}
+
+void pprpa_destroy(pprpa_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    reset_integrals(c);
+    if (c->d_eps) cudaFree(c->d_eps);
+    for (auto& t : c->pairs) {
+        if (t.d_pp) cudaFree(t.d_pp);
+        if (t.d_pq) cudaFree(t.d_pq);
+    }
+    for (auto& kv : c->ws)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int pprpa_set_orbitals(pprpa_ctx* c, int nmo, const double* occ, const double* eps) {
+    PP_TRY(check_ctx(c));
+    if (nmo <= 0 || !occ || !eps) return set_error(PPRPA_ERR_ARG, "set_orbitals: bad arguments");
+    int nocc = 0;
+    for (int i = 0; i < nmo; ++i) {
+        if (occ[i] != 0.0 && occ[i] != 1.0)
+            return set_error(PPRPA_ERR_ARG, "set_orbitals: occupations must be 0 or 1 (closed shell)");
+        if (occ[i] == 1.0) {
+            if (i != nocc) return set_error(PPRPA_ERR_ARG, "set_orbitals: occupied orbitals must come first");
+            ++nocc;
+        }
+        if (!std::isfinite(eps[i])) return set_error(PPRPA_ERR_ARG, "set_orbitals: non-finite energy");
+        if (i > 0 && eps[i] < eps[i - 1]) return set_error(PPRPA_ERR_ARG, "set_orbitals: energies must be ascending");
+    }
+    reset_integrals(c);
+    c->nmo = nmo;
+    c->nocc = nocc;
+    c->occ.assign(occ, occ + nmo);
+    c->eps.assign(eps, eps + nmo);
+    c->no = nocc;
+    c->nv = nmo - nocc;
+    return upload_eps(c);
+}
+
+int pprpa_set_active(pprpa_ctx* c, int nocc_act, int nvir_act) {
+    PP_TRY(check_ctx(c));
+    if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "set_active: call set_orbitals first");
+    if (nocc_act < 0 || nvir_act < 0 || nocc_act > c->nocc || nvir_act > c->nmo - c->nocc)
+        return set_error(PPRPA_ERR_ARG, "set_active: active space larger than the orbital space");
+    if (nocc_act + nvir_act == 0) return set_error(PPRPA_ERR_ARG, "set_active: empty active space");
+    if (c->have_L) return set_error(PPRPA_ERR_STATE, "set_active must precede set_ao / set_mo");
+    c->no = nocc_act;
+    c->nv = nvir_act;
+    for (auto& t : c->pairs) t.ready = false;
+    return upload_eps(c);
+}
+
+int pprpa_set_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const double* ao3c, int where) {
+    PP_TRY(check_ctx(c));
+    if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "set_ao: call set_orbitals first");
+    if (nbasis <= 0 || naux <= 0 || !C || !ao3c || (where != PPRPA_HOST && where != PPRPA_DEVICE))
+        return set_error(PPRPA_ERR_ARG, "set_ao: bad arguments");
+    if (c->have_L) reset_integrals(c);
+    const int n = c->n(), nmo = c->nmo;
+    cudaStream_t st = c->stream;
+    const int first = c->nocc - c->no;
+    // active columns of C (nbasis x n) on the device
+    double* d_Cact;
+    PP_TRY(ws_get(c, "ao_Cact", sizeof(double) * nbasis * n, (void**)&d_Cact));
+    if (where == PPRPA_HOST) {
+        std::vector<double> ca((size_t)nbasis * n);
+        for (int m = 0; m < nbasis; ++m)
+            for (int p = 0; p < n; ++p) ca[(size_t)m * n + p] = C[(size_t)m * nmo + first + p];
+        PP_CUDA(cudaMemcpyAsync(d_Cact, ca.data(), sizeof(double) * ca.size(), cudaMemcpyHostToDevice, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+    } else {
+        PP_CUDA(cudaMemcpy2DAsync(d_Cact, sizeof(double) * n, C + first, sizeof(double) * nmo,
+                                  sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
+    }
+    const int64_t nb2 = (int64_t)nbasis * nbasis;
+    PP_CUDA(cudaMalloc(&c->d_L, sizeof(double) * (size_t)naux * n * n));
+    c->naux = naux;
+    // chunk of P: AO slices (host input) plus the half-transformed H = AO^P C_act
+    const int64_t per_p = sizeof(double) * (nb2 + (int64_t)nbasis * n);
+    const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (2LL << 30) / per_p));
+    double *d_ao = nullptr, *d_H;
+    if (where == PPRPA_HOST) PP_TRY(ws_get(c, "ao_slab", sizeof(double) * nb2 * pc, (void**)&d_ao));
+    PP_TRY(ws_get(c, "ao_H", sizeof(double) * (size_t)nbasis * n * pc, (void**)&d_H));
+    for (int P0 = 0; P0 < naux; P0 += pc) {
+        const int np = std::min(pc, naux - P0);
+        const double* src;
+        if (where == PPRPA_HOST) {
+            PP_CUDA(cudaMemcpyAsync(d_ao, ao3c + (size_t)P0 * nb2, sizeof(double) * nb2 * np,
+                                    cudaMemcpyHostToDevice, st));
+            src = d_ao;
+        } else {
+            src = ao3c + (size_t)P0 * nb2;
+        }
+        // H^P = (P|mu nu) C_act   (nbasis x n)
+        Dgemm g1;
+        g1.M = nbasis; g1.N = n; g1.K = nbasis;
+        g1.A = src; g1.lda = nbasis; g1.sA1 = nb2;
+        g1.B = d_Cact; g1.ldb = n;
+        g1.C = d_H; g1.ldc = n; g1.sC1 = (int64_t)nbasis * n;
+        g1.nb1 = np;
+        PP_TRY(dgemm(g1, st));
+        // L^P = C_act^T H^P   (n x n)
+        Dgemm g2;
+        g2.M = n; g2.N = n; g2.K = nbasis;
+        g2.A = d_Cact; g2.lda = n; g2.transA = 1;
+        g2.B = d_H; g2.ldb = n; g2.sB1 = (int64_t)nbasis * n;
+        g2.C = c->d_L + (size_t)P0 * n * n; g2.ldc = n; g2.sC1 = (int64_t)n * n;
+        g2.nb1 = np;
+        PP_TRY(dgemm(g2, st));
+        if (where == PPRPA_HOST) PP_CUDA(cudaStreamSynchronize(st));
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    c->have_L = true;
+    return PPRPA_OK;
+}
+
+int pprpa_set_mo(pprpa_ctx* c, int naux, const double* L, int where) {
+    PP_TRY(check_ctx(c));
+    if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "set_mo: call set_orbitals first");
+    if (naux <= 0 || !L || (where != PPRPA_HOST && where != PPRPA_DEVICE))
+        return set_error(PPRPA_ERR_ARG, "set_mo: bad arguments");
+    if (c->have_L) reset_integrals(c);
+    const int n = c->n(), nmo = c->nmo;
+    cudaStream_t st = c->stream;
+    std::vector<int> orb(n);
+    const int first = c->nocc - c->no;
+    for (int p = 0; p < n; ++p) orb[p] = first + p;
+    int* d_orb;
+    PP_TRY(ws_get(c, "mo_orb", sizeof(int) * n, (void**)&d_orb));
+    PP_CUDA(cudaMemcpyAsync(d_orb, orb.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    PP_CUDA(cudaMalloc(&c->d_L, sizeof(double) * (size_t)naux * n * n));
+    c->naux = naux;
+    const int64_t nm2 = (int64_t)nmo * nmo;
+    if (where == PPRPA_DEVICE) {
+        PP_TRY(launch_extract_active(L, naux, nmo, d_orb, n, c->d_L, st));
+    } else {
+        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * nm2)));
+        double* d_slab;
+        PP_TRY(ws_get(c, "mo_slab", sizeof(double) * nm2 * pc, (void**)&d_slab));
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = std::min(pc, naux - P0);
+            PP_CUDA(cudaMemcpyAsync(d_slab, L + (size_t)P0 * nm2, sizeof(double) * nm2 * np,
+                                    cudaMemcpyHostToDevice, st));
+            PP_TRY(launch_extract_active(d_slab, np, nmo, d_orb, n, c->d_L + (size_t)P0 * n * n, st));
+            PP_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    c->have_L = true;
+    return PPRPA_OK;
+}
+
+int pprpa_get_L(pprpa_ctx* c, double* out, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (!out) return set_error(PPRPA_ERR_ARG, "get_L: null output");
+    const size_t bytes = sizeof(double) * (size_t)c->naux * c->n() * c->n();
+    PP_CUDA(cudaMemcpyAsync(out, c->d_L, bytes,
+                            where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PPRPA_OK;
+}
+
+int pprpa_dims(pprpa_ctx* c, int mult, int* n, int* naux, int* nvv, int* noo) {
+    PP_TRY(check_ctx(c));
+    if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "dims: call set_orbitals first");
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, mult, &t));
+    if (n) *n = c->n();
+    if (naux) *naux = c->naux;
+    if (nvv) *nvv = t->nvv;
+    if (noo) *noo = t->noo;
+    return PPRPA_OK;
+}
+
+int pprpa_diag(pprpa_ctx* c, int mult, double* out, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (!out) return set_error(PPRPA_ERR_ARG, "diag: null output");
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, mult, &t));
+    double *D, *work;
+    PP_TRY(ws_get(c, "diag_D", sizeof(double) * std::max(t->N, 1), (void**)&D));
+    PP_TRY(ws_get(c, "diag_work", sizeof(double) * (size_t)c->naux * c->n(), (void**)&work));
+    PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, t->d_pp, t->d_pq, t->nvv, t->N, mult, D,
+                       work, c->stream));
+    PP_CUDA(cudaMemcpyAsync(out, D, sizeof(double) * t->N,
+                            where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PPRPA_OK;
+}
+
+int pprpa_sigma(pprpa_ctx* c, int mult, int precision, int k, const double* z, double* sigma,
+                int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (k < 0 || (k > 0 && (!z || !sigma))) return set_error(PPRPA_ERR_ARG, "sigma: bad arguments");
+    if (k == 0) return PPRPA_OK;
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, mult, &t));
+    const size_t bytes = sizeof(double) * (size_t)k * t->N;
+    const double* dz = z;
+    double* ds = sigma;
+    if (where == PPRPA_HOST) {
+        double *bz, *bs;
+        PP_TRY(ws_get(c, "sig_z", bytes, (void**)&bz));
+        PP_TRY(ws_get(c, "sig_s", bytes, (void**)&bs));
+        PP_CUDA(cudaMemcpyAsync(bz, z, bytes, cudaMemcpyHostToDevice, c->stream));
+        dz = bz;
+        ds = bs;
+    }
+    int rc;
+    if (precision == PPRPA_PREC_FP64) rc = sigma_f64(c, mult, k, dz, ds);
+    else if (precision == PPRPA_PREC_BF16) rc = sigma_tc(c, mult, k, dz, ds, 1);
+    else if (precision == PPRPA_PREC_BF16 + 16) rc = sigma_tc(c, mult, k, dz, ds, 3);
+    else return set_error(PPRPA_ERR_ARG, "sigma: unknown precision");
+    if (rc != PPRPA_OK) return rc;
+    if (precision != PPRPA_PREC_FP64) PP_TRY(check_status(c));
+    if (where == PPRPA_HOST)
+        PP_CUDA(cudaMemcpyAsync(sigma, ds, bytes, cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PPRPA_OK;
+}
+
+int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");
+    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, c->last_mult, &t));
+    const int n = c->n(), naux = c->naux, mult = c->last_mult;
+    const int64_t n2 = (int64_t)n * n;
+    cudaStream_t st = c->stream;
+    const double* z = c->d_lastZ + (size_t)root * t->N;
+    const double s = 1.0;  // two-electron addition roots: z^T W z = +1
+    const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (deps) {
+        double* d;
+        PP_TRY(ws_get(c, "grad_eps", sizeof(double) * n, (void**)&d));
+        PP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
+        PP_TRY(launch_grad_eps(z, t->N, t->nvv, t->d_pp, t->d_pq, n, s, d, st));
+        PP_CUDA(cudaMemcpyAsync(deps, d, sizeof(double) * n, kind, st));
+    }
+    if (dL) {
+        // d omega / d L^P = s/2 (Zt L^P Zt^T + Zt^T L^P Zt) = s * t * Zt L^P Zt, t = +1 singlet
+        // (Zt symmetric), -1 triplet (Zt antisymmetric).
+        double *Zt, *T, *out;
+        PP_TRY(ws_get(c, "grad_Zt", sizeof(double) * n2, (void**)&Zt));
+        PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2, st));
+        PP_TRY(launch_unpack_f64(z, 1, t->N, t->d_pp, t->d_pq, n, mult, Zt, st));
+        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * n2)));
+        PP_TRY(ws_get(c, "grad_T", sizeof(double) * n2 * pc, (void**)&T));
+        if (where == PPRPA_DEVICE) out = dL;
+        else PP_TRY(ws_get(c, "grad_dL", sizeof(double) * n2 * pc, (void**)&out));
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = std::min(pc, naux - P0);
+            Dgemm g1;  // T^P = L^P Zt
+            g1.M = n; g1.N = n; g1.K = n;
+            g1.A = c->d_L + (size_t)P0 * n2; g1.lda = n; g1.sA1 = n2;
+            g1.B = Zt; g1.ldb = n;
+            g1.C = T; g1.ldc = n; g1.sC1 = n2;
+            g1.nb1 = np;
+            PP_TRY(dgemm(g1, st));
+            Dgemm g2;  // dL^P = (s t) Zt T^P
+            g2.M = n; g2.N = n; g2.K = n;
+            g2.A = Zt; g2.lda = n;
+            g2.B = T; g2.ldb = n; g2.sB1 = n2;
+            double* dst = where == PPRPA_DEVICE ? out + (size_t)P0 * n2 : out;
+            g2.C = dst; g2.ldc = n; g2.sC1 = n2;
+            g2.nb1 = np;
+            g2.alpha = s * (mult == 1 ? 1.0 : -1.0);
+            PP_TRY(dgemm(g2, st));
+            if (where == PPRPA_HOST) {
+                PP_CUDA(cudaMemcpyAsync(dL + (size_t)P0 * n2, out, sizeof(double) * n2 * np,
+                                        cudaMemcpyDeviceToHost, st));
+                PP_CUDA(cudaStreamSynchronize(st));
+            }
+        }
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
+}  // extern "C"

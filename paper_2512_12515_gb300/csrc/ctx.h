@@ -1,0 +1,73 @@
+// Internal state of a ppRPA context (host runtime of the C ABI).
+#pragma once
+#include <cuda.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "tc.h"
+
+namespace pprpa {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PairTable {
+    int nvv = 0, noo = 0, N = 0;
+    std::vector<int> pp, pq;
+    int* d_pp = nullptr;
+    int* d_pq = nullptr;
+    bool ready = false;
+};
+
+}  // namespace pprpa
+
+struct pprpa_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 152;
+
+    int nmo = 0, nocc = 0;
+    std::vector<double> occ, eps;
+    int no = -1, nv = -1;  // active space
+    bool have_L = false;
+    int naux = 0;
+    double* d_eps = nullptr;  // active orbital energies (n)
+    double* d_L = nullptr;    // [naux][n][n]
+
+    pprpa::PairTable pairs[2];  // [0] singlet, [1] triplet
+
+    // BF16 copies of L for the tensor-core sigma
+    pprpa::PadMap pm;
+    __nv_bfloat16* d_Lhi = nullptr;
+    __nv_bfloat16* d_Llo = nullptr;
+    bool bf16_ready = false;
+
+    int* d_status = nullptr;
+    std::map<std::string, pprpa::DevBuf> ws;  // grow-only named workspaces
+    std::map<std::string, int> tuned_bn;      // autotuned N tile per problem key
+
+    // last solve (for gradients)
+    int last_mult = 0;
+    int last_nroots = 0;
+    int last_N = 0;
+    double* d_lastZ = nullptr;
+
+    int n() const { return no + nv; }
+};
+
+namespace pprpa {
+
+int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out);
+int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out);
+int ensure_bf16(pprpa_ctx* c);
+int sigma_f64(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma);
+int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms);
+int check_status(pprpa_ctx* c);
+
+}  // namespace pprpa

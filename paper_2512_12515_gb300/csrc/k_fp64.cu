@@ -1,0 +1,573 @@
+// FP64 kernels: tiled GEMM and the HBM-bound elementwise steps of the ppRPA path.
+//
+// GB300 has a small FP64 pipe, so these kernels aim at keeping it busy with
+// simple register tiling; everything here is either latency-bound (small
+// shapes) or HBM-bound (pair packing, diagonal, residuals).
+#include "kernels.h"
+
+namespace pprpa {
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM, 64x64 tile, 16-deep k slab, 256 threads, 4x4 outputs per thread.
+constexpr int DG_BM = 64, DG_BN = 64, DG_BK = 16;
+
+__global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int n0 = blockIdx.x * DG_BN, m0 = blockIdx.y * DG_BM;
+    const int z = blockIdx.z;
+    const int split = z % g.splitk;
+    const int b = z / g.splitk;
+    const int i2 = b % g.nb2, i1 = b / g.nb2;
+    const double* A0 = g.A + i1 * g.sA1 + i2 * g.sA2;
+    const double* B0 = g.B + i1 * g.sB1 + i2 * g.sB2;
+    double* C = g.C + i1 * g.sC1 + i2 * g.sC2;
+    int kchunk = (g.K + g.splitk - 1) / g.splitk;
+    kchunk = (kchunk + DG_BK - 1) / DG_BK * DG_BK;
+    const int kbeg = split * kchunk;
+    const int kend = min(g.K, kbeg + kchunk);
+
+    __shared__ double As[DG_BK][DG_BM + 1];
+    __shared__ double Bs[DG_BK][DG_BN + 1];
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (int r = 0; r < g.nr; ++r) {
+        const double* A = A0 + r * g.sAr;
+        const double* B = B0 + r * g.sBr;
+        for (int k0 = kbeg; k0 < kend; k0 += DG_BK) {
+            for (int i = tid; i < DG_BM * DG_BK; i += 256) {
+                int mm, kk;
+                if (!g.transA) { mm = i / DG_BK; kk = i % DG_BK; }
+                else { kk = i / DG_BM; mm = i % DG_BM; }
+                const int64_t gm = m0 + mm, gk = k0 + kk;
+                double v = 0.0;
+                if (gm < g.M && gk < kend) v = g.transA ? A[gk * g.lda + gm] : A[gm * g.lda + gk];
+                As[kk][mm] = v;
+            }
+            for (int i = tid; i < DG_BN * DG_BK; i += 256) {
+                int nn, kk;
+                if (!g.transB) { kk = i / DG_BN; nn = i % DG_BN; }
+                else { nn = i / DG_BK; kk = i % DG_BK; }
+                const int64_t gn = n0 + nn, gk = k0 + kk;
+                double v = 0.0;
+                if (gn < g.N && gk < kend) v = g.transB ? B[gn * g.ldb + gk] : B[gk * g.ldb + gn];
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < DG_BK; ++kk) {
+                double a[4], bb[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty + 16 * i;
+        if (gm >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gn = n0 + tx + 16 * j;
+            if (gn >= g.N) continue;
+            double* c = C + gm * g.ldc + gn;
+            if (g.splitk > 1) {
+                atomicAdd(c, g.alpha * acc[i][j]);
+            } else {
+                double v = g.alpha * acc[i][j];
+                if (g.beta != 0.0) v += g.beta * (*c);
+                *c = v;
+            }
+        }
+    }
+}
+
+int auto_splitk(int M, int N, int K, int batches) {
+    const int64_t tiles = ceil_div(M, DG_BM) * ceil_div(N, DG_BN) * (int64_t)batches;
+    const int64_t target = 4 * 152;
+    if (tiles >= target) return 1;
+    int64_t s = ceil_div(target, tiles);
+    const int64_t kmax = ceil_div(K, 4 * DG_BK);  // keep >= 4 k-slabs per split
+    if (s > kmax) s = kmax;
+    if (s > 1024) s = 1024;
+    return s < 1 ? 1 : (int)s;
+}
+
+int dgemm(const Dgemm& g, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0) return PPRPA_OK;
+    const int64_t zb = (int64_t)g.nb1 * g.nb2 * g.splitk;
+    if (zb > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: too many batches");
+    if (g.K <= 0 || g.nr <= 0) {
+        // C = beta * C
+        if (g.splitk > 1) return PPRPA_OK;
+    }
+    dim3 grid((unsigned)ceil_div(g.N, DG_BN), (unsigned)ceil_div(g.M, DG_BM), (unsigned)zb);
+    if (grid.y > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: M too large");
+    dgemm_kernel<<<grid, 256, 0, st>>>(g);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void extract_active_kernel(const double* __restrict__ Lfull, int naux, int nmo,
+                                      const int* __restrict__ orb, int n,
+                                      double* __restrict__ Lact) {
+    const int64_t total = (int64_t)naux * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = t % n;
+        const int p = (t / n) % n;
+        const int64_t P = t / ((int64_t)n * n);
+        Lact[t] = Lfull[(P * nmo + orb[p]) * nmo + orb[q]];
+    }
+}
+
+int launch_extract_active(const double* Lfull, int naux, int nmo, const int* orb, int n,
+                          double* Lact, cudaStream_t st) {
+    const int64_t total = (int64_t)naux * n * n;
+    if (!total) return PPRPA_OK;
+    extract_active_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0,
+                            st>>>(Lfull, naux, nmo, orb, n, Lact);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal of M (singlet: ((pp|qq) + (pq|pq)) / (1 + d_pq); triplet: (pp|qq) - (pq|pq)).
+__global__ void ldiag_kernel(const double* __restrict__ L, int naux, int n, double* __restrict__ Ld) {
+    const int64_t total = (int64_t)naux * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int p = t % n;
+        const int64_t P = t / n;
+        Ld[t] = L[(P * n + p) * n + p];
+    }
+}
+
+__global__ void diag_kernel(const double* __restrict__ L, const double* __restrict__ Ld, int naux,
+                            int n, const double* __restrict__ eps, const int* __restrict__ pp,
+                            const int* __restrict__ pq, int nvv, int N, int mult,
+                            double* __restrict__ D) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= N) return;
+    const int p = pp[I], q = pq[I];
+    double J = 0.0, K = 0.0;
+    for (int P = 0; P < naux; ++P) {
+        const double lpq = L[((int64_t)P * n + p) * n + q];
+        J = fma(Ld[(int64_t)P * n + p], Ld[(int64_t)P * n + q], J);
+        K = fma(lpq, lpq, K);
+    }
+    const double w = I < nvv ? 1.0 : -1.0;
+    double two_e;
+    if (mult == 1) two_e = (J + K) / (p == q ? 2.0 : 1.0);
+    else two_e = J - K;
+    D[I] = w * (eps[p] + eps[q]) + two_e;
+}
+
+int launch_diag(const double* L, int naux, int n, const double* eps, const int* pp,
+                const int* pq, int nvv, int N, int mult, double* D, double* work,
+                cudaStream_t st) {
+    if (N <= 0) return PPRPA_OK;
+    const int64_t tot = (int64_t)naux * n;
+    ldiag_kernel<<<(unsigned)std::min<int64_t>(ceil_div(tot, 256), 4096), 256, 0, st>>>(L, naux, n, work);
+    PP_CHECK_LAUNCH();
+    diag_kernel<<<(unsigned)ceil_div(N, 128), 128, 0, st>>>(L, work, naux, n, eps, pp, pq, nvv, N,
+                                                           mult, D);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pair packing (FP64 sigma path).  Zt must be zeroed by the caller.
+__global__ void unpack_f64_kernel(const double* __restrict__ z, int k, int N,
+                                  const int* __restrict__ pp, const int* __restrict__ pq, int n,
+                                  int mult, double* __restrict__ Zt) {
+    const int64_t total = (int64_t)k * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = t % N;
+        const int64_t j = t / N;
+        const int p = pp[I], q = pq[I];
+        const double v = z[t];
+        double* Z = Zt + j * (int64_t)n * n;
+        if (mult == 1) {
+            if (p == q) Z[(int64_t)p * n + p] = 1.4142135623730951 * v;
+            else { Z[(int64_t)p * n + q] = v; Z[(int64_t)q * n + p] = v; }
+        } else {
+            Z[(int64_t)p * n + q] = v;
+            Z[(int64_t)q * n + p] = -v;
+        }
+    }
+}
+
+int launch_unpack_f64(const double* z, int k, int N, const int* pp, const int* pq, int n,
+                      int mult, double* Zt, cudaStream_t st) {
+    const int64_t total = (int64_t)k * N;
+    if (!total) return PPRPA_OK;
+    unpack_f64_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(
+        z, k, N, pp, pq, n, mult, Zt);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+__global__ void pack_f64_kernel(const double* __restrict__ O, const double* __restrict__ z, int k,
+                                int N, int nvv, const int* __restrict__ pp,
+                                const int* __restrict__ pq, int n, const double* __restrict__ eps,
+                                int mult, double* __restrict__ sigma) {
+    const int64_t total = (int64_t)k * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = t % N;
+        const int64_t j = t / N;
+        const int p = pp[I], q = pq[I];
+        double o = O[j * (int64_t)n * n + (int64_t)p * n + q];
+        if (mult == 1 && p == q) o *= 0.7071067811865476;
+        const double w = I < nvv ? 1.0 : -1.0;
+        sigma[t] = fma(w * (eps[p] + eps[q]), z[t], o);
+    }
+}
+
+int launch_pack_f64(const double* O, const double* z, int k, int N, int nvv, const int* pp,
+                    const int* pq, int n, const double* eps, int mult, double* sigma,
+                    cudaStream_t st) {
+    const int64_t total = (int64_t)k * N;
+    if (!total) return PPRPA_OK;
+    pack_f64_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(
+        O, z, k, N, nvv, pp, pq, n, eps, mult, sigma);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// BF16 layouts for the tensor-core sigma.
+PadMap make_padmap(int no, int nv) {
+    PadMap m;
+    m.no = no;
+    m.nv = nv;
+    m.no_p = (int)round_up(no, 8);
+    m.nv_p = (int)round_up(nv, 8);
+    m.n_pad = m.no_p + m.nv_p;
+    return m;
+}
+
+__device__ __forceinline__ int pad_to_orb(const PadMap& pm, int r) {
+    if (r < pm.no) return r;
+    if (r >= pm.no_p && r < pm.no_p + pm.nv) return pm.no + (r - pm.no_p);
+    return -1;
+}
+
+__global__ void quantize_bf16_kernel(const double* __restrict__ L, int naux, int n, PadMap pm,
+                                     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+    const int64_t np = pm.n_pad;
+    const int64_t total = (int64_t)naux * np * np;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = t % np;
+        const int r = (t / np) % np;
+        const int64_t P = t / (np * np);
+        const int p = pad_to_orb(pm, r), q = pad_to_orb(pm, c);
+        double x = 0.0;
+        if (p >= 0 && q >= 0) x = L[(P * n + p) * n + q];
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        hi[t] = h;
+        if (lo) lo[t] = __double2bfloat16(x - (double)__bfloat162float(h));
+    }
+}
+
+int launch_quantize_bf16(const double* L, int naux, int n, PadMap pm, __nv_bfloat16* hi,
+                         __nv_bfloat16* lo, cudaStream_t st) {
+    const int64_t total = (int64_t)naux * pm.n_pad * pm.n_pad;
+    if (!total) return PPRPA_OK;
+    quantize_bf16_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 64), 256, 0,
+                           st>>>(L, naux, n, pm, hi, lo);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// Writes the transposed pair matrix Zt^T of each vector into the B operand stacks.
+// The caller zeroes the stacks (padding and the triplet diagonal stay zero).
+__global__ void unpack_bf16_kernel(const double* __restrict__ z, int k, int N, int nvv,
+                                   const int* __restrict__ pp, const int* __restrict__ pq,
+                                   PadMap pm, int mult, __nv_bfloat16* __restrict__ xs_hi,
+                                   __nv_bfloat16* __restrict__ xs_lo, int ldx,
+                                   __nv_bfloat16* __restrict__ ys_hi,
+                                   __nv_bfloat16* __restrict__ ys_lo, int ldy) {
+    const int64_t total = (int64_t)k * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = t % N;
+        const int64_t j = t / N;
+        const double v = z[t];
+        int p = pp[I], q = pq[I];
+        __nv_bfloat16 *hi, *lo;
+        int64_t rows, ld;
+        if (I < nvv) { p -= pm.no; q -= pm.no; hi = xs_hi; lo = xs_lo; rows = pm.nv; ld = ldx; }
+        else { hi = ys_hi; lo = ys_lo; rows = pm.no; ld = ldy; }
+        const int64_t base = j * rows * ld;
+        // Zt[p][q] (p <= q) and Zt[q][p]; stack entry [c][d] = Zt[d][c].
+        double zpq, zqp;
+        if (mult == 1) {
+            zpq = (p == q) ? 1.4142135623730951 * v : v;
+            zqp = zpq;
+        } else {
+            zpq = v;
+            zqp = -v;
+        }
+        const int64_t e1 = base + (int64_t)q * ld + p;  // [c=q][d=p] = Zt[p][q]
+        const int64_t e2 = base + (int64_t)p * ld + q;  // [c=p][d=q] = Zt[q][p]
+        __nv_bfloat16 h1 = __double2bfloat16(zpq);
+        hi[e1] = h1;
+        if (lo) lo[e1] = __double2bfloat16(zpq - (double)__bfloat162float(h1));
+        if (p != q) {
+            __nv_bfloat16 h2 = __double2bfloat16(zqp);
+            hi[e2] = h2;
+            if (lo) lo[e2] = __double2bfloat16(zqp - (double)__bfloat162float(h2));
+        }
+    }
+}
+
+int launch_unpack_bf16(const double* z, int k, int N, int nvv, const int* pp, const int* pq,
+                       PadMap pm, int mult, __nv_bfloat16* xs_hi, __nv_bfloat16* xs_lo, int ldx,
+                       __nv_bfloat16* ys_hi, __nv_bfloat16* ys_lo, int ldy, cudaStream_t st) {
+    const int64_t total = (int64_t)k * N;
+    if (!total) return PPRPA_OK;
+    unpack_bf16_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(
+        z, k, N, nvv, pp, pq, pm, mult, xs_hi, xs_lo, ldx, ys_hi, ys_lo, ldy);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+__global__ void pack_f32_kernel(const float* __restrict__ O, const double* __restrict__ z, int k,
+                                int N, int nvv, const int* __restrict__ pp,
+                                const int* __restrict__ pq, PadMap pm,
+                                const double* __restrict__ eps, int mult,
+                                double* __restrict__ sigma) {
+    const int64_t total = (int64_t)k * N;
+    const int64_t np = pm.n_pad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = t % N;
+        const int64_t j = t / N;
+        const int p = pp[I], q = pq[I];
+        double o = (double)O[j * np * np + (int64_t)pm.map(p) * np + pm.map(q)];
+        if (mult == 1 && p == q) o *= 0.7071067811865476;
+        const double w = I < nvv ? 1.0 : -1.0;
+        sigma[t] = fma(w * (eps[p] + eps[q]), z[t], o);
+    }
+}
+
+int launch_pack_f32(const float* O, const double* z, int k, int N, int nvv, const int* pp,
+                    const int* pq, PadMap pm, const double* eps, int mult, double* sigma,
+                    cudaStream_t st) {
+    const int64_t total = (int64_t)k * N;
+    if (!total) return PPRPA_OK;
+    pack_f32_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(
+        O, z, k, N, nvv, pp, pq, pm, eps, mult, sigma);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Davidson vector kernels.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// R = SZ - omega * W * Zr; norms2[j] += ||R_j||^2 (norms2 zeroed by the caller).
+__global__ void residual_kernel(const double* __restrict__ SZ, const double* __restrict__ Zr,
+                                const double* __restrict__ omega, int N, int nvv,
+                                double* __restrict__ R, double* __restrict__ norms2) {
+    __shared__ double sh[32];
+    const int j = blockIdx.y;
+    const double om = omega[j];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = (int64_t)j * N + i;
+        const double w = i < nvv ? 1.0 : -1.0;
+        const double r = SZ[t] - om * w * Zr[t];
+        R[t] = r;
+        acc = fma(r, r, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(norms2 + j, acc);
+}
+
+int launch_residual(const double* SZ, const double* Zr, const double* omega, int k, int N,
+                    int nvv, double* R, double* norms2, cudaStream_t st) {
+    if (!k || !N) return PPRPA_OK;
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), k);
+    residual_kernel<<<grid, 256, 0, st>>>(SZ, Zr, omega, N, nvv, R, norms2);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// Diagonal preconditioner: out_t = R_sel[t] / (D - omega_sel[t] * w), |denominator| >= 1e-4.
+__global__ void correction_kernel(const double* __restrict__ R, const double* __restrict__ D,
+                                  const double* __restrict__ omega, const int* __restrict__ sel,
+                                  int N, int nvv, double* __restrict__ out) {
+    const int t = blockIdx.y;
+    const int j = sel[t];
+    const double om = omega[j];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = i < nvv ? 1.0 : -1.0;
+        double den = D[i] - om * w;
+        if (fabs(den) < 1e-4) den = den < 0.0 ? -1e-4 : 1e-4;
+        out[(int64_t)t * N + i] = R[(int64_t)j * N + i] / den;
+    }
+}
+
+int launch_correction(const double* R, const double* D, const double* omega, const int* sel,
+                      int kn, int N, int nvv, double* out, cudaStream_t st) {
+    if (!kn || !N) return PPRPA_OK;
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), kn);
+    correction_kernel<<<grid, 256, 0, st>>>(R, D, omega, sel, N, nvv, out);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+__global__ void row_norms2_kernel(const double* __restrict__ X, int N, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int j = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = X[(int64_t)j * N + i];
+        acc = fma(x, x, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(out + j, acc);
+}
+
+int launch_row_norms2(const double* X, int k, int N, double* out, cudaStream_t st) {
+    if (!k || !N) return PPRPA_OK;
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), k);
+    row_norms2_kernel<<<grid, 256, 0, st>>>(X, N, out);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+__global__ void scatter_unit_kernel(double* V, int ld, const int* idx, int k) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < k) V[(int64_t)t * ld + idx[t]] = 1.0;
+}
+
+int launch_scatter_unit(double* V, int ld, const int* idx, int k, cudaStream_t st) {
+    if (!k) return PPRPA_OK;
+    scatter_unit_kernel<<<(unsigned)ceil_div(k, 128), 128, 0, st>>>(V, ld, idx, k);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// Explicit ppRPA matrix from the dense (pr|qs) table: eri[(p*n+r)*n*n + (q*n+s)].
+__global__ void build_matrix_kernel(const double* __restrict__ eri, int n,
+                                    const int* __restrict__ pp, const int* __restrict__ pq, int N,
+                                    int nvv, const double* __restrict__ eps, int mult,
+                                    double* __restrict__ M) {
+    const int64_t total = (int64_t)N * N;
+    const int64_t n2 = (int64_t)n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int J = t % N;
+        const int I = t / N;
+        const int p = pp[I], q = pq[I], r = pp[J], s = pq[J];
+        const double direct = eri[((int64_t)p * n + r) * n2 + (int64_t)q * n + s];  // <pq|rs>
+        const double exch = eri[((int64_t)p * n + s) * n2 + (int64_t)q * n + r];    // <pq|sr>
+        double v;
+        if (mult == 1) {
+            const double f = ((p == q) ? 0.7071067811865476 : 1.0) * ((r == s) ? 0.7071067811865476 : 1.0);
+            v = f * (direct + exch);
+        } else {
+            v = direct - exch;
+        }
+        if (I == J) v += (I < nvv ? 1.0 : -1.0) * (eps[p] + eps[q]);
+        M[t] = v;
+    }
+}
+
+int launch_build_matrix(const double* eri, int n, const int* pp, const int* pq, int N, int nvv,
+                        const double* eps, int mult, double* M, cudaStream_t st) {
+    const int64_t total = (int64_t)N * N;
+    if (!total) return PPRPA_OK;
+    build_matrix_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 64), 256, 0, st>>>(
+        eri, n, pp, pq, N, nvv, eps, mult, M);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// d omega / d eps_p = s * sum_I w_I z_I^2 (d_{p,p_I} + d_{p,q_I}).  deps zeroed by the caller.
+__global__ void grad_eps_kernel(const double* __restrict__ z, int N, int nvv,
+                                const int* __restrict__ pp, const int* __restrict__ pq, double s,
+                                double* __restrict__ deps) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= N) return;
+    const double w = I < nvv ? 1.0 : -1.0;
+    const double v = s * w * z[I] * z[I];
+    atomicAdd(deps + pp[I], v);
+    atomicAdd(deps + pq[I], v);
+}
+
+int launch_grad_eps(const double* z, int N, int nvv, const int* pp, const int* pq, int n,
+                    double s, double* deps, cudaStream_t st) {
+    (void)n;
+    if (!N) return PPRPA_OK;
+    grad_eps_kernel<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(z, N, nvv, pp, pq, s, deps);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa
+
+namespace pprpa {
+
+// out[0] = sum_{i < nw} omega_i - sum_{I < nvv} D_I  (one block, FP64).
+__global__ void ec_sum_kernel(const double* __restrict__ omega, int nw, const double* __restrict__ D,
+                              int nvv, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) acc += omega[i];
+    for (int i = threadIdx.x; i < nvv; i += blockDim.x) acc -= D[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+int launch_ec_sum(const double* omega, int nw, const double* D, int nvv, double* out,
+                  cudaStream_t st) {
+    ec_sum_kernel<<<1, 1024, 0, st>>>(omega, nw, D, nvv, out);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+__global__ void set_diag_kernel(double* M, int N, int nvv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) M[(int64_t)i * N + i] = i < nvv ? 1.0 : -1.0;
+}
+
+int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st) {
+    PP_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)N * N, st));
+    set_diag_kernel<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(W, N, nvv);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa

@@ -1,0 +1,533 @@
+// Blackwell tensor-core (tcgen05 + TMEM + TMA) BF16 GEMM for the density-fitted
+// ppRPA sigma sandwich  O_k = sum_P L^P Zt_k L^P  (Sec. "ppRPA Equation" of the
+// LibppRPA paper, evaluated with <pq|rs> = sum_P L^P_pr L^P_qs).
+//
+// Two stages, both "C = A * B^T" with K-major BF16 operands, FP32 accumulation
+// in tensor memory:
+//   stage 1:  T^P[a, (k, c)] = sum_d L^P[a, d] Zt_k[d, c]
+//             M = naux * n_pad rows (P, a), N = k * nblock (vectors side by side),
+//             K = nblock; stored as BF16 (hi, and lo = residual for the split form).
+//   stage 2:  O_k[a, b] += sum_{P, q} T^P[a, (k, q)] L^P[q, b]
+//             M, N = one pair block (virtual or occupied), K = naux * n_pad,
+//             split over K across CTAs; FP32 atomic accumulation into O.
+// The BF16x3 split form issues hi*hi + hi*lo + lo*hi per K step.
+//
+// Kernel organisation (one CTA per SM, persistent over a static work list):
+//   warps 0-3  epilogue (TMEM lanes 0-127 -> registers -> global)
+//   warp 4     TMA producer (one thread)
+//   warp 5     TMEM allocator + MMA issuer (one thread)
+// Shared-memory ring of STAGES operand slots (full/empty mbarriers) and two
+// TMEM accumulators (full/empty mbarriers) so the epilogue of one tile
+// overlaps the MMAs of the next.  Every wait is bounded; on expiry the kernel
+// raises DEV_TIMEOUT in *status, drains its own copies and MMAs, frees TMEM
+// and returns.
+#include <cuda.h>
+
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+#include "tc.h"
+
+namespace pprpa {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;  // one 128-byte swizzle row of BF16
+constexpr int TC_THREADS = 192;
+constexpr int TC_SMEM_LIMIT = 227 * 1024;
+constexpr unsigned long long TC_WAIT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the abort flag) on expiry or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > TC_WAIT_NS) {
+                *abort_flag = 1;
+                atomicOr(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* m, int x, int y,
+                                       uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* m, int x, int y, int z,
+                                       uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* m, int x, int y, int z,
+                                       int w, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (tcgen05 descriptor format, version 1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct ItemCoord {
+    int m0, n0, batch, kb0, kb1;
+};
+
+__device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
+    ItemCoord c;
+    if (p.mode == 0) {
+        const int nb = item % p.tiles_n;
+        const int mb = item / p.tiles_n;
+        c.m0 = mb * TC_BM;
+        c.n0 = nb * p.BN;
+        c.batch = 0;
+        c.kb0 = 0;
+        c.kb1 = p.kb_total;
+    } else {
+        // item = ((split * nbatch) + batch) * ntiles + tile : K-slices outermost so that
+        // concurrently running CTAs share the same slice of L in L2.
+        const int tile = item % p.ntiles;
+        const int rest = item / p.ntiles;
+        const int batch = rest % p.nbatch;
+        const int split = rest / p.nbatch;
+        const int2 t = p.tile_list[tile];
+        c.m0 = t.x * TC_BM;
+        c.n0 = t.y * p.BN;
+        c.batch = batch;
+        const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
+        c.kb0 = split * per;
+        c.kb1 = min(p.kb_total, c.kb0 + per);
+    }
+    return c;
+}
+
+template <int NTERMS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
+                   const __grid_constant__ CUtensorMap tmA_lo,
+                   const __grid_constant__ CUtensorMap tmB_hi,
+                   const __grid_constant__ CUtensorMap tmB_lo, const TcParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * TC_MAX_STAGES + 5];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = p.stages;
+    const uint32_t a_bytes = TC_BM * TC_BK * 2;
+    const uint32_t b_bytes = (uint32_t)p.BN * TC_BK * 2;
+    const uint32_t slot_bytes = (a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (TC_MAX_STAGES + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + 2 + a); };
+    const uint32_t done_bar = bar0 + 8u * (2 * TC_MAX_STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 128);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        const uint32_t ncols = p.tmem_cols;
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            // last issued parity per slot (for draining on abort)
+            uint32_t issued_mask = 0, issued_par = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
+                const ItemCoord c = decode_item(p, item);
+                for (int kb = c.kb0; kb < c.kb1; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, &abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = smem_u32(smem + (size_t)stage * slot_bytes);
+                    const uint32_t fb = full_bar(stage);
+                    mbar_expect_tx(fb, slot_bytes);
+                    const uint32_t a_hi = sbase, b_hi = sbase + a_bytes;
+                    const uint32_t a_lo = sbase + a_bytes + b_bytes,
+                                   b_lo = sbase + 2 * a_bytes + b_bytes;
+                    if (p.mode == 0) {
+                        const int x = p.a_col_off + kb * TC_BK;
+                        tma_2d(a_hi, &tmA_hi, x, c.m0, fb);
+                        tma_2d(b_hi, &tmB_hi, kb * TC_BK, c.n0, fb);
+                        if (NTERMS == 3) {
+                            tma_2d(a_lo, &tmA_lo, x, c.m0, fb);
+                            tma_2d(b_lo, &tmB_lo, kb * TC_BK, c.n0, fb);
+                        }
+                    } else {
+                        const int P = kb / p.kq_blocks;
+                        const int q = (kb % p.kq_blocks) * TC_BK;
+                        tma_4d(a_hi, &tmA_hi, q, c.batch, p.row_off + c.m0, P, fb);
+                        tma_3d(b_hi, &tmB_hi, q, p.col_off + c.n0, P, fb);
+                        if (NTERMS == 3) {
+                            tma_4d(a_lo, &tmA_lo, q, c.batch, p.row_off + c.m0, P, fb);
+                            tma_3d(b_lo, &tmB_lo, q, p.col_off + c.n0, P, fb);
+                        }
+                    }
+                    issued_mask |= 1u << stage;
+                    issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+                    if (++stage == S) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (abort_flag) {
+                // let every copy this thread issued land before the CTA exits
+                for (int s = 0; s < S; ++s) {
+                    if (!(issued_mask & (1u << s))) continue;
+                    const uint32_t par = (issued_par >> s) & 1u;
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_try(full_bar(s), par) && gtimer() - t0 < TC_WAIT_NS) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = idesc_bf16(p.BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
+                const ItemCoord c = decode_item(p, item);
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(acc * p.BN);
+                for (int kb = c.kb0; kb < c.kb1; ++kb) {
+                    if (!mbar_wait(full_bar(stage), phase, &abort_flag, p.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = smem_u32(smem + (size_t)stage * slot_bytes);
+                    const uint32_t a_hi = sbase, b_hi = sbase + a_bytes;
+                    const uint32_t a_lo = sbase + a_bytes + b_bytes,
+                                   b_lo = sbase + 2 * a_bytes + b_bytes;
+#pragma unroll
+                    for (int k = 0; k < TC_BK / 16; ++k) {
+                        const uint32_t off = k * 32;
+                        const uint32_t first = (kb == c.kb0 && k == 0) ? 0u : 1u;
+                        mma_bf16(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
+                        if (NTERMS == 3) {
+                            mma_bf16(dt, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+                            mma_bf16(dt, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(empty_bar(stage));
+                    if (++stage == S) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            // all MMAs of this CTA complete before TMEM is released
+            mma_commit(done_bar);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(done_bar, 0) && gtimer() - t0 < TC_WAIT_NS) {
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 0-3, TMEM lanes 32*warp ..) ----------------
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        const int row = warp * 32 + lane;
+        for (int item = blockIdx.x; item < p.total_items; item += gridDim.x) {
+            const ItemCoord c = decode_item(p, item);
+            if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status)) break;
+            tc_fence_after();
+            const uint32_t tbase =
+                tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * p.BN);
+            if (p.mode == 0) {
+                const int64_t R = (int64_t)c.m0 + row;
+                const bool rok = R < p.M_rows;
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + c0, v);
+                    if (!rok) continue;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int n = c.n0 + c0 + 8 * h;
+                        if (n >= p.n_total) continue;
+                        const int j = n / p.n_per_j;
+                        const int cc = n - j * p.n_per_j;
+                        const int q = p.t_col_off + cc;
+                        const int64_t base = (R * p.k_vec + j) * (int64_t)p.n_pad;
+                        const bool vec = (cc + 8 <= p.n_per_j) && (n + 8 <= p.n_total) &&
+                                         ((q & 7) == 0);
+                        if (vec) {
+                            __align__(16) __nv_bfloat16 hb[8];
+                            __align__(16) __nv_bfloat16 lb[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const float x = v[8 * h + e];
+                                hb[e] = __float2bfloat16_rn(x);
+                                lb[e] = __float2bfloat16_rn(x - __bfloat162float(hb[e]));
+                            }
+                            *(uint4*)(p.t_hi + base + q) = *(const uint4*)hb;
+                            if (NTERMS == 3) *(uint4*)(p.t_lo + base + q) = *(const uint4*)lb;
+                        } else {
+                            for (int e = 0; e < 8; ++e) {
+                                const int ne = n + e;
+                                if (ne >= p.n_total) break;
+                                const int je = ne / p.n_per_j;
+                                const int ce = ne - je * p.n_per_j;
+                                const int64_t off =
+                                    (R * p.k_vec + je) * (int64_t)p.n_pad + p.t_col_off + ce;
+                                const float x = v[8 * h + e];
+                                const __nv_bfloat16 hv = __float2bfloat16_rn(x);
+                                p.t_hi[off] = hv;
+                                if (NTERMS == 3)
+                                    p.t_lo[off] = __float2bfloat16_rn(x - __bfloat162float(hv));
+                            }
+                        }
+                    }
+                }
+            } else {
+                const int a = c.m0 + row;
+                const bool rok = a < p.m_valid;
+                float* Ob = p.O + (int64_t)c.batch * p.n_pad * p.n_pad +
+                            (int64_t)(p.row_off + a) * p.n_pad + p.col_off;
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + c0, v);
+                    if (!rok) continue;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int b = c.n0 + c0 + e;
+                        if (b < p.n_valid) atomicAdd(Ob + b, v[e]);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty_bar(acc));
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 5) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)p.tmem_cols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps through the driver entry point (no link to libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    return fn;
+}
+
+}  // namespace
+
+int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
+                   const uint64_t* strides_bytes, const uint32_t* box) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return set_error(PPRPA_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    if (((uintptr_t)ptr & 15) != 0) return set_error(PPRPA_ERR_ARG, "tensor map base not 16-byte aligned");
+    cuuint64_t d[5], s[4];
+    cuuint32_t b[5], e[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        e[i] = 1;
+        if (i + 1 < rank) {
+            s[i] = strides_bytes[i];
+            if (s[i] % 16 != 0) return set_error(PPRPA_ERR_ARG, "tensor map stride not a multiple of 16 bytes");
+        }
+    }
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(ptr),
+                    d, s, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PPRPA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return PPRPA_OK;
+}
+
+int tc_stages_for(int BN, int nterms) {
+    const int slot = (TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
+    int s = (TC_SMEM_LIMIT - 2048) / slot;
+    if (s > TC_MAX_STAGES) s = TC_MAX_STAGES;
+    return s;
+}
+
+int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
+                   const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st) {
+    if (p.total_items <= 0) return PPRPA_OK;
+    if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0)
+        return set_error(PPRPA_ERR_ARG, "tc_gemm: BN must be a multiple of 16 in [16, 256]");
+    p.stages = tc_stages_for(p.BN, nterms);
+    if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm: tile too large for shared memory");
+    int cols = 32;
+    while (cols < 2 * p.BN) cols <<= 1;
+    p.tmem_cols = cols;
+    const int slot = (TC_BM * TC_BK * 2 + p.BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
+    const size_t smem = (size_t)slot * p.stages + 1024;
+    const int grid = p.total_items < num_sms ? p.total_items : num_sms;
+    if (nterms == 3) {
+        cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<3><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p);
+    } else {
+        cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p);
+    }
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa

@@ -1,0 +1,526 @@
+// pprpa_solve: explicit-matrix full diagonalisation and the Davidson solver.
+//
+// Davidson (standard, for M z = omega W z, W = diag(I_nvv, -I_noo)):
+//   guess    unit vectors at the lowest diagonal entries of the A block
+//   sigma    Sg = M V for the new vectors (FP64, BF16 or BF16x3 split)
+//   project  G = V Sg^T, S = V W V^T (FP64 dot products)
+//   RR       shift-Cholesky + Jacobi on the GPU (one CTA), roots selected by
+//            positive norm (Eq. xy_norm), lowest first
+//   residual r_j = Sg^T c_j - omega_j W V^T c_j
+//   correct  r_j / (D - omega_j w), two passes of classical Gram-Schmidt
+//            against V, Cholesky-QR among the new vectors
+//   restart  collapse to the current Ritz vectors when the subspace is full
+// Mixed precision runs the same loop with BF16 sigma until the residuals
+// reach the BF16 noise level, collapses to the Ritz vectors, recomputes
+// their sigma with the BF16x3 split form and continues to conv_tol.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+
+#include "ctx.h"
+
+namespace pprpa {
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double total_ms = 0.0;
+    cudaStream_t st;
+    explicit Timer(cudaStream_t s) : st(s) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, st); }
+    void stop() {
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        total_ms += ms;
+    }
+};
+
+// C[i][j] (+)= alpha * sum_k A_i[k] B_j[k] for i < na, j < nb (rows of length K, stride lda/ldb).
+// Always accumulates atomically; zero_first clears the na x nb block of C (ld ldc) first.
+int dots(const double* A, int64_t lda, int na, const double* B, int64_t ldb, int nb, int K,
+         double* C, int64_t ldc, double alpha, bool zero_first, cudaStream_t st) {
+    if (na <= 0 || nb <= 0) return PPRPA_OK;
+    if (zero_first)
+        PP_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * nb, na, st));
+    if (K <= 0) return PPRPA_OK;
+    Dgemm g;
+    g.M = na; g.N = nb; g.K = K;
+    g.A = A; g.lda = lda;
+    g.B = B; g.ldb = ldb; g.transB = 1;
+    g.C = C; g.ldc = ldc;
+    g.alpha = alpha;
+    g.splitk = std::max(2, auto_splitk(na, nb, K, 1));
+    return dgemm(g, st);
+}
+
+// Out[j] = alpha * sum_i coef[j][i] X[i] + beta * Out[j]   (nc x m) x (m x N)
+int combine(const double* coef, int ldc_, int nc, int m, const double* X, int64_t N, double* Out,
+            double alpha, double beta, cudaStream_t st) {
+    if (nc <= 0) return PPRPA_OK;
+    Dgemm g;
+    g.M = nc; g.N = (int)N; g.K = m;
+    g.A = coef; g.lda = ldc_;
+    g.B = X; g.ldb = N;
+    g.C = Out; g.ldc = N;
+    g.alpha = alpha; g.beta = beta;
+    return dgemm(g, st);
+}
+
+void fix_phase(double* z, int N) {
+    int imax = 0;
+    double vmax = -1.0;
+    for (int i = 0; i < N; ++i)
+        if (std::fabs(z[i]) > vmax) { vmax = std::fabs(z[i]); imax = i; }
+    if (N > 0 && z[imax] < 0.0)
+        for (int i = 0; i < N; ++i) z[i] = -z[i];
+}
+
+int write_outputs(pprpa_ctx* c, PairTable* pt, int nroots, const double* d_Z, const double* h_omega,
+                  double* omega, double* X, double* Y) {
+    const int N = pt->N;
+    std::vector<double> Z((size_t)nroots * N);
+    PP_CUDA(cudaMemcpyAsync(Z.data(), d_Z, sizeof(double) * Z.size(), cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    for (int j = 0; j < nroots; ++j) {
+        fix_phase(Z.data() + (size_t)j * N, N);
+        if (omega) omega[j] = h_omega[j];
+        if (X) std::copy(Z.begin() + (size_t)j * N, Z.begin() + (size_t)j * N + pt->nvv, X + (size_t)j * pt->nvv);
+        if (Y && pt->noo)
+            std::copy(Z.begin() + (size_t)j * N + pt->nvv, Z.begin() + (size_t)(j + 1) * N, Y + (size_t)j * pt->noo);
+    }
+    // keep the eigenvectors for gradients
+    if (c->d_lastZ) cudaFree(c->d_lastZ);
+    c->d_lastZ = nullptr;
+    PP_CUDA(cudaMalloc(&c->d_lastZ, sizeof(double) * Z.size()));
+    PP_CUDA(cudaMemcpyAsync(c->d_lastZ, Z.data(), sizeof(double) * Z.size(), cudaMemcpyHostToDevice, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    c->last_nroots = nroots;
+    c->last_N = N;
+    return PPRPA_OK;
+}
+
+// Shift candidates between the highest two-electron removal estimate `lo`
+// and the lowest addition estimate `hi`, best guess first.
+std::vector<double> shift_candidates(double lo, double hi, double prev, bool have_prev) {
+    std::vector<double> m;
+    if (have_prev) m.push_back(prev);
+    if (hi > lo) {
+        const double fr[] = {0.5, 0.25, 0.75, 0.1, 0.9, 0.4, 0.6, 0.02, 0.98};
+        for (double f : fr) m.push_back(lo + f * (hi - lo));
+    } else {
+        const double d = std::max(1e-3, std::fabs(hi - lo));
+        for (int t = 1; t <= 8; ++t) m.push_back(hi - d * t);
+    }
+    return m;
+}
+
+int env_int(const char* name, int dflt) {
+    const char* s = getenv(name);
+    return s ? atoi(s) : dflt;
+}
+double env_dbl(const char* name, double dflt) {
+    const char* s = getenv(name);
+    return s ? atof(s) : dflt;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Explicit ppRPA matrix: the (pr|qs) = sum_P L^P_pr L^P_qs table as one
+// (n^2 x n^2) FP64 product of the fitted integrals, then the spin-adapted
+// elements of Sec. "ppRPA Equation" gathered from it.
+static int build_explicit(pprpa_ctx* c, PairTable* pt, int mult, double* eri, double* M) {
+    const int64_t n2 = (int64_t)c->n() * c->n();
+    Dgemm g;
+    g.M = (int)n2; g.N = (int)n2; g.K = c->naux;
+    g.A = c->d_L; g.lda = n2; g.transA = 1;
+    g.B = c->d_L; g.ldb = n2;
+    g.C = eri; g.ldc = n2;
+    PP_TRY(dgemm(g, c->stream));
+    return launch_build_matrix(eri, c->n(), pt->d_pp, pt->d_pq, pt->N, pt->nvv, c->d_eps, mult, M,
+                               c->stream);
+}
+
+static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, double* omega, double* X,
+                      double* Y, double* ec, pprpa_info* info) {
+    const int N = pt->N, nvv = pt->nvv, n = c->n();
+    cudaStream_t st = c->stream;
+    if (N > 1024) return set_error(PPRPA_ERR_ARG, "full diagonalisation is limited to N <= 1024 pairs; use Davidson");
+    Timer tt(st);
+    tt.start();
+    const int64_t n2 = (int64_t)n * n;
+    double *eri, *M, *W, *work, *om, *coef, *rinfo, *D, *dwork, *mus, *dec;
+    PP_TRY(ws_get(c, "full_eri", sizeof(double) * n2 * n2, (void**)&eri));
+    PP_TRY(ws_get(c, "full_M", sizeof(double) * (size_t)N * N, (void**)&M));
+    PP_TRY(ws_get(c, "full_W", sizeof(double) * (size_t)N * N, (void**)&W));
+    PP_TRY(ws_get(c, "full_work", sizeof(double) * (4 * (size_t)N * N + N), (void**)&work));
+    PP_TRY(ws_get(c, "full_om", sizeof(double) * N, (void**)&om));
+    PP_TRY(ws_get(c, "full_coef", sizeof(double) * (size_t)N * N, (void**)&coef));
+    PP_TRY(ws_get(c, "full_info", sizeof(double) * 8, (void**)&rinfo));
+    PP_TRY(ws_get(c, "full_D", sizeof(double) * N, (void**)&D));
+    PP_TRY(ws_get(c, "full_dwork", sizeof(double) * (size_t)c->naux * n, (void**)&dwork));
+    PP_TRY(ws_get(c, "full_mus", sizeof(double) * 32, (void**)&mus));
+    PP_TRY(ws_get(c, "full_ec", sizeof(double), (void**)&dec));
+    PP_TRY(build_explicit(c, pt, o->mult, eri, M));
+    PP_TRY(launch_metric_matrix(W, N, nvv, st));
+    PP_TRY(launch_diag(c->d_L, c->naux, n, c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
+    std::vector<double> hD(N);
+    PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    PP_CUDA(cudaStreamSynchronize(st));
+    double hi = 1e300, lo = -1e300;
+    for (int i = 0; i < nvv; ++i) hi = std::min(hi, hD[i]);
+    for (int i = nvv; i < N; ++i) lo = std::max(lo, -hD[i]);
+    if (pt->noo == 0) lo = hi - 1.0;
+    // wide scan: the diagonal only estimates the gap edges
+    std::vector<double> cand = shift_candidates(lo, hi, 0.0, false);
+    for (int t = 1; t <= 6; ++t) {
+        cand.push_back(lo - 0.25 * t);
+        cand.push_back(hi + 0.25 * t);
+    }
+    cand.resize(std::min<size_t>(cand.size(), 32));
+    PP_CUDA(cudaMemcpyAsync(mus, cand.data(), sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
+    RRArgs a;
+    a.G = M; a.S = W; a.ld = N; a.m = N;
+    a.mus = mus; a.nmu = (int)cand.size();
+    a.nwant = o->nroots; a.nkeep = nvv;
+    a.work = work; a.omega = om; a.coef = coef; a.info = rinfo;
+    PP_TRY(launch_rayleigh_ritz(a, st));
+    double hinfo[8];
+    PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+    PP_CUDA(cudaStreamSynchronize(st));
+    if ((int)hinfo[0] == DEV_NOTPD)
+        return set_error(PPRPA_ERR_UNSTABLE, "full: no shift makes M - mu W positive definite");
+    if ((int)hinfo[2] != nvv)
+        return set_error(PPRPA_ERR_UNSTABLE, "full: root count by norm differs from the pair count");
+    std::vector<double> h_om(nvv);
+    PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * nvv, cudaMemcpyDeviceToHost, st));
+    if (ec) {
+        PP_TRY(launch_ec_sum(om, nvv, D, nvv, dec, st));
+        PP_CUDA(cudaMemcpyAsync(ec, dec, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(write_outputs(c, pt, o->nroots, coef, h_om.data(), omega, X, Y));
+    tt.stop();
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->converged = 1;
+        info->mu = hinfo[1];
+        info->t_total_ms = tt.total_ms;
+    }
+    c->last_mult = o->mult;
+    return PPRPA_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, double* omega,
+                          double* X, double* Y, pprpa_info* info) {
+    const int N = pt->N, nvv = pt->nvv, noo = pt->noo;
+    const int nroots = o->nroots;
+    cudaStream_t st = c->stream;
+    const int nguess = std::min(nvv, std::max(2 * nroots, nroots + 8));
+    int m_max = o->max_subspace > 0 ? o->max_subspace : std::max(8 * nroots, nguess + 4 * nroots);
+    m_max = std::min(m_max, 128);
+    m_max = std::min(m_max, N);
+    if (m_max < nguess + 1 && N > nguess) m_max = std::min(N, nguess + 1);
+    const int nkeep = std::min(nguess, m_max - 1 > 0 ? m_max - 1 : 1);
+    const int max_new = nroots;
+    Timer t_all(st), t_sig(st);
+    t_all.start();
+
+    double *V, *Sg, *G, *S, *D, *dwork, *R, *Zr, *SZ, *Dn, *Dn2, *H, *rwork, *om, *coef, *rinfo,
+        *mus, *nrm, *Gm, *Tm, *cwork, *dom;
+    int *keep, *sel, *idx;
+    PP_TRY(ws_get(c, "dv_V", sizeof(double) * (size_t)m_max * N, (void**)&V));
+    PP_TRY(ws_get(c, "dv_Sg", sizeof(double) * (size_t)m_max * N, (void**)&Sg));
+    PP_TRY(ws_get(c, "dv_G", sizeof(double) * m_max * m_max, (void**)&G));
+    PP_TRY(ws_get(c, "dv_S", sizeof(double) * m_max * m_max, (void**)&S));
+    PP_TRY(ws_get(c, "dv_D", sizeof(double) * N, (void**)&D));
+    PP_TRY(ws_get(c, "dv_dwork", sizeof(double) * (size_t)c->naux * c->n(), (void**)&dwork));
+    PP_TRY(ws_get(c, "dv_R", sizeof(double) * (size_t)nroots * N, (void**)&R));
+    PP_TRY(ws_get(c, "dv_Zr", sizeof(double) * (size_t)m_max * N, (void**)&Zr));
+    PP_TRY(ws_get(c, "dv_SZ", sizeof(double) * (size_t)m_max * N, (void**)&SZ));
+    const int nbuf = std::max(max_new, std::max(nkeep, nroots));
+    PP_TRY(ws_get(c, "dv_Dn", sizeof(double) * (size_t)nbuf * N, (void**)&Dn));
+    PP_TRY(ws_get(c, "dv_Dn2", sizeof(double) * (size_t)nbuf * N, (void**)&Dn2));
+    PP_TRY(ws_get(c, "dv_H", sizeof(double) * m_max * m_max, (void**)&H));
+    PP_TRY(ws_get(c, "dv_rwork", sizeof(double) * (4 * (size_t)m_max * m_max + m_max), (void**)&rwork));
+    PP_TRY(ws_get(c, "dv_om", sizeof(double) * m_max, (void**)&om));
+    PP_TRY(ws_get(c, "dv_coef", sizeof(double) * m_max * m_max, (void**)&coef));
+    PP_TRY(ws_get(c, "dv_info", sizeof(double) * 8, (void**)&rinfo));
+    PP_TRY(ws_get(c, "dv_mus", sizeof(double) * 32, (void**)&mus));
+    PP_TRY(ws_get(c, "dv_nrm", sizeof(double) * m_max, (void**)&nrm));
+    PP_TRY(ws_get(c, "dv_Gm", sizeof(double) * m_max * m_max, (void**)&Gm));
+    PP_TRY(ws_get(c, "dv_Tm", sizeof(double) * m_max * m_max, (void**)&Tm));
+    PP_TRY(ws_get(c, "dv_cwork", sizeof(double) * (m_max * m_max + m_max), (void**)&cwork));
+    PP_TRY(ws_get(c, "dv_keep", sizeof(int) * m_max, (void**)&keep));
+    PP_TRY(ws_get(c, "dv_sel", sizeof(int) * m_max, (void**)&sel));
+    PP_TRY(ws_get(c, "dv_idx", sizeof(int) * m_max, (void**)&idx));
+    PP_TRY(ws_get(c, "dv_dom", sizeof(double) * m_max, (void**)&dom));
+
+    // a3: diagonal, then the initial guess
+    PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
+    std::vector<double> hD(N);
+    PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    PP_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> order(nvv);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hD[a] < hD[b]; });
+    double dv_min = hD[order[0]], oo_max = -1e300;
+    for (int i = nvv; i < N; ++i) oo_max = std::max(oo_max, -hD[i]);
+    PP_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)nguess * N, st));
+    PP_CUDA(cudaMemcpyAsync(idx, order.data(), sizeof(int) * nguess, cudaMemcpyHostToDevice, st));
+    PP_TRY(launch_scatter_unit(V, N, idx, nguess, st));
+
+    const bool mixed = o->precision == PPRPA_PREC_BF16;
+    int stage = mixed ? 1 : 0;
+    const double tol1 = env_dbl("PPRPA_STAGE1_TOL", std::max(o->conv_tol * 10.0, 1e-2));
+    auto run_sigma = [&](int k, const double* z, double* out) -> int {
+        t_sig.start();
+        int rc;
+        if (stage == 0) rc = sigma_f64(c, o->mult, k, z, out);
+        else rc = sigma_tc(c, o->mult, k, z, out, stage == 1 ? 1 : 3);
+        t_sig.stop();
+        if (rc != PPRPA_OK) return rc;
+        if (stage != 0) PP_TRY(check_status(c));
+        if (info) {
+            info->n_sigma += k;
+            info->sigma_flops += (double)k * 3.0 * c->naux * c->n() *
+                                 ((double)c->nv * c->nv + (double)c->no * c->no);
+        }
+        return PPRPA_OK;
+    };
+    auto project_block = [&](int m0, int m) -> int {
+        const int kn = m - m0;
+        // G[0:m, m0:m] and G[m0:m, 0:m0]
+        PP_TRY(dots(V, N, m, Sg + (size_t)m0 * N, N, kn, N, G + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + (size_t)m0 * N, N, kn, Sg, N, m0, N, G + (size_t)m0 * m_max, m_max, 1.0, true, st));
+        // S[0:m, m0:m] = V W V^T (virtual pairs +, occupied pairs -)
+        PP_TRY(dots(V, N, m, V + (size_t)m0 * N, N, kn, nvv, S + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + nvv, N, m, V + (size_t)m0 * N + nvv, N, kn, noo, S + m0, m_max, -1.0, false, st));
+        return PPRPA_OK;
+    };
+    // collapse the basis onto the first nk Ritz vectors (coef rows), orthonormalised
+    auto collapse = [&](int nk, int m, bool resigma) -> int {
+        PP_TRY(dots(coef, m, nk, coef, m, nk, m, Gm, nk, 1.0, true, st));
+        PP_TRY(launch_cholqr_small(Gm, nk, 1e-14, Tm, keep, cwork, st));
+        PP_TRY(combine(Tm, nk, nk, nk, coef, m, H, 1.0, 0.0, st));  // H = T coef (nk x m)
+        PP_TRY(combine(H, m, nk, m, V, N, Dn2, 1.0, 0.0, st));
+        PP_CUDA(cudaMemcpyAsync(V, Dn2, sizeof(double) * (size_t)nk * N, cudaMemcpyDeviceToDevice, st));
+        if (resigma) {
+            PP_TRY(run_sigma(nk, V, Sg));
+        } else {
+            PP_TRY(combine(H, m, nk, m, Sg, N, Dn2, 1.0, 0.0, st));
+            PP_CUDA(cudaMemcpyAsync(Sg, Dn2, sizeof(double) * (size_t)nk * N, cudaMemcpyDeviceToDevice, st));
+        }
+        return project_block(0, nk);
+    };
+
+    int m = nguess;
+    PP_TRY(run_sigma(nguess, V, Sg));
+    PP_TRY(project_block(0, m));
+    double mu_prev = 0.0;
+    bool have_mu = false;
+    double lo_est = oo_max, hi_est = dv_min;
+    if (noo == 0) lo_est = dv_min - 1.0;
+    std::vector<double> h_om(m_max), h_nrm(nroots), best_hist;
+    int rc_final = PPRPA_ERR_NOCONV;
+    int it = 0, stage1_iters = 0;
+    double hinfo[8] = {0};
+    for (it = 1; it <= o->max_iter; ++it) {
+        // ---- Rayleigh-Ritz ----
+        std::vector<double> cand = shift_candidates(lo_est, hi_est, mu_prev, have_mu);
+        for (int t = 1; t <= 4 && cand.size() < 32; ++t) {
+            cand.push_back(lo_est - 0.5 * t);
+            cand.push_back(hi_est - 0.05 * t);
+        }
+        cand.resize(std::min<size_t>(cand.size(), 32));
+        PP_CUDA(cudaMemcpyAsync(mus, cand.data(), sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
+        RRArgs a;
+        a.G = G; a.S = S; a.ld = m_max; a.m = m;
+        a.mus = mus; a.nmu = (int)cand.size();
+        a.nwant = nroots; a.nkeep = std::max(nkeep, nroots);
+        a.work = rwork; a.omega = om; a.coef = coef; a.info = rinfo;
+        PP_TRY(launch_rayleigh_ritz(a, st));
+        PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * a.nkeep, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+        if ((int)hinfo[0] == DEV_NOTPD)
+            return set_error(PPRPA_ERR_UNSTABLE, "Davidson: no shift makes the projected pencil definite");
+        const int npos = (int)hinfo[2];
+        if (npos < nroots)
+            return set_error(PPRPA_ERR_UNSTABLE, "Davidson: subspace holds fewer addition roots than requested");
+        mu_prev = hinfo[1];
+        have_mu = true;
+        hi_est = hinfo[3];
+        if (hinfo[4] > -1e299) lo_est = hinfo[4];
+        const int nk_avail = std::min(npos, a.nkeep);
+        // ---- Ritz vectors and residuals of the targets ----
+        PP_TRY(combine(coef, m, nroots, m, V, N, Zr, 1.0, 0.0, st));
+        PP_TRY(combine(coef, m, nroots, m, Sg, N, SZ, 1.0, 0.0, st));
+        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * nroots, st));
+        PP_TRY(launch_residual(SZ, Zr, om, nroots, N, nvv, R, nrm, st));
+        PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * nroots, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+        double rmax = 0.0;
+        std::vector<int> todo;
+        for (int j = 0; j < nroots; ++j) {
+            h_nrm[j] = std::sqrt(h_nrm[j]);
+            rmax = std::max(rmax, h_nrm[j]);
+            if (!(h_nrm[j] <= o->conv_tol)) todo.push_back(j);
+        }
+        if (env_int("PPRPA_LOG", 0))
+            fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e\n", it, stage, m,
+                    mu_prev, h_om[0], rmax);
+        if (info) info->max_resid = rmax;
+        if (stage == 1) {
+            ++stage1_iters;
+            best_hist.push_back(rmax);
+            bool stalled = false;
+            if (best_hist.size() >= 4) {
+                const double prev = best_hist[best_hist.size() - 4];
+                stalled = rmax > 0.5 * prev;
+            }
+            if (rmax <= tol1 || stalled || stage1_iters >= o->max_iter / 2) {
+                stage = 2;
+                PP_TRY(collapse(nk_avail, m, true));
+                m = nk_avail;
+                continue;
+            }
+        }
+        if (todo.empty()) {
+            rc_final = PPRPA_OK;
+            break;
+        }
+        if (it == o->max_iter) break;
+        // ---- correction vectors ----
+        const int kn = (int)todo.size();
+        PP_CUDA(cudaMemcpyAsync(sel, todo.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, st));
+        PP_TRY(launch_correction(R, D, om, sel, kn, N, nvv, Dn, st));
+        if (m + kn > m_max) {
+            PP_TRY(collapse(nk_avail, m, false));
+            m = nk_avail;
+        }
+        // ---- orthogonalise against V (two passes of classical Gram-Schmidt) ----
+        std::vector<double> n_before(kn), n_after(kn);
+        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
+        PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
+        PP_CUDA(cudaMemcpyAsync(n_before.data(), nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            PP_TRY(dots(V, N, m, Dn, N, kn, N, H, kn, 1.0, true, st));  // H = V Dn^T (m x kn)
+            Dgemm g;  // Dn -= H^T V
+            g.M = kn; g.N = N; g.K = m;
+            g.A = H; g.lda = kn; g.transA = 1;
+            g.B = V; g.ldb = N;
+            g.C = Dn; g.ldc = N;
+            g.alpha = -1.0; g.beta = 1.0;
+            PP_TRY(dgemm(g, st));
+        }
+        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
+        PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
+        PP_CUDA(cudaMemcpyAsync(n_after.data(), nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> live;
+        for (int t = 0; t < kn; ++t)
+            if (n_after[t] > 1e-20 * std::max(n_before[t], 1e-300)) live.push_back(t);
+        if (live.empty()) break;  // stagnation: no new directions
+        // compact live rows into Dn2
+        for (size_t t = 0; t < live.size(); ++t)
+            PP_CUDA(cudaMemcpyAsync(Dn2 + t * N, Dn + (size_t)live[t] * N, sizeof(double) * N,
+                                    cudaMemcpyDeviceToDevice, st));
+        int kl = (int)live.size();
+        // ---- Cholesky-QR twice among the new vectors ----
+        std::vector<int> hkeep(kl, 1);
+        for (int pass = 0; pass < 2; ++pass) {
+            PP_TRY(dots(Dn2, N, kl, Dn2, N, kl, N, Gm, kl, 1.0, true, st));
+            PP_TRY(launch_cholqr_small(Gm, kl, 1e-12, Tm, keep, cwork, st));
+            PP_TRY(combine(Tm, kl, kl, kl, Dn2, N, Dn, 1.0, 0.0, st));
+            PP_CUDA(cudaMemcpyAsync(Dn2, Dn, sizeof(double) * (size_t)kl * N, cudaMemcpyDeviceToDevice, st));
+            std::vector<int> kp(kl);
+            PP_CUDA(cudaMemcpyAsync(kp.data(), keep, sizeof(int) * kl, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaStreamSynchronize(st));
+            for (int t = 0; t < kl; ++t) hkeep[t] &= kp[t];
+        }
+        int added = 0;
+        for (int t = 0; t < kl; ++t) {
+            if (!hkeep[t]) continue;
+            PP_CUDA(cudaMemcpyAsync(V + (size_t)(m + added) * N, Dn2 + (size_t)t * N, sizeof(double) * N,
+                                    cudaMemcpyDeviceToDevice, st));
+            ++added;
+        }
+        if (added == 0) break;
+        PP_TRY(run_sigma(added, V + (size_t)m * N, Sg + (size_t)m * N));
+        PP_TRY(project_block(m, m + added));
+        m += added;
+    }
+    if (mixed && stage == 1) stage = 2;  // not reached normally
+    PP_TRY(write_outputs(c, pt, nroots, Zr, h_om.data(), omega, X, Y));
+    t_all.stop();
+    if (info) {
+        info->iters = std::min(it, o->max_iter);
+        info->iters_stage1 = stage1_iters;
+        info->converged = rc_final == PPRPA_OK;
+        info->mu = mu_prev;
+        info->t_sigma_ms = t_sig.total_ms;
+        info->t_total_ms = t_all.total_ms;
+    }
+    c->last_mult = o->mult;
+    if (rc_final != PPRPA_OK) return set_error(PPRPA_ERR_NOCONV, "Davidson: max_iter reached");
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa
+
+using namespace pprpa;
+
+extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, double* X, double* Y,
+                           double* ec, pprpa_info* info) {
+    if (!c || !o) return set_error(PPRPA_ERR_ARG, "solve: null argument");
+    PP_CUDA(cudaSetDevice(c->device));
+    if (!c->have_L) return set_error(PPRPA_ERR_STATE, "solve: integrals not set");
+    if (o->mult != 1 && o->mult != 3) return set_error(PPRPA_ERR_ARG, "solve: mult must be 1 or 3");
+    if (o->channel != PPRPA_CHANNEL_PP) return set_error(PPRPA_ERR_ARG, "solve: only the pp channel is supported");
+    if (o->method != PPRPA_METHOD_FULL && o->method != PPRPA_METHOD_DAVIDSON)
+        return set_error(PPRPA_ERR_ARG, "solve: unknown method");
+    if (o->precision != PPRPA_PREC_FP64 && o->precision != PPRPA_PREC_BF16)
+        return set_error(PPRPA_ERR_ARG, "solve: unknown precision");
+    PairTable* pt;
+    PP_TRY(ensure_pairs(c, o->mult, &pt));
+    if (o->nroots < 1 || o->nroots > pt->nvv) return set_error(PPRPA_ERR_ARG, "solve: nroots out of range");
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (o->method == PPRPA_METHOD_FULL) return solve_full(c, o, pt, omega, X, Y, ec, info);
+    if (!(o->conv_tol > 0.0) || o->max_iter < 1) return set_error(PPRPA_ERR_ARG, "solve: bad tolerance / max_iter");
+    if (ec) *ec = NAN;
+    return solve_davidson(c, o, pt, omega, X, Y, info);
+}
+
+extern "C" int pprpa_build_matrix(pprpa_ctx* c, int mult, double* Mout, int where) {
+    if (!c || !Mout) return set_error(PPRPA_ERR_ARG, "build_matrix: null argument");
+    PP_CUDA(cudaSetDevice(c->device));
+    if (!c->have_L) return set_error(PPRPA_ERR_STATE, "build_matrix: integrals not set");
+    PairTable* pt;
+    PP_TRY(ensure_pairs(c, mult, &pt));
+    const int64_t n2 = (int64_t)c->n() * c->n();
+    const size_t mbytes = sizeof(double) * (size_t)pt->N * pt->N;
+    double *eri, *M;
+    PP_TRY(ws_get(c, "bm_eri", sizeof(double) * n2 * n2, (void**)&eri));
+    if (where == PPRPA_DEVICE) M = Mout;
+    else PP_TRY(ws_get(c, "bm_M", mbytes, (void**)&M));
+    PP_TRY(build_explicit(c, pt, mult, eri, M));
+    if (where != PPRPA_DEVICE)
+        PP_CUDA(cudaMemcpyAsync(Mout, M, mbytes, cudaMemcpyDeviceToHost, c->stream));
+    PP_CUDA(cudaStreamSynchronize(c->stream));
+    return PPRPA_OK;
+}

@@ -1,0 +1,46 @@
+// Host/device interface of the tcgen05 BF16 GEMM used by the sigma sandwich.
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace pprpa {
+
+constexpr int TC_MAX_STAGES = 8;
+
+struct TcParams {
+    int mode = 0;      // 0: stage 1 (BF16 T output), 1: stage 2 (FP32 atomic O output)
+    int BN = 256;      // N tile (multiple of 16, <= 256)
+    int stages = 0;    // set by the launcher
+    int tmem_cols = 0; // set by the launcher
+    int total_items = 0;
+    int kb_total = 0;  // 64-wide K blocks per work item before splitting
+    int* status = nullptr;
+    // stage 1
+    int tiles_n = 0;
+    int64_t M_rows = 0;  // naux * n_pad
+    int a_col_off = 0;   // K offset of the block inside L_pad columns
+    int n_per_j = 0;     // columns per vector (block size)
+    int n_total = 0;     // k * n_per_j
+    int t_col_off = 0;   // column offset of the block in T rows
+    int n_pad = 0;
+    int k_vec = 0;
+    __nv_bfloat16* t_hi = nullptr;
+    __nv_bfloat16* t_lo = nullptr;
+    // stage 2
+    const int2* tile_list = nullptr;  // (m tile, n tile) pairs to compute
+    int ntiles = 0, nbatch = 0, nsplit = 1;
+    int kq_blocks = 0;   // ceil(n_pad / 64)
+    int row_off = 0, col_off = 0;
+    int m_valid = 0, n_valid = 0;
+    float* O = nullptr;  // [k][n_pad][n_pad]
+};
+
+int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
+                   const uint64_t* strides_bytes, const uint32_t* box);
+int tc_stages_for(int BN, int nterms);
+int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
+                   const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms,
+                   cudaStream_t st);
+
+}  // namespace pprpa

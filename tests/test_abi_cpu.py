@@ -1,0 +1,77 @@
+"""C-ABI checks that need no GPU: the library loads and exports every
+function include/pprpa.h declares, the binding mirrors the header, and host
+argument validation returns error codes instead of crashing."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pprpa.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pprpa_[A-Za-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_12515_gb300 import build
+
+    build.build()
+    from paper_2512_12515_gb300 import _lib
+
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pprpa_create", "pprpa_destroy", "pprpa_set_orbitals", "pprpa_set_active",
+                     "pprpa_set_ao", "pprpa_set_mo", "pprpa_sigma", "pprpa_diag",
+                     "pprpa_build_matrix", "pprpa_solve", "pprpa_grad"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_mirrors_header():
+    from paper_2512_12515_gb300 import _lib
+
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_error_strings(lib):
+    assert lib.pprpa_strerror(0) == b"ok"
+    for code in range(-1, -9, -1):
+        assert lib.pprpa_strerror(code) != b"unknown error"
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.pprpa_set_orbitals(None, 3, None, None) == -1
+    assert lib.pprpa_solve(None, None, None, None, None, None, None) == -1
+    lib.pprpa_destroy(None)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.pprpa_create(ctypes.byref(h), 0, None)
+    assert rc in (-1, -2) and not h.value
+    assert len(lib.pprpa_last_error()) > 0
+
+
+def test_options_struct_layout_matches_header():
+    from paper_2512_12515_gb300 import _lib
+
+    # int, int, int, int, int, double, int, int, int  -> 48 bytes with alignment
+    assert ctypes.sizeof(_lib.Options) == 48
+    assert ctypes.sizeof(_lib.Info) == 4 * 4 + 6 * 8

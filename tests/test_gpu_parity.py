@@ -1,0 +1,189 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances:
+* FP64 kernels (AO->MO, diagonal, explicit matrix, FP64 sigma): 1e-11
+  relative to the largest entry; only the summation order differs.
+* Eigenvalues, FP64 (full diagonalisation and Davidson): 1e-8 Ha.
+* BF16 sigma: operands rounded to 8 significant bits, so a few 1e-3 of
+  the two-electron magnitude; BF16x3 split sigma: a few 1e-6.
+* Mixed-precision Davidson (BF16, then BF16x3 split): |d omega| <= 1e-5 Ha.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pp():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_12515_gb300 as m
+
+    return m
+
+
+def make(no, nv, naux, seed, extra=4):
+    nb = no + nv + extra
+    spec = synth.SystemSpec("t", nb, no + 2, naux, no, nv, seed)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], no, nv)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    return spec, s, L, s["eps"][orb]
+
+
+def gpu_ctx(pp, spec, s):
+    c = pp.Context(0)
+    c.set_orbitals(s["occ"], s["eps"])
+    c.set_active(spec.nocc_act, spec.nvir_act)
+    c.set_ao(s["C"], s["ao3c"])
+    return c
+
+
+CASES = [(5, 20, 120, 1), (1, 7, 9, 2), (3, 33, 50, 3), (13, 70, 97, 4)]
+
+
+@pytest.mark.parametrize("no,nv,naux,seed", CASES)
+def test_ao_to_mo(pp, no, nv, naux, seed):
+    spec, s, L, eps = make(no, nv, naux, seed)
+    with gpu_ctx(pp, spec, s) as c:
+        got = c.get_L()
+    assert np.abs(got - L).max() <= 1e-12 * np.abs(L).max()
+
+
+def test_set_mo_matches_set_ao(pp):
+    spec, s, L, eps = make(4, 11, 30, 5)
+    Lfull = oracle.ao_to_mo(s["ao3c"], s["C"], np.arange(spec.nmo))
+    with pp.Context(0) as c:
+        c.set_orbitals(s["occ"], s["eps"])
+        c.set_active(4, 11)
+        c.set_mo(np.ascontiguousarray(Lfull))
+        got = c.get_L()
+    assert np.abs(got - L).max() <= 1e-13
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("no,nv,naux,seed", CASES[:3])
+def test_diag_and_explicit_matrix(pp, mult, no, nv, naux, seed):
+    spec, s, L, eps = make(no, nv, naux, seed)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    with gpu_ctx(pp, spec, s) as c:
+        D = c.diag(mult)
+        Mg = c.build_matrix(mult)
+    scale = np.abs(M).max()
+    assert np.abs(D - np.diag(M)).max() <= 1e-12 * scale
+    assert np.abs(Mg - M).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("no,nv,naux,seed", CASES)
+def test_sigma_all_precisions(pp, mult, no, nv, naux, seed):
+    spec, s, L, eps = make(no, nv, naux, seed)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    Z = synth.random_trial_vectors(nvv + noo, 5, 7 + seed)
+    ref = Z @ M.T
+    two_e = Z @ (M - np.diag(np.diag(M))).T
+    scale = np.abs(two_e).max()
+    with gpu_ctx(pp, spec, s) as c:
+        s64 = c.sigma(mult, Z, pp.PREC_FP64)
+        s16 = c.sigma(mult, Z, pp.PREC_BF16)
+        s48 = c.sigma(mult, Z, pp.PREC_BF16_SPLIT)
+    assert np.abs(s64 - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(s16 - ref).max() <= 2e-2 * scale
+    assert np.abs(s48 - ref).max() <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("k", [1, 3, 17])
+def test_sigma_batch_sizes_and_device_pointers(pp, k):
+    import torch
+
+    spec, s, L, eps = make(6, 40, 64, 8)
+    M, nvv, noo = oracle.build_matrix(eps, 6, L, 1)
+    Z = synth.random_trial_vectors(nvv + noo, k, 3)
+    with gpu_ctx(pp, spec, s) as c:
+        zd = torch.as_tensor(Z, device="cuda")
+        out = c.sigma(1, zd, pp.PREC_BF16_SPLIT)
+        got = out.cpu().numpy()
+    two_e = Z @ (M - np.diag(np.diag(M))).T
+    assert np.abs(got - Z @ M.T).max() <= 2e-5 * np.abs(two_e).max()
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_full_diagonalisation_small_workload(pp, mult):
+    spec = synth.CONFIGS["c0"]
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    eps = s["eps"][orb]
+    M, nvv, noo = oracle.build_matrix(eps, spec.nocc_act, L, mult)
+    ref = oracle.solve_full(M, nvv, noo)
+    ec_ref = oracle.correlation_energy(M, nvv, noo, ref)[0]
+    with gpu_ctx(pp, spec, s) as c:
+        res = c.solve(mult=mult, nroots=nvv, method=pp.METHOD_FULL, want_ec=True)
+    assert np.abs(res["omega"] - ref["omega_pp"]).max() <= 1e-8
+    assert abs(res["ec"] - ec_ref) <= 1e-8
+    Z = np.hstack([res["X"], res["Y"]]).T
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    assert np.allclose(np.einsum("ik,i,ik->k", Z, w, Z), 1.0, atol=1e-10)
+    # eigenvectors of the non-degenerate lowest roots, under the phase convention
+    gap = np.diff(ref["omega_pp"][:6])
+    for r in range(5):
+        if gap[r] > 1e-4 and (r == 0 or gap[r - 1] > 1e-4):
+            assert np.abs(Z[:, r] - ref["z_pp"][:, r]).max() < 1e-7
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("prec,tol", [("PREC_FP64", 1e-8), ("PREC_BF16", 1e-5)])
+def test_davidson_small_workload(pp, mult, prec, tol):
+    spec = synth.CONFIGS["c0"]
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    eps = s["eps"][orb]
+    M, nvv, noo = oracle.build_matrix(eps, spec.nocc_act, L, mult)
+    ref = oracle.solve_full(M, nvv, noo)["omega_pp"][:10]
+    with gpu_ctx(pp, spec, s) as c:
+        res = c.solve(mult=mult, nroots=10, precision=getattr(pp, prec),
+                      conv_tol=1e-7 if prec == "PREC_FP64" else 1e-5)
+    assert res["info"]["converged"] == 1
+    assert np.abs(res["omega"] - ref).max() <= tol
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_gradient_matches_oracle(pp, mult):
+    spec, s, L, eps = make(3, 9, 14, 12)
+    M, nvv, noo = oracle.build_matrix(eps, 3, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    with gpu_ctx(pp, spec, s) as c:
+        c.solve(mult=mult, nroots=3, method=pp.METHOD_FULL)
+        for r in range(3):
+            dL, de = c.grad(r)
+            de_ref, dL_ref = oracle.grad_omega(eps, 3, L, mult, sol["z_pp"][:, r])
+            assert np.abs(de - de_ref).max() <= 1e-9
+            assert np.abs(dL - dL_ref).max() <= 1e-9 * max(1.0, np.abs(dL_ref).max())
+
+
+def test_error_paths(pp):
+    spec, s, L, eps = make(2, 5, 8, 1)
+    with pp.Context(0) as c:
+        with pytest.raises(pp.PprpaError) as e:
+            c.solve(mult=1, nroots=2)
+        assert e.value.code == -7  # no integrals yet
+        c.set_orbitals(s["occ"], s["eps"])
+        with pytest.raises(pp.PprpaError):
+            c.set_active(100, 2)
+        c.set_active(2, 5)
+        c.set_ao(s["C"], s["ao3c"])
+        with pytest.raises(pp.PprpaError):
+            c.solve(mult=2, nroots=1)
+        with pytest.raises(pp.PprpaError):
+            c.solve(mult=1, nroots=1000)
+        with pytest.raises(pp.PprpaError):
+            c.grad(0)
+        r = c.solve(mult=1, nroots=2, max_iter=1, conv_tol=1e-14, raise_noconv=False)
+        assert r["rc"] == -4
