@@ -19,9 +19,9 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2512_12515_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__.build()
     from paper_2512_12515_gb300 import _lib
 
     return _lib.load()
