@@ -32,7 +32,7 @@ def _pairs_all(n, no, mult):
     return np.concatenate([pv, po]), np.concatenate([qv, qo]), len(pv), len(po)
 
 
-def ri_sigma(eps_act, nocc_act, L_act, mult, Z, p_chunk=16):
+def ri_sigma(eps_act, nocc_act, L_act, mult, Z):
     """sigma = M z for k vectors (rows of ``Z``), from the density-fitted integrals.
 
     With <ab|cd> = sum_P L^P_ac L^P_bd, the two-electron part of
@@ -60,10 +60,14 @@ def ri_sigma(eps_act, nocc_act, L_act, mult, Z, p_chunk=16):
     else:
         Zt[:, p, q] = Z
         Zt[:, q, p] = -Z
+    naux = L.shape[0]
+    Lrows = L.reshape(naux * n, n)  # rows (P, b)
     O = np.zeros((k, n, n))
-    for p0 in range(0, L.shape[0], p_chunk):
-        Lc = L[p0:p0 + p_chunk][:, None]  # (c, 1, n, n)
-        O += np.matmul(np.matmul(Lc, Zt[None]), Lc).sum(axis=0)
+    for j in range(k):
+        # sum_P L^P Zt L^P as two matrix products over the stacked index (P, b):
+        # T^P = L^P Zt for all P at once, then O[a, c] = sum_{P, b} T^P[a, b] L^P[b, c].
+        T = (Lrows @ Zt[j]).reshape(naux, n, n)
+        O[j] = T.transpose(1, 0, 2).reshape(n, naux * n) @ Lrows
     two_e = O[:, p, q]
     if mult == 1:
         two_e = two_e / np.where(p == q, np.sqrt(2.0), 1.0)[None, :]
