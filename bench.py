@@ -1,0 +1,368 @@
+"""Benchmark of the ppRPA hot path on GB300: the density-fitted sigma sandwich.
+
+Workload (default): nbasis 900, 50 occupied + 600 virtual active orbitals,
+naux 2700, synthetic inputs (see synth/).  One step = sigma = M z for the
+10-vector trial block a Davidson iteration for the lowest 10 singlet roots
+applies, in the mixed-precision form (BF16 tensor-core sandwich with FP32
+accumulation, FP64 in and out), with the fitted integrals resident in HBM.
+value = algorithmic sigma TFLOP/s (3 naux n (nv^2 + no^2) per vector).
+The JSON line also carries the live roofline of the tensor-core GEMM, the
+end-to-end rate through the C ABI with host buffers, the BF16x3 split and
+FP64 forms of the same block, time-to-solution of the lowest 10 roots on the
+small stable workload (FP64 vs mixed), and the CPU oracle baseline.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ppRPA lowest-10-root solve time & sigma TFLOP/s, mixed vs FP64 at 1e-5 Ha"
+WORKLOADS = {
+    "c2": synth.CONFIGS["c2"],
+    "c1": synth.CONFIGS["c1"],
+    "c4": synth.CONFIGS["c4"],
+}
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_sample(spec, frac=0.1, seed=3):
+    """Time the FP64 oracle on a bounded sample of the workload: its own AO->MO
+    transform and one RI sigma application over the first `frac` of the
+    auxiliary index (sigma cost is linear in naux).  Returns seconds per full
+    single-vector sigma and what the sample was."""
+    import oracle
+
+    s = synth.make_system(spec, with_ao=False)
+    nP = max(1, int(round(spec.naux * frac)))
+    _, ao = next(synth.ao_slices(spec, nP))
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    L = oracle.ao_to_mo(ao, s["C"], orb)
+    eps = s["eps"][orb]
+    nvv = spec.nvir_act * (spec.nvir_act + 1) // 2
+    noo = spec.nocc_act * (spec.nocc_act + 1) // 2
+    z = synth.random_trial_vectors(nvv + noo, 1, seed)
+    t0 = time.perf_counter()
+    oracle.ri_sigma(eps, spec.nocc_act, L, 1, z)
+    dt = time.perf_counter() - t0
+    return dt * spec.naux / nP, f"1 FP64 RI sigma over {nP} of {spec.naux} aux functions (oracle), scaled by naux"
+
+
+def run_reference(args, spec, rank):
+    """The oracle as the reference arm: FP64 RI sigma on a bounded sample."""
+    if rank != 0:
+        return
+    f_vec = 3.0 * spec.naux * spec.n_act * (spec.nvir_act ** 2 + spec.nocc_act ** 2)
+    for _ in range(args.warmup):
+        cpu_sample(spec, args.cpu_frac)
+    times = []
+    sample = ""
+    for _ in range(args.steps):
+        t, sample = cpu_sample(spec, args.cpu_frac)
+        times.append(t)
+    t_vec = float(np.mean(times))
+    value = f_vec / t_vec / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_vec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{spec.name}: nbasis={spec.nbasis} nocc={spec.nocc} "
+                               f"nocc_act={spec.nocc_act} nvir_act={spec.nvir_act} naux={spec.naux}; "
+                               "one step = oracle FP64 sigma of one trial vector (sampled over naux)",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def setup_context(pp, torch, spec, device, stream):
+    """Generate the workload and run the FP64 AO->MO transform on the device.
+    Returns (context, ao2mo_ms, occ/eps host arrays)."""
+    head = synth.make_system(spec, with_ao=False)
+    ao = torch.empty((spec.naux, spec.nbasis, spec.nbasis), dtype=torch.float64, device=device)
+    for p0, blk in synth.ao_slices(spec, 96):
+        ao[p0:p0 + blk.shape[0]].copy_(torch.from_numpy(blk))
+    C = torch.from_numpy(head["C"]).to(device)
+    c = pp.Context(device.index or 0, stream=stream.cuda_stream)
+    c.set_orbitals(head["occ"], head["eps"])
+    c.set_active(spec.nocc_act, spec.nvir_act)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c.set_ao(C, ao)
+    torch.cuda.synchronize()
+    ao2mo_ms = (time.perf_counter() - t0) * 1e3
+    del ao
+    torch.cuda.empty_cache()
+    return c, ao2mo_ms, head
+
+
+def small_solve(pp, torch, stream):
+    """Time-to-solution of the lowest 10 singlet roots on the small stable workload
+    (nbasis 40, 5 + 20 active, naux 120), FP64 form and mixed form."""
+    spec = synth.CONFIGS["c0"]
+    s = synth.make_system(spec)
+    out = {}
+    with pp.Context(0, stream=stream.cuda_stream) as c:
+        c.set_orbitals(s["occ"], s["eps"])
+        c.set_active(spec.nocc_act, spec.nvir_act)
+        c.set_ao(s["C"], s["ao3c"])
+        for name, prec, tol in (("fp64", pp.PREC_FP64, 1e-7), ("mixed", pp.PREC_BF16, 1e-5)):
+            c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
+            t0 = time.perf_counter()
+            r = c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
+            out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "omega": r["omega"],
+                         "iters": r["info"]["iters"], "converged": r["info"]["converged"]}
+    d = float(np.abs(out["mixed"]["omega"] - out["fp64"]["omega"]).max())
+    for v in out.values():
+        v["omega"] = [float(x) for x in v["omega"]]
+    out["max_abs_domega_mixed_vs_fp64"] = d
+    out["workload"] = "nbasis=40 nocc=5 nvir_act=20 naux=120 (stable), lowest 10 singlet N+2 roots"
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--nroots", type=int, default=10)
+    ap.add_argument("--cpu-frac", type=float, default=0.1)
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / solve side measurements")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, spec, rank)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import paper_2512_12515_gb300 as pp
+
+    # the library runs on a stream of ours, so events on it bracket its kernels
+    lib_stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(lib_stream)
+    c, ao2mo_ms, head = setup_context(pp, torch, spec, device, lib_stream)
+    n, naux, nvv, noo = c.dims(1)
+    N = nvv + noo
+    k = args.nroots  # the Davidson block: one trial vector per wanted root
+    z = synth.random_trial_vectors(N, k, 11)
+    z /= np.linalg.norm(z, axis=1, keepdims=True)
+    zd = torch.from_numpy(z).to(device)
+    sd = torch.empty_like(zd)
+    f_vec = 3.0 * spec.naux * spec.n_act * (spec.nvir_act ** 2 + spec.nocc_act ** 2)
+
+    def step(prec):
+        c.sigma(1, zd, prec, out=sd)
+
+    for _ in range(max(3, args.warmup)):
+        step(pp.PREC_BF16)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------- timed region: BF16 sigma of the 10-vector block ----------------
+    stream = lib_stream
+    clk = ClockSampler(local)
+    c.profile(True)
+    launches0 = pp.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(pp.PREC_BF16)
+    ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    launches = pp.kernel_launches() - launches0
+    prof = c.profile(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([elapsed], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps * 1e3
+    value = world * args.steps * k * f_vec / elapsed / 1e12
+
+    # roofline of the tensor-core GEMM (all its launches in the timed region)
+    tot_ms = float(prof[:, 1].sum())
+    tot_launch = float(prof[:, 0].sum())
+    alg = float(prof[:, 2].sum())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("bf16_tflops_sustained")
+    peak_src = "of measured (sustained bf16)"
+    if peak is None:
+        peak, peak_src = 1700.0, "of fallback (sustained bf16)"
+    achieved = alg / (tot_ms * 1e-3) / 1e12 if tot_ms > 0 else 0.0
+    names = ["stage1 (T = L Zt)", "stage2 (O += T L)"]
+    per_stage = {names[i]: {"launches": int(prof[i, 0]), "ms": float(prof[i, 1]),
+                            "alg_tflops": float(prof[i, 2]) / (prof[i, 1] * 1e-3) / 1e12
+                            if prof[i, 1] > 0 else None} for i in range(2)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"{spec.name}: nbasis={spec.nbasis} nocc={spec.nocc} "
+                               f"nocc_act={spec.nocc_act} nvir_act={spec.nvir_act} naux={spec.naux}; "
+                               f"one step = sigma of a {k}-vector singlet Davidson block "
+                               "(BF16 tensor-core sandwich, FP32 accumulation, FP64 in/out)",
+                   "flops_per_vector": f_vec,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (BF16 L "
+                         f"{spec.naux * (spec.n_act + 8) ** 2 * 2 / 1e9:.1f} GB, T "
+                         f"{spec.naux * (spec.n_act + 8) ** 2 * k * 2 / 1e9:.0f} GB)"},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "ao2mo_fp64_ms": ao2mo_ms,
+        "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel<1> (sigma sandwich, both stages)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "peak_source": peak_src,
+                     "traffic": None, "launches_per_step": tot_launch / args.steps,
+                     "avg_launch_ms": tot_ms / tot_launch if tot_launch else None,
+                     "per_stage": per_stage},
+    }
+
+    if rank == 0:
+        # ---- end to end through the C ABI with host buffers (z in, sigma out) ----
+        zh = torch.from_numpy(z).pin_memory()
+        sh = torch.empty_like(zh).pin_memory()
+        for _ in range(1):
+            c.sigma(1, zh, pp.PREC_BF16, out=sh)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            c.sigma(1, zh, pp.PREC_BF16, out=sh)
+            chk = float(sh[0, 0])  # the result is on the host
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        out["e2e"] = {"value": k * f_vec / e2e_s / 1e12, "unit": "TFLOP/s",
+                      "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(z.nbytes),
+                      "path": "pprpa_sigma with pinned host z and sigma (copies inside the call)"}
+        if not args.no_extra:
+            # ---- the same block through the BF16x3 split form and the FP64 form ----
+            c.sigma(1, zd, pp.PREC_BF16_SPLIT, out=sd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.sigma(1, zd, pp.PREC_BF16_SPLIT, out=sd)
+            torch.cuda.synchronize()
+            t_split = time.perf_counter() - t0
+            s_split = sd.cpu().numpy()
+            c.sigma(1, zd, pp.PREC_BF16, out=sd)
+            s_bf16 = sd.cpu().numpy()
+            z1 = zd[:1].contiguous()
+            s1 = torch.empty_like(z1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.sigma(1, z1, pp.PREC_FP64, out=s1)
+            torch.cuda.synchronize()
+            t64 = time.perf_counter() - t0
+            s64 = s1.cpu().numpy()[0]
+            ref = np.abs(s64).max()
+            out["precision_forms"] = {
+                "bf16x3_split_tflops": k * f_vec / t_split / 1e12,
+                "fp64_tflops": f_vec / t64 / 1e12,
+                "fp64_ms_per_vector": t64 * 1e3,
+                "max_rel_err_vs_fp64": {"bf16": float(np.abs(s_bf16[0] - s64).max() / ref),
+                                        "bf16x3_split": float(np.abs(s_split[0] - s64).max() / ref)},
+            }
+            out["solve_small"] = small_solve(pp, torch, lib_stream)
+        # ---- CPU oracle baseline (bounded sample) ----
+        if world == 1:
+            t_sig, sample = cpu_sample(spec, args.cpu_frac)
+            out["cpu_baseline"] = {"value": f_vec / t_sig / 1e12, "unit": "TFLOP/s",
+                                   "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+        print(json.dumps(out), flush=True)
+    c.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

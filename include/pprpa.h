@@ -180,7 +180,17 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
  * be NULL.  Host or device per `where`. */
 int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
 
-/* ---- diagnostics ---------------------------------------------------------- */
+/* ---- diagnostics ----------------------------------------------------------
+ * pprpa_profile: CUDA-event timing of every tensor-core sigma GEMM launch,
+ * recorded on the context's stream.  enable = 1 clears the records and
+ * starts recording, 0 stops.  `out` (host, nullable) receives 4 rows of
+ * {launches, total_ms, algorithmic_flops}: stage 1 BF16, stage 2 BF16,
+ * stage 1 BF16x3, stage 2 BF16x3.  algorithmic_flops counts the sigma work
+ * 3*naux*n*(nv^2+no^2) per vector split as 2/3 (stage 1) and 1/3 (stage 2),
+ * independent of padding and of the number of split products.  Reading
+ * synchronises the context's stream. */
+int pprpa_profile(pprpa_ctx* ctx, int enable, double* out);
+
 const char* pprpa_strerror(int code);
 const char* pprpa_last_error(void);
 /* Number of kernels this library has launched on the calling process. */

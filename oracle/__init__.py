@@ -27,6 +27,7 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
 from .pprpa_ref import (  # noqa: F401
     active_orbitals,
     ao_to_mo,
+    ao_to_mo_rows,
     pair_list,
     eri_phys,
     build_matrix,

@@ -75,23 +75,28 @@ def ri_sigma(eps_act, nocc_act, L_act, mult, Z):
     return d[None, :] * Z + two_e
 
 
-def ri_sigma_rows(eps_act, nocc_act, L_act, mult, z, rows):
+def ri_sigma_rows(eps_act, nocc_act, L_act, mult, z, rows, Lrow=None):
     """Selected components sigma_I = sum_J M_IJ z_J, one row at a time.
 
     Each row I = (p, q) of M is formed from its definition (Sec. ppRPA
     Equation): the needed <pq|rs> = sum_P L^P_pr L^P_qs for all r, s is one
     product of the P-columns of orbitals p and q.  Used to check sampled
-    outputs at sizes where the full matrix does not fit.
+    outputs at sizes where the full matrix does not fit.  ``Lrow(p)`` may
+    supply L^P_{p, :} as an (naux, n) array instead of ``L_act``.
     """
     eps = np.asarray(eps_act, dtype=np.float64)
-    L = np.asarray(L_act, dtype=np.float64)
+    if Lrow is None:
+        L = np.asarray(L_act, dtype=np.float64)
+
+        def Lrow(p):
+            return L[:, p, :]
     n = eps.shape[0]
     P1, P2, nvv, noo = _pairs_all(n, nocc_act, mult)
     w = np.concatenate([np.ones(nvv), -np.ones(noo)])
     out = np.zeros(len(rows))
     for t, I in enumerate(rows):
         a, b = P1[I], P2[I]
-        V = L[:, a, :].T @ L[:, b, :]  # V[r, s] = <ab|rs>
+        V = Lrow(a).T @ Lrow(b)  # V[r, s] = <ab|rs>
         direct = V[P1, P2]
         exch = V[P2, P1]
         if mult == 1:
@@ -138,6 +143,7 @@ def davidson(sigma_fn, diag, nvv, noo, nroots, tol=1e-6, max_iter=200, max_space
     n_sigma = nguess
     omega = None
     resid = None
+    Zr = None
     for it in range(1, max_iter + 1):
         G = V.T @ Sig
         G = 0.5 * (G + G.T)
@@ -191,5 +197,5 @@ def davidson(sigma_fn, diag, nvv, noo, nroots, tol=1e-6, max_iter=200, max_space
         n_sigma += Vn.shape[1]
         V = np.hstack([V, Vn])
         Sig = np.hstack([Sig, Sn])
-    return {"omega": omega, "z": V @ Ct if omega is not None else None, "resid": resid,
+    return {"omega": omega, "z": Zr if omega is not None else None, "resid": resid,
             "iters": max_iter, "n_sigma": n_sigma, "converged": False}

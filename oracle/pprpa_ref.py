@@ -41,6 +41,25 @@ def ao_to_mo(ao3c, C, orb):
     return np.einsum("Pmn,mp,nq->Ppq", ao3c, ca, ca, optimize=True)
 
 
+def ao_to_mo_rows(ao3c, C, orb, rows):
+    """L^P_{p q} for p in ``rows`` (indices into ``orb``) and all q in ``orb``.
+
+    The same transform as :func:`ao_to_mo`, restricted to a few rows, for
+    checking sampled outputs of workloads whose full L does not fit.
+    Returns an array (len(rows), naux, n).
+    """
+    ca = np.asarray(C, dtype=np.float64)[:, orb]
+    half = np.einsum("Pmn,nq->Pmq", ao3c, ca, optimize=True) if len(rows) > 8 else None
+    out = []
+    for r in rows:
+        cr = ca[:, r]
+        if half is not None:
+            out.append(np.einsum("m,Pmq->Pq", cr, half))
+        else:
+            out.append(np.einsum("Pmn,m->Pn", ao3c, cr) @ ca)
+    return np.array(out)
+
+
 def pair_list(n, mult):
     """Pair indices in row-major upper-triangle order.
 

@@ -88,6 +88,7 @@ SIGNATURES = {
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
+    "pprpa_profile": (_I, [_P, _I, _P]),
 }
 
 _lib = None
@@ -254,6 +255,14 @@ class Context:
             _check(rc)
         return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
                 "info": info.as_dict(), "rc": rc}
+
+    def profile(self, enable=None):
+        """Read the tensor-core GEMM timing records (4 x {launches, ms, flops});
+        enable=True/False clears and starts/stops recording after the read."""
+        out = np.zeros(12)
+        _check(self.lib.pprpa_profile(self._h, -1 if enable is None else int(bool(enable)),
+                                      out.ctypes.data))
+        return out.reshape(4, 3)
 
     def grad(self, root, dL=None, deps=None):
         n, naux, _, _ = self.dims(1)

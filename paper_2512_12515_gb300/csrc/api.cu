@@ -161,6 +161,10 @@ void pprpa_destroy(pprpa_ctx* c) {
     }
     for (auto& kv : c->ws)
         if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& r : c->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -434,6 +438,30 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
         }
     }
     PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
+int pprpa_profile(pprpa_ctx* c, int enable, double* out) {
+    PP_TRY(check_ctx(c));
+    if (out) {
+        PP_CUDA(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < 12; ++i) out[i] = 0.0;
+        for (auto& r : c->prof) {
+            float ms = 0.f;
+            PP_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+            out[3 * r.kind + 0] += 1.0;
+            out[3 * r.kind + 1] += ms;
+            out[3 * r.kind + 2] += r.flops;
+        }
+    }
+    if (enable >= 0) {
+        for (auto& r : c->prof) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        c->prof.clear();
+        c->profile = enable != 0;
+    }
     return PPRPA_OK;
 }
 

@@ -16,6 +16,12 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+struct ProfRec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;        // 0 s1 bf16, 1 s2 bf16, 2 s1 split, 3 s2 split
+    double flops = 0.0;  // algorithmic sigma flops of the launch
+};
+
 struct PairTable {
     int nvv = 0, noo = 0, N = 0;
     std::vector<int> pp, pq;
@@ -51,6 +57,10 @@ struct pprpa_ctx {
     int* d_status = nullptr;
     std::map<std::string, pprpa::DevBuf> ws;  // grow-only named workspaces
     std::map<std::string, int> tuned_bn;      // autotuned N tile per problem key
+
+    // per-launch profiling of the tensor-core GEMMs
+    bool profile = false;
+    std::vector<pprpa::ProfRec> prof;
 
     // last solve (for gradients)
     int last_mult = 0;

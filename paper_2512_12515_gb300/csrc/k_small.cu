@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     if (tid == 0) a.info[0] = DEV_NOTPD;
     // scale for the pivot test
     double sc = 0.0;
-    for (int i = tid; i < m; i += nt) sc = fmax(sc, fabs(a.G[i * ld + i]) + fabs(a.S[i * ld + i]));
+    for (int i = tid; i < m; i += nt)
+        sc = fmax(sc, fabs(a.G[i * ld + i] + (a.Go ? a.Go[i * ld + i] : 0.0)) + fabs(a.S[i * ld + i]));
     for (int o = 16; o > 0; o >>= 1) sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, o));
     if ((tid & 31) == 0) red[tid >> 5] = sc;
     __syncthreads();
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         // K = sym(G) - mu S (S symmetric: read the upper triangle)
         for (int t = tid; t < m * m; t += nt) {
             const int i = t / m, j = t % m;
-            const double g = 0.5 * (a.G[i * ld + j] + a.G[j * ld + i]);
+            double g = 0.5 * (a.G[i * ld + j] + a.G[j * ld + i]);
+            if (a.Go) g += 0.5 * (a.Go[i * ld + j] + a.Go[j * ld + i]);
             const double s = (i <= j) ? a.S[i * ld + j] : a.S[j * ld + i];
             Kc[i * lw + j] = g - mu * s;
         }

@@ -81,7 +81,8 @@ int launch_grad_eps(const double* z, int N, int nvv, const int* pp, const int* p
 // ---------------------------------------------------------------------------
 // One-CTA dense FP64 linear algebra (Rayleigh-Ritz, block orthonormalisation).
 struct RRArgs {
-    const double* G = nullptr;  // m x m (ld), symmetrised inside
+    const double* G = nullptr;   // m x m (ld): V^T M V restricted to virtual pairs (or all of M)
+    const double* Go = nullptr;  // optional m x m (ld): occupied-pair part; G + Go is symmetrised
     const double* S = nullptr;  // m x m (ld), upper block valid
     int ld = 0, m = 0;
     const double* mus = nullptr;  // device: candidate shifts
@@ -95,6 +96,25 @@ struct RRArgs {
                                // [4]=omega_max_hh, [5]=sweeps
 };
 int launch_rayleigh_ritz(const RRArgs& a, cudaStream_t st);
+
+// General Rayleigh-Ritz for an indefinite pencil: G c = theta S c with G = Gv + Go = V^T M V,
+// solved as X = S^-1 G; keeps the lowest real roots of positive norm c^T S c, normalised to
+// c^T S c = 1.
+struct RRGenArgs {
+    const double* Gv = nullptr;  // m x m (ld): rows V (virtual-pair part) . M V
+    const double* Go = nullptr;  // m x m (ld): occupied-pair part
+    const double* S = nullptr;   // m x m (ld), upper triangle valid
+    int ld = 0, m = 0;
+    int nwant = 0, nkeep = 0;
+    double imag_tol = 1e-9;   // |Im theta| <= imag_tol * max|theta| counts as real
+    double norm_tol = 1e-8;   // |c^T S c| below this (for |c| = 1) is not classified
+    double* work = nullptr;   // >= 3*m*m + m doubles
+    double* omega = nullptr;  // nkeep
+    double* coef = nullptr;   // nkeep x m
+    double* info = nullptr;   // [0] status, [2] kept, [3] lowest kept, [4] highest negative-norm
+                              // seen, [5] real count, [6] lowest complex real part, [7] max |Im|
+};
+int launch_rr_general(const RRGenArgs& a, cudaStream_t st);
 
 // Block orthonormalisation of k rows: given Gram Gm (k x k), returns T (k x k) with
 // T * X orthonormal rows; rows whose residual pivot is below tol are zeroed and flagged

@@ -12,6 +12,8 @@
 
 namespace pprpa {
 
+static int env_int(const char* name, int dflt);
+
 int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out) {
     DevBuf& b = c->ws[name];
     if (b.bytes < bytes) {
@@ -54,9 +56,10 @@ int sigma_f64(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma)
     double *Zt, *O, *T;
     PP_TRY(ws_get(c, "f64_Zt", sizeof(double) * n2 * k, (void**)&Zt));
     PP_TRY(ws_get(c, "f64_O", sizeof(double) * n2 * k, (void**)&O));
-    // chunk of P such that T = [pc][k][n][n] stays within ~4 GB
+    // chunk of P such that T = [pc][k][n][n] stays within the budget (default 4 GB)
     const int64_t per_p = sizeof(double) * n2 * k;
-    int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (4LL << 30) / per_p));
+    const int64_t budget = (int64_t)env_int("PPRPA_F64_CHUNK_MB", 4096) << 20;
+    int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, budget / per_p));
     PP_TRY(ws_get(c, "f64_T", per_p * pc, (void**)&T));
     PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2 * k, st));
     PP_TRY(launch_unpack_f64(d_z, k, pt->N, pt->d_pp, pt->d_pq, n, mult, Zt, st));
@@ -123,17 +126,38 @@ static std::vector<int2> triangle_tiles(int valid, int BN) {
     return t;
 }
 
-// N tile of the second stage: the multiple of 16 (<= 256) that wastes the least
-// padding over the block, larger on ties.  The autotuner may override it.
+// N tile of the second stage: tensor-core efficiency needs wide tiles, so among the
+// multiples of 16 in [64, 256] (or up to the block when it is narrower) take the one
+// that pads the block least, the wider one on ties.  The autotuner may override it.
 int stage2_bn(int valid) {
-    int best = 16;
-    int64_t best_waste = INT64_MAX;
-    for (int bn = 16; bn <= 256; bn += 16) {
-        const int64_t waste = ceil_div(valid, bn) * bn - valid;
-        const int64_t w = waste * 1000 + (256 - bn);  // prefer larger tiles on ties
-        if (w < best_waste) { best_waste = w; best = bn; }
+    const int lo = valid >= 64 ? 64 : 16;
+    int best = 256, best_pad = INT32_MAX;
+    for (int bn = 256; bn >= lo; bn -= 16) {
+        const int pad = (int)(ceil_div(valid, bn) * bn) - valid;
+        if (pad < best_pad) { best_pad = pad; best = bn; }
     }
     return best;
+}
+
+// Launch with optional event timing (pprpa_profile).
+static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap& a_hi,
+                        const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
+                        const TcParams& p, int nterms) {
+    ProfRec r;
+    const bool rec = c->profile && c->prof.size() < 200000;
+    if (rec) {
+        r.kind = kind;
+        r.flops = flops;
+        PP_CUDA(cudaEventCreate(&r.a));
+        PP_CUDA(cudaEventCreate(&r.b));
+        PP_CUDA(cudaEventRecord(r.a, c->stream));
+    }
+    PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
+    if (rec) {
+        PP_CUDA(cudaEventRecord(r.b, c->stream));
+        c->prof.push_back(r);
+    }
+    return PPRPA_OK;
 }
 
 static int env_int(const char* name, int dflt) {
@@ -172,7 +196,7 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
                               st));
     // intermediate T [pc][n_pad][k][n_pad] (hi, lo) and output O [k][n_pad][n_pad] FP32
     const int64_t per_p = (int64_t)sizeof(__nv_bfloat16) * np * k * np;
-    const int64_t budget = (int64_t)env_int("PPRPA_T_BUDGET_MB", 40 * 1024) << 20;
+    const int64_t budget = (int64_t)env_int("PPRPA_T_BUDGET_MB", 64 * 1024) << 20;
     int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, budget / (per_p * (split ? 2 : 1))));
     __nv_bfloat16 *t_hi, *t_lo = nullptr;
     {
@@ -231,7 +255,8 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
             const int64_t items = ceil_div(p.M_rows, 128) * p.tiles_n;
             if (items > INT32_MAX) return set_error(PPRPA_ERR_ARG, "sigma: too many stage-1 tiles");
             p.total_items = (int)items;
-            PP_TRY(tc_gemm_launch(ta_hi, ta_lo, tb_hi, tb_lo, p, nterms, c->num_sms, st));
+            const double fl = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
+            PP_TRY(timed_launch(c, split ? 2 : 0, fl, ta_hi, ta_lo, tb_hi, tb_lo, p, nterms));
         }
         // ---------------- stage 2 ----------------
         for (int blk = 0; blk < 2; ++blk) {
@@ -267,10 +292,15 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
             p.nbatch = k;
             p.kq_blocks = (int)ceil_div(np, 64);
             p.kb_total = npc * p.kq_blocks;
-            // enough K slices for about four waves of work items
+            // enough K slices for about four waves of work items; in the split form also
+            // at most pcap auxiliary slices per accumulator, because the tensor-core FP32
+            // accumulation loses accuracy over very long reductions (partial sums of the
+            // slices are added in FP32 in L2)
             const int64_t base_items = (int64_t)p.ntiles * k;
             int64_t ns = ceil_div(4LL * c->num_sms, base_items);
             ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max(1, p.kb_total / 8)));
+            const int pcap = env_int(split ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", split ? 2 : 128);
+            if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
             // every K slice non-empty: recompute the count from the slice length
             const int64_t per = ceil_div(p.kb_total, ns);
             p.nsplit = (int)ceil_div(p.kb_total, per);
@@ -281,7 +311,8 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
             p.n_pad = (int)np;
             p.O = O;
             p.total_items = (int)(base_items * p.nsplit);
-            PP_TRY(tc_gemm_launch(ta_hi, ta_lo, tb_hi, tb_lo, p, nterms, c->num_sms, st));
+            const double fl = 1.0 * npc * (double)(no + nv) * (double)sz * sz * k;
+            PP_TRY(timed_launch(c, split ? 3 : 1, fl, ta_hi, ta_lo, tb_hi, tb_lo, p, nterms));
         }
     }
     PP_TRY(launch_pack_f32(O, d_z, k, pt->N, pt->nvv, pt->d_pp, pt->d_pq, pm, c->d_eps, mult,

@@ -231,11 +231,14 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     const int nroots = o->nroots;
     cudaStream_t st = c->stream;
     const int nguess = std::min(nvv, std::max(2 * nroots, nroots + 8));
-    int m_max = o->max_subspace > 0 ? o->max_subspace : std::max(8 * nroots, nguess + 4 * nroots);
+    // subspace cap and thick-restart size: unstable problems (complex pairs near the
+    // targets) need a restart that keeps many Ritz vectors, so both are generous
+    int m_max = o->max_subspace > 0 ? o->max_subspace : 128;
     m_max = std::min(m_max, 128);
     m_max = std::min(m_max, N);
     if (m_max < nguess + 1 && N > nguess) m_max = std::min(N, nguess + 1);
-    const int nkeep = std::min(nguess, m_max - 1 > 0 ? m_max - 1 : 1);
+    int nkeep = std::max(nguess, std::max(4 * nroots, 40));
+    nkeep = std::min(nkeep, std::max(1, m_max - std::max(nroots, 8)));
     const int max_new = nroots;
     Timer t_all(st), t_sig(st);
     t_all.start();
@@ -246,6 +249,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(ws_get(c, "dv_V", sizeof(double) * (size_t)m_max * N, (void**)&V));
     PP_TRY(ws_get(c, "dv_Sg", sizeof(double) * (size_t)m_max * N, (void**)&Sg));
     PP_TRY(ws_get(c, "dv_G", sizeof(double) * m_max * m_max, (void**)&G));
+    double* Go;
+    PP_TRY(ws_get(c, "dv_Go", sizeof(double) * m_max * m_max, (void**)&Go));
     PP_TRY(ws_get(c, "dv_S", sizeof(double) * m_max * m_max, (void**)&S));
     PP_TRY(ws_get(c, "dv_D", sizeof(double) * N, (void**)&D));
     PP_TRY(ws_get(c, "dv_dwork", sizeof(double) * (size_t)c->naux * c->n(), (void**)&dwork));
@@ -304,9 +309,13 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     };
     auto project_block = [&](int m0, int m) -> int {
         const int kn = m - m0;
-        // G[0:m, m0:m] and G[m0:m, 0:m0]
-        PP_TRY(dots(V, N, m, Sg + (size_t)m0 * N, N, kn, N, G + m0, m_max, 1.0, true, st));
-        PP_TRY(dots(V + (size_t)m0 * N, N, kn, Sg, N, m0, N, G + (size_t)m0 * m_max, m_max, 1.0, true, st));
+        // G = V_vv Sg_vv^T (virtual pairs) and Go = V_oo Sg_oo^T (occupied pairs), blocks
+        // [0:m, m0:m] and [m0:m, 0:m0]; V^T M V = G + Go and V^T W M V = G - Go.
+        PP_TRY(dots(V, N, m, Sg + (size_t)m0 * N, N, kn, nvv, G + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + (size_t)m0 * N, N, kn, Sg, N, m0, nvv, G + (size_t)m0 * m_max, m_max, 1.0, true, st));
+        PP_TRY(dots(V + nvv, N, m, Sg + (size_t)m0 * N + nvv, N, kn, noo, Go + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + (size_t)m0 * N + nvv, N, kn, Sg + nvv, N, m0, noo, Go + (size_t)m0 * m_max, m_max, 1.0,
+                    true, st));
         // S[0:m, m0:m] = V W V^T (virtual pairs +, occupied pairs -)
         PP_TRY(dots(V, N, m, V + (size_t)m0 * N, N, kn, nvv, S + m0, m_max, 1.0, true, st));
         PP_TRY(dots(V + nvv, N, m, V + (size_t)m0 * N + nvv, N, kn, noo, S + m0, m_max, -1.0, false, st));
@@ -333,6 +342,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(project_block(0, m));
     double mu_prev = 0.0;
     bool have_mu = false;
+    bool general = false;
+    double max_imag_below = 0.0;
     double lo_est = oo_max, hi_est = dv_min;
     if (noo == 0) lo_est = dv_min - 1.0;
     std::vector<double> h_om(m_max), h_nrm(nroots), best_hist;
@@ -340,47 +351,73 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     int it = 0, stage1_iters = 0;
     double hinfo[8] = {0};
     for (it = 1; it <= o->max_iter; ++it) {
-        // ---- Rayleigh-Ritz ----
-        std::vector<double> cand = shift_candidates(lo_est, hi_est, mu_prev, have_mu);
-        for (int t = 1; t <= 4 && cand.size() < 32; ++t) {
-            cand.push_back(lo_est - 0.5 * t);
-            cand.push_back(hi_est - 0.05 * t);
+        // ---- Rayleigh-Ritz: shifted symmetric reduction while the pencil is definite,
+        //      general (non-symmetric) projection once it is not ----
+        const int nk_req = std::max(nkeep, nroots);
+        int npos = 0;
+        if (!general) {
+            std::vector<double> cand = shift_candidates(lo_est, hi_est, mu_prev, have_mu);
+            for (int t = 1; t <= 4 && cand.size() < 32; ++t) {
+                cand.push_back(lo_est - 0.5 * t);
+                cand.push_back(hi_est - 0.05 * t);
+            }
+            cand.resize(std::min<size_t>(cand.size(), 32));
+            PP_CUDA(cudaMemcpyAsync(mus, cand.data(), sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
+            RRArgs a;
+            a.G = G; a.Go = Go; a.S = S; a.ld = m_max; a.m = m;
+            a.mus = mus; a.nmu = (int)cand.size();
+            a.nwant = nroots; a.nkeep = nk_req;
+            a.work = rwork; a.omega = om; a.coef = coef; a.info = rinfo;
+            PP_TRY(launch_rayleigh_ritz(a, st));
+            PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaStreamSynchronize(st));
+            if ((int)hinfo[0] == DEV_NOTPD) {
+                if (m > 128) return set_error(PPRPA_ERR_UNSTABLE, "Davidson: no definite shift and subspace > 128");
+                general = true;
+                if (env_int("PPRPA_LOG", 0)) fprintf(stderr, "[pprpa] no definite shift: general Rayleigh-Ritz\n");
+            } else {
+                npos = (int)hinfo[2];
+                mu_prev = hinfo[1];
+                have_mu = true;
+                hi_est = hinfo[3];
+                if (hinfo[4] > -1e299) lo_est = hinfo[4];
+            }
         }
-        cand.resize(std::min<size_t>(cand.size(), 32));
-        PP_CUDA(cudaMemcpyAsync(mus, cand.data(), sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
-        RRArgs a;
-        a.G = G; a.S = S; a.ld = m_max; a.m = m;
-        a.mus = mus; a.nmu = (int)cand.size();
-        a.nwant = nroots; a.nkeep = std::max(nkeep, nroots);
-        a.work = rwork; a.omega = om; a.coef = coef; a.info = rinfo;
-        PP_TRY(launch_rayleigh_ritz(a, st));
-        PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
-        PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * a.nkeep, cudaMemcpyDeviceToHost, st));
+        if (general) {
+            RRGenArgs g;
+            g.Gv = G; g.Go = Go; g.S = S; g.ld = m_max; g.m = m;
+            g.nwant = nroots; g.nkeep = nk_req;
+            g.work = rwork; g.omega = om; g.coef = coef; g.info = rinfo;
+            PP_TRY(launch_rr_general(g, st));
+            PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaStreamSynchronize(st));
+            if ((int)hinfo[0] == DEV_NOTPD)
+                return set_error(PPRPA_ERR_UNSTABLE, "Davidson: subspace eigenvalue iteration failed");
+            npos = (int)hinfo[2];
+        }
+        if (npos < 1)
+            return set_error(PPRPA_ERR_UNSTABLE, "Davidson: the subspace holds no real addition root");
+        const int ntg = std::min(npos, nroots);  // targets this iteration
+        PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * std::min(npos, nk_req), cudaMemcpyDeviceToHost, st));
         PP_CUDA(cudaStreamSynchronize(st));
-        if ((int)hinfo[0] == DEV_NOTPD)
-            return set_error(PPRPA_ERR_UNSTABLE, "Davidson: no shift makes the projected pencil definite");
-        const int npos = (int)hinfo[2];
-        if (npos < nroots)
-            return set_error(PPRPA_ERR_UNSTABLE, "Davidson: subspace holds fewer addition roots than requested");
-        mu_prev = hinfo[1];
-        have_mu = true;
-        hi_est = hinfo[3];
-        if (hinfo[4] > -1e299) lo_est = hinfo[4];
-        const int nk_avail = std::min(npos, a.nkeep);
+        const int nk_avail = std::min(npos, nk_req);
+        // complex Ritz values below the highest target: complex roots among the lowest
+        if (general) max_imag_below = (hinfo[6] < h_om[ntg - 1]) ? hinfo[7] : 0.0;
         // ---- Ritz vectors and residuals of the targets ----
-        PP_TRY(combine(coef, m, nroots, m, V, N, Zr, 1.0, 0.0, st));
-        PP_TRY(combine(coef, m, nroots, m, Sg, N, SZ, 1.0, 0.0, st));
-        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * nroots, st));
-        PP_TRY(launch_residual(SZ, Zr, om, nroots, N, nvv, R, nrm, st));
-        PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * nroots, cudaMemcpyDeviceToHost, st));
+        PP_TRY(combine(coef, m, ntg, m, V, N, Zr, 1.0, 0.0, st));
+        PP_TRY(combine(coef, m, ntg, m, Sg, N, SZ, 1.0, 0.0, st));
+        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * ntg, st));
+        PP_TRY(launch_residual(SZ, Zr, om, ntg, N, nvv, R, nrm, st));
+        PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * ntg, cudaMemcpyDeviceToHost, st));
         PP_CUDA(cudaStreamSynchronize(st));
         double rmax = 0.0;
         std::vector<int> todo;
-        for (int j = 0; j < nroots; ++j) {
+        for (int j = 0; j < ntg; ++j) {
             h_nrm[j] = std::sqrt(h_nrm[j]);
             rmax = std::max(rmax, h_nrm[j]);
             if (!(h_nrm[j] <= o->conv_tol)) todo.push_back(j);
         }
+        if (ntg < nroots) rmax = std::max(rmax, 1e300);  // not enough real roots yet
         if (env_int("PPRPA_LOG", 0))
             fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e\n", it, stage, m,
                     mu_prev, h_om[0], rmax);
@@ -400,9 +437,14 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
                 continue;
             }
         }
-        if (todo.empty()) {
+        if (todo.empty() && ntg == nroots) {
             rc_final = PPRPA_OK;
             break;
+        }
+        if (todo.empty()) {
+            // every current target converged but the subspace has too few real roots:
+            // expand along all targets
+            for (int j = 0; j < ntg; ++j) todo.push_back(j);
         }
         if (it == o->max_iter) break;
         // ---- correction vectors ----
@@ -472,7 +514,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         info->iters = std::min(it, o->max_iter);
         info->iters_stage1 = stage1_iters;
         info->converged = rc_final == PPRPA_OK;
-        info->mu = mu_prev;
+        info->mu = general ? 0.0 : mu_prev;
+        info->max_imag = max_imag_below;
         info->t_sigma_ms = t_sig.total_ms;
         info->t_total_ms = t_all.total_ms;
     }

@@ -187,3 +187,45 @@ def test_error_paths(pp):
             c.grad(0)
         r = c.solve(mult=1, nroots=2, max_iter=1, conv_tol=1e-14, raise_noconv=False)
         assert r["rc"] == -4
+
+
+UNSTABLE = [(4, 40, 12, 50, 1), (4, 48, 18, 56, 2)]
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("no,nv,naux,nb,seed", UNSTABLE)
+@pytest.mark.parametrize("prec,tol", [("PREC_FP64", 1e-8), ("PREC_BF16", 1e-5)])
+def test_davidson_unstable_problem(pp, mult, no, nv, naux, nb, seed, prec, tol):
+    """Synthetic problems whose removal roots have become complex: no shift makes
+    the pencil definite, the general subspace solver takes over, and the lowest
+    real roots of positive norm (here below every complex pair) are found."""
+    spec = synth.SystemSpec("u", nb, no + 2, naux, no, nv, seed)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], no, nv)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    eps = s["eps"][orb]
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    ref = oracle.solve_full(M, nvv, noo, imag_tol=1e-9)
+    assert ref["unstable"]
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    vals, vecs = np.linalg.eig(w[:, None] * M)
+    real = np.abs(vals.imag) < 1e-9
+    nrm = np.einsum("ik,i,ik->k", vecs.real, w, vecs.real)
+    pp_real = np.sort(vals.real[real & (nrm > 0)])
+    # targets: up to 5 lowest real addition roots lying below every complex pair
+    nr = int(min(5, np.count_nonzero(pp_real < vals.real[~real].min())))
+    assert nr >= 3
+    lowest = pp_real[:nr]
+    with gpu_ctx(pp, spec, s) as c:
+        res = c.solve(mult=mult, nroots=nr, precision=getattr(pp, prec),
+                      conv_tol=1e-7 if prec == "PREC_FP64" else 1e-5)
+        with pytest.raises(pp.PprpaError) as e:
+            c.solve(mult=mult, nroots=nr, method=pp.METHOD_FULL)
+        # no definite shift (unstable) or, beyond 1024 pairs, outside the full-diagonalisation range
+        assert e.value.code == (-5 if nvv + noo <= 1024 else -1)
+    assert res["info"]["converged"] == 1
+    assert res["info"]["max_imag"] == 0.0
+    assert np.abs(res["omega"] - lowest).max() <= tol
+    Z = np.hstack([res["X"], res["Y"]])
+    resid = Z @ M.T - res["omega"][:, None] * (w[None, :] * Z)
+    assert np.linalg.norm(resid, axis=1).max() <= (1e-6 if prec == "PREC_FP64" else 1e-4)

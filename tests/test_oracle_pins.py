@@ -285,3 +285,25 @@ def test_small_workload_matches_golden():
         assert np.allclose(sol["omega_pp"], ref["omega_pp"], atol=1e-10)
         assert np.allclose(sol["omega_hh"], ref["omega_hh"], atol=1e-10)
         assert abs(oracle.correlation_energy(M, nvv, noo, sol)[0] - ref["ec"]) < 1e-10
+
+
+def test_ao_to_mo_rows_matches_full_transform():
+    spec = synth.SystemSpec("t", 14, 4, 9, 3, 7, 4)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], 3, 7)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    for rows in ([0, 4, 9], list(range(10))):
+        got = oracle.ao_to_mo_rows(s["ao3c"], s["C"], orb, rows)
+        assert np.allclose(got, L[:, rows, :].transpose(1, 0, 2), atol=1e-14)
+    eps = s["eps"][orb]
+    M, nvv, noo = oracle.build_matrix(eps, 3, L, 1)
+    z = synth.random_trial_vectors(nvv + noo, 1, 2)[0]
+    rows_cache = {}
+
+    def Lrow(p):
+        if p not in rows_cache:
+            rows_cache[p] = oracle.ao_to_mo_rows(s["ao3c"], s["C"], orb, [p])[0]
+        return rows_cache[p]
+
+    got = oracle.ri_sigma_rows(eps, 3, None, 1, z, [0, 5, nvv + 1], Lrow=Lrow)
+    assert np.allclose(got, (M @ z)[[0, 5, nvv + 1]], atol=1e-13)
