@@ -161,6 +161,26 @@ int pprpa_sigma(pprpa_ctx* ctx, int mult, int precision, int k, const double* z,
  * the fitted integrals (Sec. "ppRPA Equation", spin-adapted elements). */
 int pprpa_build_matrix(pprpa_ctx* ctx, int mult, double* M, int where);
 
+/* pprpa_sigma_noalloc: the FP64 sigma of pprpa_sigma (precision PPRPA_PREC_FP64) for callers
+ * that cannot allocate device memory, e.g. code running inside another framework's
+ * fixed-budget memory pool, latency-critical loops that cannot afford the device
+ * synchronisation of cudaMalloc/cudaFree, or plugins whose host forbids allocation in its
+ * callbacks.  The paper has no counterpart: this is a deployment variant of the same
+ * contraction.  It needs no context and allocates nothing; every argument is a DEVICE
+ * pointer on the current device: L[naux][n][n] active-space fitted integrals (occupied
+ * orbitals first, n = nocc_act + nvir_act), eps[n] active orbital energies, z[k][N] trial
+ * vectors, sigma[k][N] output (pair order of this header).  Intermediates live in one
+ * 64 MiB file-scope device array, so the call is limited to 3*k*n^2*8 + 8*N + ~1 KB bytes
+ * of intermediates and returns PPRPA_ERR_ARG beyond that (use pprpa_sigma).  The first call
+ * on a device looks up that array's device address; make that first call before any stream
+ * capture.  Work is enqueued on `cuda_stream` (NULL = default stream) and the call returns
+ * without waiting for it.  All calls share the array and it keeps the last call's contents
+ * (the call clears what must start at zero): calls whose work overlaps on the GPU race, so
+ * keep them on one stream or serialise them. */
+int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int naux, const double* L,
+                        const double* eps, int k, const double* z, double* sigma,
+                        void* cuda_stream);
+
 /* ---- solve -----------------------------------------------------------------
  * pprpa_solve: lowest opts->nroots two-electron addition roots.
  * omega[nroots] ascending; X[nroots][nvv] and Y[nroots][noo] (either may be

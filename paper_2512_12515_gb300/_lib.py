@@ -89,6 +89,7 @@ SIGNATURES = {
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
     "pprpa_profile": (_I, [_P, _I, _P]),
+    "pprpa_sigma_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P, _P, _P]),
 }
 
 _lib = None
@@ -136,6 +137,23 @@ def _ptr(a, writable=False):
             raise TypeError("tensors must be contiguous float64")
         return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def sigma_noalloc(mult, nocc_act, nvir_act, L, eps, z, out, stream=None):
+    """FP64 sigma without any device allocation (pprpa_sigma_noalloc).
+
+    For callers that cannot allocate device memory; all arrays are CUDA float64
+    tensors on the current device and the work is only enqueued on ``stream``.
+    """
+    for a in (L, eps, z, out):
+        p, w = _ptr(a)
+        if w != DEVICE:
+            raise TypeError("sigma_noalloc takes device tensors only")
+    k = z.shape[0] if z.ndim == 2 else 1
+    _check(load().pprpa_sigma_noalloc(int(mult), int(nocc_act), int(nvir_act), int(L.shape[0]),
+                                      L.data_ptr(), eps.data_ptr(), k, z.data_ptr(),
+                                      out.data_ptr(), stream))
+    return out
 
 
 def kernel_launches() -> int:
