@@ -181,6 +181,47 @@ def small_solve(pp, torch, stream):
     return out
 
 
+def batch_bench(pp, torch, stream, nmol, nvec, steps, warmup):
+    """The 64-molecule batch workload: molecule m draws nocc ~ U{5..40}, nvir ~ U{50..400}
+    (all active), naux = 3 nbasis, singlet if m is even; one step = one batched BF16
+    sigma of nvec vectors per molecule (one persistent launch per stage, CUDA graph)."""
+    ctxs, zs, outs, mults = [], [], [], []
+    flops = 0.0
+    t0 = time.perf_counter()
+    for m in range(nmol):
+        spec, rng, mult = synth.batch_molecule_spec(m)
+        s = synth.make_system(spec, rng=rng)
+        c = pp.Context(0, stream=stream.cuda_stream)
+        c.set_orbitals(s["occ"], s["eps"])
+        c.set_ao(s["C"], s["ao3c"])
+        del s
+        _, _, nvv, noo = c.dims(mult)
+        z = synth.random_trial_vectors(nvv + noo, nvec, m)
+        zs.append(torch.from_numpy(z).cuda())
+        outs.append(torch.empty_like(zs[-1]))
+        ctxs.append(c)
+        mults.append(mult)
+        flops += nvec * 3.0 * spec.naux * spec.n_act * (spec.nvir_act ** 2 + spec.nocc_act ** 2)
+    setup_s = time.perf_counter() - t0
+    tiles = [c.autotune(m_, nvec, pp.PREC_BF16) for c, m_ in zip(ctxs[:4], mults[:4])]
+    for _ in range(warmup):
+        pp._lib.sigma_batch(ctxs, mults, zs, outs, pp.PREC_BF16, graph=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        pp._lib.sigma_batch(ctxs, mults, zs, outs, pp.PREC_BF16, graph=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / steps
+    for c in ctxs:
+        c.close()
+    return {"molecules": nmol, "vectors_per_molecule": nvec, "alg_flops_per_step": flops,
+            "ms_per_step": dt * 1e3, "tflops": flops / dt / 1e12, "setup_s": setup_s,
+            "autotuned_tiles_first4": tiles}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,6 +233,8 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / solve side measurements")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--batch-molecules", type=int, default=0,
+                    help="also time the batched multi-molecule sigma over this many molecules")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -352,6 +395,8 @@ def main():
                                         "bf16x3_split": float(np.abs(s_split[0] - s64).max() / ref)},
             }
             out["solve_small"] = small_solve(pp, torch, lib_stream)
+        if args.batch_molecules:
+            out["batch"] = batch_bench(pp, torch, lib_stream, args.batch_molecules, 8, 5, 2)
         # ---- CPU oracle baseline (bounded sample) ----
         if world == 1:
             t_sig, sample = cpu_sample(spec, args.cpu_frac)

@@ -157,6 +157,24 @@ int pprpa_diag(pprpa_ctx* ctx, int mult, double* out, int where);
 int pprpa_sigma(pprpa_ctx* ctx, int mult, int precision, int k, const double* z,
                 double* sigma, int where);
 
+/* pprpa_sigma_batch: sigma for many molecules at once (each its own context with its own
+ * integrals; all on one device).  Molecule m applies its matrix (multiplicity mults[m]) to
+ * ks[m] vectors z[m] -> sigma[m] (DEVICE pointers, layout of pprpa_sigma).  All stage-1
+ * products of every molecule run in one persistent tensor-core launch and all stage-2
+ * products in a second one; flags & 1 captures the device work in a CUDA graph that is
+ * replayed while the arguments (pointers and sizes) stay the same.  Runs on ctxs[0]'s
+ * stream; returns after the work completes.  precision: PPRPA_PREC_BF16 or
+ * PPRPA_PREC_BF16 + 16.  The tile widths are each context's autotuned ones (pprpa_autotune)
+ * or the model's choice. */
+int pprpa_sigma_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
+                      const double* const* z, double* const* sigma, int precision, int flags);
+
+/* pprpa_autotune: time the candidate tensor-core tile widths of both sigma stages on this
+ * context's problem (multiplicity mult, k vectors) and keep the fastest for later sigma
+ * calls.  tiles (nullable, host int[4]) receives the chosen widths: stage 1 virtual,
+ * stage 1 occupied, stage 2 virtual, stage 2 occupied (0 = block empty). */
+int pprpa_autotune(pprpa_ctx* ctx, int mult, int k, int precision, int* tiles);
+
 /* pprpa_build_matrix: explicit M = [[A, B], [B^T, C]] (N x N, FP64) from
  * the fitted integrals (Sec. "ppRPA Equation", spin-adapted elements). */
 int pprpa_build_matrix(pprpa_ctx* ctx, int mult, double* M, int where);
@@ -199,6 +217,14 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
  * (active orbitals).  Computed in FP64 on the device.  Either output may
  * be NULL.  Host or device per `where`. */
 int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
+
+/* pprpa_grad_vector: the same Hellmann-Feynman contraction for an explicit pair vector
+ * z[N] of multiplicity `mult` (Sec. "Analytic Gradient": d(z^T M z)/d theta = z^T (dM/d theta) z),
+ * i.e. the gradient of the Rayleigh quotient at fixed z; for a converged root normalised to
+ * z^T W z = 1 it is d omega / d theta.  z, dL[naux][n][n] and deps[n] are host or device per
+ * `where`; either output may be NULL. */
+int pprpa_grad_vector(pprpa_ctx* ctx, int mult, const double* z, double* dL, double* deps,
+                      int where);
 
 /* ---- diagnostics ----------------------------------------------------------
  * pprpa_profile: CUDA-event timing of every tensor-core sigma GEMM launch,

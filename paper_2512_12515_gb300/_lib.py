@@ -85,11 +85,14 @@ SIGNATURES = {
     "pprpa_build_matrix": (_I, [_P, _I, _P, _I]),
     "pprpa_solve": (_I, [_P, ctypes.POINTER(Options), _P, _P, _P, _P, ctypes.POINTER(Info)]),
     "pprpa_grad": (_I, [_P, _I, _P, _P, _I]),
+    "pprpa_grad_vector": (_I, [_P, _I, _P, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
     "pprpa_profile": (_I, [_P, _I, _P]),
     "pprpa_sigma_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P, _P, _P]),
+    "pprpa_sigma_batch": (_I, [_I, _P, _P, _P, _P, _P, _I, _I]),
+    "pprpa_autotune": (_I, [_P, _I, _I, _I, _P]),
 }
 
 _lib = None
@@ -137,6 +140,18 @@ def _ptr(a, writable=False):
             raise TypeError("tensors must be contiguous float64")
         return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def sigma_batch(contexts, mults, zs, outs, precision=PREC_BF16, graph=True):
+    """Batched sigma over molecules (pprpa_sigma_batch); zs / outs are CUDA tensors."""
+    n = len(contexts)
+    ctxs = (_P * n)(*[c._h.value for c in contexts])
+    mu = (_I * n)(*[int(m) for m in mults])
+    ks = (_I * n)(*[int(z.shape[0]) for z in zs])
+    zp = (_P * n)(*[z.data_ptr() for z in zs])
+    op = (_P * n)(*[o.data_ptr() for o in outs])
+    _check(load().pprpa_sigma_batch(n, ctxs, mu, ks, zp, op, int(precision), 1 if graph else 0))
+    return outs
 
 
 def sigma_noalloc(mult, nocc_act, nvir_act, L, eps, z, out, stream=None):
@@ -273,6 +288,27 @@ class Context:
             _check(rc)
         return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
                 "info": info.as_dict(), "rc": rc}
+
+    def autotune(self, mult, k, precision=PREC_BF16):
+        """Tune the tensor-core tile widths on this problem; returns the four widths."""
+        t = (_I * 4)()
+        _check(self.lib.pprpa_autotune(self._h, int(mult), int(k), int(precision), t))
+        return list(t)
+
+    def grad_vector(self, mult, z, dL=None, deps=None):
+        """d(z^T M z)/dL^P_pq and d(z^T M z)/d eps_p for an explicit pair vector z."""
+        n, naux, _, _ = self.dims(mult)
+        if dL is None:
+            dL = np.empty((naux, n, n)) if isinstance(z, np.ndarray) else z.new_empty((naux, n, n))
+        if deps is None:
+            deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        pz, wz = _ptr(z)
+        p1, w1 = _ptr(dL, True)
+        p2, w2 = _ptr(deps, True)
+        if not (wz == w1 == w2):
+            raise ValueError("z, dL and deps must live on the same side")
+        _check(self.lib.pprpa_grad_vector(self._h, int(mult), pz, p1, p2, w1))
+        return dL, deps
 
     def profile(self, enable=None):
         """Read the tensor-core GEMM timing records (4 x {launches, ms, flops});

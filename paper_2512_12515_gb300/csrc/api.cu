@@ -165,6 +165,7 @@ void pprpa_destroy(pprpa_ctx* c) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    destroy_batch_plan(c->batch_plan);
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -381,18 +382,17 @@ int pprpa_sigma(pprpa_ctx* c, int mult, int precision, int k, const double* z, d
     return PPRPA_OK;
 }
 
-int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
-    PP_TRY(check_ctx(c));
-    PP_TRY(need_L(c));
-    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");
-    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
+}  // extern "C"
+
+namespace pprpa {
+// d omega / d L^P and d omega / d eps for one W-normalised pair vector z (device, N).
+static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, double* dL,
+                          double* deps, int where) {
     PairTable* t;
-    PP_TRY(ensure_pairs(c, c->last_mult, &t));
-    const int n = c->n(), naux = c->naux, mult = c->last_mult;
+    PP_TRY(ensure_pairs(c, mult, &t));
+    const int n = c->n(), naux = c->naux;
     const int64_t n2 = (int64_t)n * n;
     cudaStream_t st = c->stream;
-    const double* z = c->d_lastZ + (size_t)root * t->N;
-    const double s = 1.0;  // two-electron addition roots: z^T W z = +1
     const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (deps) {
         double* d;
@@ -439,6 +439,66 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
     }
     PP_CUDA(cudaStreamSynchronize(st));
     return PPRPA_OK;
+}
+}  // namespace pprpa
+
+extern "C" {
+
+int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");
+    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, c->last_mult, &t));
+    // two-electron addition roots: z^T W z = +1
+    return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, 1.0, dL, deps, where);
+}
+
+int pprpa_grad_vector(pprpa_ctx* c, int mult, const double* z, double* dL, double* deps, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (!z) return set_error(PPRPA_ERR_ARG, "grad_vector: null z");
+    PairTable* t;
+    PP_TRY(ensure_pairs(c, mult, &t));
+    const double* dz = z;
+    if (where == PPRPA_HOST) {
+        double* b;
+        PP_TRY(ws_get(c, "gradv_z", sizeof(double) * t->N, (void**)&b));
+        PP_CUDA(cudaMemcpyAsync(b, z, sizeof(double) * t->N, cudaMemcpyHostToDevice, c->stream));
+        dz = b;
+    }
+    return grad_of_vector(c, mult, dz, 1.0, dL, deps, where);
+}
+
+int pprpa_sigma_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
+                      const double* const* z, double* const* sigma, int precision, int flags) {
+    if (nmol <= 0 || !ctxs || !mults || !ks || !z || !sigma)
+        return set_error(PPRPA_ERR_ARG, "sigma_batch: bad arguments");
+    if (precision != PPRPA_PREC_BF16 && precision != PPRPA_PREC_BF16 + 16)
+        return set_error(PPRPA_ERR_ARG, "sigma_batch: precision must be BF16 or BF16x3");
+    PP_TRY(check_ctx(ctxs[0]));
+    for (int m = 0; m < nmol; ++m) {
+        if (!ctxs[m] || ctxs[m]->device != ctxs[0]->device)
+            return set_error(PPRPA_ERR_ARG, "sigma_batch: all contexts must share one device");
+        PP_TRY(need_L(ctxs[m]));
+        if ((mults[m] != 1 && mults[m] != 3) || ks[m] <= 0 || !z[m] || !sigma[m])
+            return set_error(PPRPA_ERR_ARG, "sigma_batch: bad molecule arguments");
+    }
+    cudaStream_t st = ctxs[0]->stream;
+    const int nterms = precision == PPRPA_PREC_BF16 ? 1 : 3;
+    PP_TRY(sigma_tc_batch(nmol, ctxs, mults, ks, z, sigma, nterms, st, ctxs[0], (flags & 1) != 0));
+    PP_TRY(check_status(ctxs[0]));
+    return PPRPA_OK;
+}
+
+int pprpa_autotune(pprpa_ctx* c, int mult, int k, int precision, int* tiles) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if ((mult != 1 && mult != 3) || k <= 0) return set_error(PPRPA_ERR_ARG, "autotune: bad arguments");
+    if (precision != PPRPA_PREC_BF16 && precision != PPRPA_PREC_BF16 + 16)
+        return set_error(PPRPA_ERR_ARG, "autotune: precision must be BF16 or BF16x3");
+    return autotune_tiles(c, mult, k, precision == PPRPA_PREC_BF16 ? 1 : 3, tiles);
 }
 
 int pprpa_profile(pprpa_ctx* c, int enable, double* out) {

@@ -62,6 +62,9 @@ struct pprpa_ctx {
     bool profile = false;
     std::vector<pprpa::ProfRec> prof;
 
+    // batched-sigma plan (tensor maps, work items, CUDA graph) owned by this context
+    void* batch_plan = nullptr;
+
     // last solve (for gradients)
     int last_mult = 0;
     int last_nroots = 0;
@@ -78,6 +81,11 @@ int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out);
 int ensure_bf16(pprpa_ctx* c);
 int sigma_f64(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma);
 int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms);
+int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
+                   const double* const* z, double* const* sigma, int nterms, cudaStream_t st,
+                   pprpa_ctx* owner, bool use_graph);
+void destroy_batch_plan(void* plan);
+int autotune_tiles(pprpa_ctx* c, int mult, int k, int nterms, int* bn_out);
 int check_status(pprpa_ctx* c);
 
 }  // namespace pprpa

@@ -312,8 +312,10 @@ __global__ void unpack_bf16_kernel(const double* __restrict__ z, int k, int N, i
         int p = pp[I], q = pq[I];
         __nv_bfloat16 *hi, *lo;
         int64_t rows, ld;
-        if (I < nvv) { p -= pm.no; q -= pm.no; hi = xs_hi; lo = xs_lo; rows = pm.nv; ld = ldx; }
-        else { hi = ys_hi; lo = ys_lo; rows = pm.no; ld = ldy; }
+        // each vector owns a block of rows padded to a multiple of 8 (nv_p / no_p); the
+        // padding rows stay zero
+        if (I < nvv) { p -= pm.no; q -= pm.no; hi = xs_hi; lo = xs_lo; rows = pm.nv_p; ld = ldx; }
+        else { hi = ys_hi; lo = ys_lo; rows = pm.no_p; ld = ldy; }
         const int64_t base = j * rows * ld;
         // Zt[p][q] (p <= q) and Zt[q][p]; stack entry [c][d] = Zt[d][c].
         double zpq, zqp;

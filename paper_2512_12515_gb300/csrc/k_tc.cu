@@ -23,6 +23,7 @@
 // and returns.
 #include <cuda.h>
 
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -204,12 +205,18 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
     return c;
 }
 
-template <int NTERMS>
+// One kernel body for both launch forms.  Single: the tensor maps and the parameters are
+// kernel parameters and work items are decoded arithmetically.  Batched: work item i is
+// items[i]; it names a job (one molecule and stage block) whose tensor maps and epilogue
+// parameters live in global memory, so molecules of different sizes and tile widths share
+// one persistent launch.  p.slot_bn sizes the shared-memory slots (the widest B tile).
+template <int NTERMS, bool BATCHED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                    const __grid_constant__ CUtensorMap tmA_lo,
                    const __grid_constant__ CUtensorMap tmB_hi,
-                   const __grid_constant__ CUtensorMap tmB_lo, const TcParams p) {
+                   const __grid_constant__ CUtensorMap tmB_lo, const TcParams p,
+                   const TcJob* __restrict__ jobs, const TcItem* __restrict__ items) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * TC_MAX_STAGES + 5];
     __shared__ uint32_t tmem_slot;
@@ -219,14 +226,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.stages;
     const uint32_t a_bytes = TC_BM * TC_BK * 2;
-    const uint32_t b_bytes = (uint32_t)p.BN * TC_BK * 2;
-    const uint32_t slot_bytes = (a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
+    const uint32_t b_slot = (uint32_t)p.slot_bn * TC_BK * 2;
+    const uint32_t slot_bytes = (a_bytes + b_slot) * (NTERMS == 3 ? 2 : 1);
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (TC_MAX_STAGES + s); };
     auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + a); };
     auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + 2 + a); };
     const uint32_t done_bar = bar0 + 8u * (2 * TC_MAX_STAGES + 4);
+
+    // work item -> (coordinates, parameters, tensor maps)
+    auto fetch = [&](int item, ItemCoord& c, const TcParams*& q, const CUtensorMap*& mA_hi,
+                     const CUtensorMap*& mA_lo, const CUtensorMap*& mB_hi,
+                     const CUtensorMap*& mB_lo) {
+        if constexpr (BATCHED) {
+            const TcItem it = items[item];
+            const TcJob* jb = jobs + it.job;
+            q = &jb->p;
+            mA_hi = &jb->a_hi; mA_lo = &jb->a_lo; mB_hi = &jb->b_hi; mB_lo = &jb->b_lo;
+            c.m0 = it.m0; c.n0 = it.n0; c.batch = it.batch; c.kb0 = it.kb0; c.kb1 = it.kb1;
+        } else {
+            q = &p;
+            mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
+            c = decode_item(p, item);
+        }
+    };
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -263,7 +287,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t issued_mask = 0, issued_par = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
-                const ItemCoord c = decode_item(p, item);
+                ItemCoord c;
+                const TcParams* q;
+                const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
+                fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
+                const uint32_t b_bytes = (uint32_t)q->BN * TC_BK * 2;
+                const uint32_t tx = (a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
                 for (int kb = c.kb0; kb < c.kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, &abort_flag, p.status)) {
                         ok = false;
@@ -271,26 +300,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t sbase = smem_u32(smem + (size_t)stage * slot_bytes);
                     const uint32_t fb = full_bar(stage);
-                    mbar_expect_tx(fb, slot_bytes);
+                    mbar_expect_tx(fb, tx);
                     const uint32_t a_hi = sbase, b_hi = sbase + a_bytes;
-                    const uint32_t a_lo = sbase + a_bytes + b_bytes,
-                                   b_lo = sbase + 2 * a_bytes + b_bytes;
-                    if (p.mode == 0) {
-                        const int x = p.a_col_off + kb * TC_BK;
-                        tma_2d(a_hi, &tmA_hi, x, c.m0, fb);
-                        tma_2d(b_hi, &tmB_hi, kb * TC_BK, c.n0, fb);
+                    const uint32_t a_lo = sbase + a_bytes + b_slot,
+                                   b_lo = sbase + 2 * a_bytes + b_slot;
+                    if (q->mode == 0) {
+                        const int x = q->a_col_off + kb * TC_BK;
+                        tma_2d(a_hi, mA_hi, x, c.m0, fb);
+                        tma_2d(b_hi, mB_hi, kb * TC_BK, c.n0, fb);
                         if (NTERMS == 3) {
-                            tma_2d(a_lo, &tmA_lo, x, c.m0, fb);
-                            tma_2d(b_lo, &tmB_lo, kb * TC_BK, c.n0, fb);
+                            tma_2d(a_lo, mA_lo, x, c.m0, fb);
+                            tma_2d(b_lo, mB_lo, kb * TC_BK, c.n0, fb);
                         }
                     } else {
-                        const int P = kb / p.kq_blocks;
-                        const int q = (kb % p.kq_blocks) * TC_BK;
-                        tma_4d(a_hi, &tmA_hi, q, c.batch, p.row_off + c.m0, P, fb);
-                        tma_3d(b_hi, &tmB_hi, q, p.col_off + c.n0, P, fb);
+                        const int P = kb / q->kq_blocks;
+                        const int qq = (kb % q->kq_blocks) * TC_BK;
+                        tma_4d(a_hi, mA_hi, qq, c.batch, q->row_off + c.m0, P, fb);
+                        tma_3d(b_hi, mB_hi, qq, q->col_off + c.n0, P, fb);
                         if (NTERMS == 3) {
-                            tma_4d(a_lo, &tmA_lo, q, c.batch, p.row_off + c.m0, P, fb);
-                            tma_3d(b_lo, &tmB_lo, q, p.col_off + c.n0, P, fb);
+                            tma_4d(a_lo, mA_lo, qq, c.batch, q->row_off + c.m0, P, fb);
+                            tma_3d(b_lo, mB_lo, qq, q->col_off + c.n0, P, fb);
                         }
                     }
                     issued_mask |= 1u << stage;
@@ -315,17 +344,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 5) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = idesc_bf16(p.BN);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
-                const ItemCoord c = decode_item(p, item);
+                ItemCoord c;
+                const TcParams* q;
+                const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
+                fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
+                const int bn = q->BN;
+                const uint32_t idesc = idesc_bf16(bn);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(acc * p.BN);
+                const uint32_t dt = tmem_base + (uint32_t)(acc * p.slot_bn);
                 for (int kb = c.kb0; kb < c.kb1; ++kb) {
                     if (!mbar_wait(full_bar(stage), phase, &abort_flag, p.status)) {
                         ok = false;
@@ -334,8 +367,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t sbase = smem_u32(smem + (size_t)stage * slot_bytes);
                     const uint32_t a_hi = sbase, b_hi = sbase + a_bytes;
-                    const uint32_t a_lo = sbase + a_bytes + b_bytes,
-                                   b_lo = sbase + 2 * a_bytes + b_bytes;
+                    const uint32_t a_lo = sbase + a_bytes + b_slot,
+                                   b_lo = sbase + 2 * a_bytes + b_slot;
 #pragma unroll
                     for (int k = 0; k < TC_BK / 16; ++k) {
                         const uint32_t off = k * 32;
@@ -369,28 +402,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         uint32_t acc_phase = 0;
         const int row = warp * 32 + lane;
         for (int item = blockIdx.x; item < p.total_items; item += gridDim.x) {
-            const ItemCoord c = decode_item(p, item);
+            ItemCoord c;
+            const TcParams* q;
+            const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
+            fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
+            const int bn = q->BN;
             if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status)) break;
             tc_fence_after();
             const uint32_t tbase =
-                tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * p.BN);
-            if (p.mode == 0) {
+                tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * p.slot_bn);
+            if (q->mode == 0) {
                 const int64_t R = (int64_t)c.m0 + row;
-                const bool rok = R < p.M_rows;
-                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                const bool rok = R < q->M_rows;
+                const int n_per_j = q->n_per_j, n_total = q->n_total, k_vec = q->k_vec;
+                const int t_col_off = q->t_col_off;
+                const int64_t n_pad = q->n_pad;
+                __nv_bfloat16* t_hi = q->t_hi;
+                __nv_bfloat16* t_lo = q->t_lo;
+                for (int c0 = 0; c0 < bn; c0 += 16) {
                     float v[16];
                     tmem_ld16(tbase + c0, v);
                     if (!rok) continue;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int n = c.n0 + c0 + 8 * h;
-                        if (n >= p.n_total) continue;
-                        const int j = n / p.n_per_j;
-                        const int cc = n - j * p.n_per_j;
-                        const int q = p.t_col_off + cc;
-                        const int64_t base = (R * p.k_vec + j) * (int64_t)p.n_pad;
-                        const bool vec = (cc + 8 <= p.n_per_j) && (n + 8 <= p.n_total) &&
-                                         ((q & 7) == 0);
+                        if (n >= n_total) continue;
+                        const int j = n / n_per_j;
+                        const int cc = n - j * n_per_j;
+                        const int qc = t_col_off + cc;
+                        const int64_t base = (R * k_vec + j) * n_pad;
+                        const bool vec = (cc + 8 <= n_per_j) && (n + 8 <= n_total) && ((qc & 7) == 0);
                         if (vec) {
                             __align__(16) __nv_bfloat16 hb[8];
                             __align__(16) __nv_bfloat16 lb[8];
@@ -400,38 +441,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 hb[e] = __float2bfloat16_rn(x);
                                 lb[e] = __float2bfloat16_rn(x - __bfloat162float(hb[e]));
                             }
-                            *(uint4*)(p.t_hi + base + q) = *(const uint4*)hb;
-                            if (NTERMS == 3) *(uint4*)(p.t_lo + base + q) = *(const uint4*)lb;
+                            *(uint4*)(t_hi + base + qc) = *(const uint4*)hb;
+                            if (NTERMS == 3) *(uint4*)(t_lo + base + qc) = *(const uint4*)lb;
                         } else {
                             for (int e = 0; e < 8; ++e) {
                                 const int ne = n + e;
-                                if (ne >= p.n_total) break;
-                                const int je = ne / p.n_per_j;
-                                const int ce = ne - je * p.n_per_j;
-                                const int64_t off =
-                                    (R * p.k_vec + je) * (int64_t)p.n_pad + p.t_col_off + ce;
+                                if (ne >= n_total) break;
+                                const int je = ne / n_per_j;
+                                const int ce = ne - je * n_per_j;
+                                const int64_t off = (R * k_vec + je) * n_pad + t_col_off + ce;
                                 const float x = v[8 * h + e];
                                 const __nv_bfloat16 hv = __float2bfloat16_rn(x);
-                                p.t_hi[off] = hv;
-                                if (NTERMS == 3)
-                                    p.t_lo[off] = __float2bfloat16_rn(x - __bfloat162float(hv));
+                                t_hi[off] = hv;
+                                if (NTERMS == 3) t_lo[off] = __float2bfloat16_rn(x - __bfloat162float(hv));
                             }
                         }
                     }
                 }
             } else {
                 const int a = c.m0 + row;
-                const bool rok = a < p.m_valid;
-                float* Ob = p.O + (int64_t)c.batch * p.n_pad * p.n_pad +
-                            (int64_t)(p.row_off + a) * p.n_pad + p.col_off;
-                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                const bool rok = a < q->m_valid;
+                const int n_valid = q->n_valid;
+                float* Ob = q->O + (int64_t)c.batch * q->n_pad * q->n_pad +
+                            (int64_t)(q->row_off + a) * q->n_pad + q->col_off;
+                for (int c0 = 0; c0 < bn; c0 += 16) {
                     float v[16];
                     tmem_ld16(tbase + c0, v);
                     if (!rok) continue;
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int b = c.n0 + c0 + e;
-                        if (b < p.n_valid) atomicAdd(Ob + b, v[e]);
+                        if (b < n_valid) atomicAdd(Ob + b, v[e]);
                     }
                 }
             }
@@ -506,25 +546,58 @@ int tc_stages_for(int BN, int nterms) {
     return s;
 }
 
+static int slot_bytes_for(int BN, int nterms) {
+    return (TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
+}
+
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st) {
     if (p.total_items <= 0) return PPRPA_OK;
     if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0)
         return set_error(PPRPA_ERR_ARG, "tc_gemm: BN must be a multiple of 16 in [16, 256]");
+    p.slot_bn = p.BN;
     p.stages = tc_stages_for(p.BN, nterms);
     if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * p.BN) cols <<= 1;
     p.tmem_cols = cols;
-    const int slot = (TC_BM * TC_BK * 2 + p.BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
-    const size_t smem = (size_t)slot * p.stages + 1024;
+    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
     const int grid = p.total_items < num_sms ? p.total_items : num_sms;
     if (nterms == 3) {
-        cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<3><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p);
+        cudaFuncSetAttribute(tc_gemm_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<3, false><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
     } else {
-        cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p);
+        cudaFuncSetAttribute(tc_gemm_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1, false><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+    }
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_items, int max_bn,
+                           int nterms, int num_sms, int* status, cudaStream_t st) {
+    if (total_items <= 0) return PPRPA_OK;
+    if (max_bn < 16 || max_bn > 256 || (max_bn % 16) != 0)
+        return set_error(PPRPA_ERR_ARG, "tc_gemm_batched: bad tile width");
+    TcParams p;
+    p.total_items = total_items;
+    p.status = status;
+    p.slot_bn = max_bn;
+    p.BN = max_bn;
+    p.stages = tc_stages_for(max_bn, nterms);
+    int cols = 32;
+    while (cols < 2 * max_bn) cols <<= 1;
+    p.tmem_cols = cols;
+    const size_t smem = (size_t)slot_bytes_for(max_bn, nterms) * p.stages + 1024;
+    const int grid = total_items < num_sms ? total_items : num_sms;
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    if (nterms == 3) {
+        cudaFuncSetAttribute(tc_gemm_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<3, true><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
+    } else {
+        cudaFuncSetAttribute(tc_gemm_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1, true><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
     }
     PP_CHECK_LAUNCH();
     return PPRPA_OK;

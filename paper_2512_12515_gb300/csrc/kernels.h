@@ -53,8 +53,8 @@ PadMap make_padmap(int no, int nv);
 int launch_quantize_bf16(const double* L, int naux, int n, PadMap pm, __nv_bfloat16* hi,
                          __nv_bfloat16* lo, cudaStream_t st);
 // z (k x N) -> B operands of the first sandwich stage, bf16 hi[/lo]:
-//   Xs[j][c][d] = Zt_j[no_p+d][no_p+c] (virtual block, ld = ldx),
-//   Ys[j][c][d] = Zt_j[d][c]            (occupied block, ld = ldy).
+//   Xs[j][c][d] = Zt_j[no_p+d][no_p+c] (virtual block, c < nv_p rows per vector, ld = ldx),
+//   Ys[j][c][d] = Zt_j[d][c]            (occupied block, c < no_p rows per vector, ld = ldy).
 int launch_unpack_bf16(const double* z, int k, int N, int nvv, const int* pp, const int* pq,
                        PadMap pm, int mult, __nv_bfloat16* xs_hi, __nv_bfloat16* xs_lo,
                        int ldx, __nv_bfloat16* ys_hi, __nv_bfloat16* ys_lo, int ldy,

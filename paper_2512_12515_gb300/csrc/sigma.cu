@@ -165,159 +165,458 @@ static int env_int(const char* name, int dflt) {
     return s ? atoi(s) : dflt;
 }
 
+// ---------------------------------------------------------------------------
 // Tensor-core form.  nterms = 1: BF16 operands; nterms = 3: BF16x3 split.
-int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms) {
-    PairTable* pt;
-    PP_TRY(ensure_pairs(c, mult, &pt));
-    PP_TRY(ensure_bf16(c));
-    const PadMap pm = c->pm;
-    const int no = c->no, nv = c->nv, naux = c->naux;
-    const int64_t np = pm.n_pad;
-    cudaStream_t st = c->stream;
-    const bool split = nterms == 3;
+//
+// A sigma call is planned as a list of jobs, one per (stage, pair block, P chunk): each
+// job carries its tensor maps and kernel parameters.  A single molecule runs its jobs
+// one launch at a time; a batch of molecules runs all stage-1 jobs in one persistent
+// launch and all stage-2 jobs in another.
 
-    // B operands of stage 1: Xs [k][nv][nv_p], Ys [k][no][no_p]
-    const int ldx = pm.nv_p, ldy = std::max(pm.no_p, 8);
-    const size_t xs_bytes = sizeof(__nv_bfloat16) * (size_t)k * std::max(nv, 1) * ldx;
-    const size_t ys_bytes = sizeof(__nv_bfloat16) * (size_t)k * std::max(no, 1) * ldy;
-    __nv_bfloat16 *xs_hi, *xs_lo, *ys_hi, *ys_lo;
-    PP_TRY(ws_get(c, "tc_xs_hi", xs_bytes, (void**)&xs_hi));
-    PP_TRY(ws_get(c, "tc_xs_lo", xs_bytes, (void**)&xs_lo));
-    PP_TRY(ws_get(c, "tc_ys_hi", ys_bytes, (void**)&ys_hi));
-    PP_TRY(ws_get(c, "tc_ys_lo", ys_bytes, (void**)&ys_lo));
-    PP_CUDA(cudaMemsetAsync(xs_hi, 0, xs_bytes, st));
-    PP_CUDA(cudaMemsetAsync(ys_hi, 0, ys_bytes, st));
-    if (split) {
-        PP_CUDA(cudaMemsetAsync(xs_lo, 0, xs_bytes, st));
-        PP_CUDA(cudaMemsetAsync(ys_lo, 0, ys_bytes, st));
-    }
-    PP_TRY(launch_unpack_bf16(d_z, k, pt->N, pt->nvv, pt->d_pp, pt->d_pq, pm, mult, xs_hi,
-                              split ? xs_lo : nullptr, ldx, ys_hi, split ? ys_lo : nullptr, ldy,
-                              st));
+struct TcPrepared {
+    PairTable* pt = nullptr;
+    PadMap pm;
+    int k = 0, mult = 1, nterms = 1, pc = 0;
+    int ldx = 0, ldy = 0;
+    __nv_bfloat16 *xs_hi = nullptr, *xs_lo = nullptr, *ys_hi = nullptr, *ys_lo = nullptr;
+    __nv_bfloat16 *t_hi = nullptr, *t_lo = nullptr;
+    float* O = nullptr;
+    const double* d_z = nullptr;
+};
+
+struct TcJobHost {
+    TcJob job;
+    int kind = 0;        // profile row
+    double flops = 0.0;  // algorithmic
+};
+
+// Buffers (allocated on first use, sized for k vectors).
+static int tc_alloc(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms, TcPrepared& pr,
+                    cudaStream_t st) {
+    PP_TRY(ensure_pairs(c, mult, &pr.pt));
+    PP_TRY(ensure_bf16(c));
+    pr.pm = c->pm;
+    pr.k = k;
+    pr.mult = mult;
+    pr.nterms = nterms;
+    pr.d_z = d_z;
+    const PadMap pm = c->pm;
+    const int64_t np = pm.n_pad;
+    const bool split = nterms == 3;
+    pr.ldx = std::max(pm.nv_p, 8);
+    pr.ldy = std::max(pm.no_p, 8);
+    const size_t xs_bytes = sizeof(__nv_bfloat16) * (size_t)k * pr.ldx * pr.ldx;
+    const size_t ys_bytes = sizeof(__nv_bfloat16) * (size_t)k * pr.ldy * pr.ldy;
+    PP_TRY(ws_get(c, "tc_xs_hi", xs_bytes, (void**)&pr.xs_hi));
+    PP_TRY(ws_get(c, "tc_xs_lo", xs_bytes, (void**)&pr.xs_lo));
+    PP_TRY(ws_get(c, "tc_ys_hi", ys_bytes, (void**)&pr.ys_hi));
+    PP_TRY(ws_get(c, "tc_ys_lo", ys_bytes, (void**)&pr.ys_lo));
     // intermediate T [pc][n_pad][k][n_pad] (hi, lo) and output O [k][n_pad][n_pad] FP32
     const int64_t per_p = (int64_t)sizeof(__nv_bfloat16) * np * k * np;
     const int64_t budget = (int64_t)env_int("PPRPA_T_BUDGET_MB", 64 * 1024) << 20;
-    int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, budget / (per_p * (split ? 2 : 1))));
-    __nv_bfloat16 *t_hi, *t_lo = nullptr;
+    pr.pc = (int)std::max<int64_t>(1, std::min<int64_t>(c->naux, budget / (per_p * (split ? 2 : 1))));
     {
-        // T is zero-initialised once per allocation: padding columns are never written.
+        // T is zero-initialised once per allocation: padding columns only ever hold zeros
         DevBuf before = c->ws["tc_t_hi"];
-        PP_TRY(ws_get(c, "tc_t_hi", per_p * pc, (void**)&t_hi));
-        if (c->ws["tc_t_hi"].p != before.p) PP_CUDA(cudaMemsetAsync(t_hi, 0, c->ws["tc_t_hi"].bytes, st));
+        PP_TRY(ws_get(c, "tc_t_hi", per_p * pr.pc, (void**)&pr.t_hi));
+        if (c->ws["tc_t_hi"].p != before.p) PP_CUDA(cudaMemsetAsync(pr.t_hi, 0, c->ws["tc_t_hi"].bytes, st));
         if (split) {
             DevBuf b2 = c->ws["tc_t_lo"];
-            PP_TRY(ws_get(c, "tc_t_lo", per_p * pc, (void**)&t_lo));
-            if (c->ws["tc_t_lo"].p != b2.p) PP_CUDA(cudaMemsetAsync(t_lo, 0, c->ws["tc_t_lo"].bytes, st));
+            PP_TRY(ws_get(c, "tc_t_lo", per_p * pr.pc, (void**)&pr.t_lo));
+            if (c->ws["tc_t_lo"].p != b2.p) PP_CUDA(cudaMemsetAsync(pr.t_lo, 0, c->ws["tc_t_lo"].bytes, st));
         }
     }
-    float* O;
     const size_t o_bytes = sizeof(float) * (size_t)k * np * np;
-    PP_TRY(ws_get(c, "tc_O", o_bytes, (void**)&O));
-    PP_CUDA(cudaMemsetAsync(O, 0, o_bytes, st));
+    PP_TRY(ws_get(c, "tc_O", o_bytes, (void**)&pr.O));
+    return PPRPA_OK;
+}
 
-    const int BN1 = env_int("PPRPA_BN1", 256);
-    for (int P0 = 0; P0 < naux; P0 += pc) {
-        const int npc = std::min(pc, naux - P0);
-        const __nv_bfloat16* Lh = c->d_Lhi + (int64_t)P0 * np * np;
-        const __nv_bfloat16* Ll = c->d_Llo + (int64_t)P0 * np * np;
-        // ---------------- stage 1 ----------------
-        for (int blk = 0; blk < 2; ++blk) {
-            const int sz = blk == 0 ? nv : no;
-            if (sz == 0) continue;
-            CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-            const uint64_t adims[2] = {(uint64_t)np, (uint64_t)npc * np};
-            const uint64_t astr[1] = {(uint64_t)np * 2};
-            const uint32_t abox[2] = {64, 128};
-            PP_TRY(make_tmap_bf16(&ta_hi, Lh, 2, adims, astr, abox));
-            PP_TRY(make_tmap_bf16(&ta_lo, Ll, 2, adims, astr, abox));
-            const int ld = blk == 0 ? ldx : ldy;
-            const uint64_t bdims[2] = {(uint64_t)sz, (uint64_t)k * sz};
-            const uint64_t bstr[1] = {(uint64_t)ld * 2};
-            const int BN = std::min(BN1, (int)round_up(std::max(16, (int)std::min<int64_t>(256, (int64_t)k * sz)), 16));
-            const uint32_t bbox[2] = {64, (uint32_t)BN};
-            PP_TRY(make_tmap_bf16(&tb_hi, blk == 0 ? xs_hi : ys_hi, 2, bdims, bstr, bbox));
-            PP_TRY(make_tmap_bf16(&tb_lo, blk == 0 ? xs_lo : ys_lo, 2, bdims, bstr, bbox));
-            TcParams p;
-            p.mode = 0;
-            p.BN = BN;
-            p.status = c->d_status;
-            p.M_rows = (int64_t)npc * np;
-            p.a_col_off = blk == 0 ? pm.no_p : 0;
-            p.n_per_j = sz;
-            p.n_total = k * sz;
-            p.t_col_off = blk == 0 ? pm.no_p : 0;
-            p.n_pad = (int)np;
-            p.k_vec = k;
-            p.t_hi = t_hi;
-            p.t_lo = t_lo;
-            p.kb_total = (int)ceil_div(sz, 64);
-            p.tiles_n = (int)ceil_div(p.n_total, BN);
-            const int64_t items = ceil_div(p.M_rows, 128) * p.tiles_n;
-            if (items > INT32_MAX) return set_error(PPRPA_ERR_ARG, "sigma: too many stage-1 tiles");
-            p.total_items = (int)items;
-            const double fl = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
-            PP_TRY(timed_launch(c, split ? 2 : 0, fl, ta_hi, ta_lo, tb_hi, tb_lo, p, nterms));
-        }
-        // ---------------- stage 2 ----------------
-        for (int blk = 0; blk < 2; ++blk) {
-            const int sz = blk == 0 ? nv : no;
-            if (sz == 0) continue;
-            const int off = blk == 0 ? pm.no_p : 0;
-            std::string key = std::string("bn2_") + std::to_string(sz);
-            int BN = c->tuned_bn.count(key) ? c->tuned_bn[key] : stage2_bn(sz);
-            const int forced = env_int("PPRPA_BN2", 0);
-            if (forced) BN = forced;
-            std::vector<int2> tiles = triangle_tiles(sz, BN);
+// Device work before the GEMMs: the packed B operands of stage 1 and a zeroed O.
+static int tc_device_prep(pprpa_ctx* c, const TcPrepared& pr, cudaStream_t st) {
+    const bool split = pr.nterms == 3;
+    const size_t xs_bytes = sizeof(__nv_bfloat16) * (size_t)pr.k * pr.ldx * pr.ldx;
+    const size_t ys_bytes = sizeof(__nv_bfloat16) * (size_t)pr.k * pr.ldy * pr.ldy;
+    PP_CUDA(cudaMemsetAsync(pr.xs_hi, 0, xs_bytes, st));
+    PP_CUDA(cudaMemsetAsync(pr.ys_hi, 0, ys_bytes, st));
+    if (split) {
+        PP_CUDA(cudaMemsetAsync(pr.xs_lo, 0, xs_bytes, st));
+        PP_CUDA(cudaMemsetAsync(pr.ys_lo, 0, ys_bytes, st));
+    }
+    PP_TRY(launch_unpack_bf16(pr.d_z, pr.k, pr.pt->N, pr.pt->nvv, pr.pt->d_pp, pr.pt->d_pq, pr.pm,
+                              pr.mult, pr.xs_hi, split ? pr.xs_lo : nullptr, pr.ldx, pr.ys_hi,
+                              split ? pr.ys_lo : nullptr, pr.ldy, st));
+    const int64_t np = pr.pm.n_pad;
+    PP_CUDA(cudaMemsetAsync(pr.O, 0, sizeof(float) * (size_t)pr.k * np * np, st));
+    (void)c;
+    return PPRPA_OK;
+}
+
+static int tc_prepare(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms,
+                      TcPrepared& pr, cudaStream_t st) {
+    PP_TRY(tc_alloc(c, mult, k, d_z, nterms, pr, st));
+    return tc_device_prep(c, pr, st);
+}
+
+static std::string tune_key(int stage, int sz, int k) {
+    return "s" + std::to_string(stage) + "_" + std::to_string(sz) + "_" + std::to_string(k);
+}
+
+// Tile width of a stage: forced by the environment, else the autotuned value, else the model.
+static int tile_bn(pprpa_ctx* c, int stage, int sz, int k, int szp) {
+    const int forced = env_int(stage == 1 ? "PPRPA_BN1" : "PPRPA_BN2", 0);
+    if (forced) return forced;
+    auto it = c->tuned_bn.find(tune_key(stage, sz, k));
+    if (it != c->tuned_bn.end()) return it->second;
+    if (stage == 1) return (int)round_up(std::max(16, (int)std::min<int64_t>(256, (int64_t)k * szp)), 16);
+    return stage2_bn(sz);
+}
+
+// Jobs of one P chunk [P0, P0 + npc).
+static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vector<TcJobHost>& s1,
+                   std::vector<TcJobHost>& s2, std::vector<std::vector<int2>>& tiles) {
+    const PadMap pm = pr.pm;
+    const int no = c->no, nv = c->nv, k = pr.k;
+    const int64_t np = pm.n_pad;
+    const bool split = pr.nterms == 3;
+    const __nv_bfloat16* Lh = c->d_Lhi + (int64_t)P0 * np * np;
+    const __nv_bfloat16* Ll = c->d_Llo + (int64_t)P0 * np * np;
+    for (int blk = 0; blk < 2; ++blk) {  // stage 1: T = L Zt on the virtual / occupied columns
+        const int sz = blk == 0 ? nv : no;
+        if (sz == 0) continue;
+        TcJobHost h;
+        TcJob& j = h.job;
+        const uint64_t adims[2] = {(uint64_t)np, (uint64_t)npc * np};
+        const uint64_t astr[1] = {(uint64_t)np * 2};
+        const uint32_t abox[2] = {64, 128};
+        PP_TRY(make_tmap_bf16(&j.a_hi, Lh, 2, adims, astr, abox));
+        PP_TRY(make_tmap_bf16(&j.a_lo, Ll, 2, adims, astr, abox));
+        const int ld = blk == 0 ? pr.ldx : pr.ldy;
+        const int szp = blk == 0 ? pm.nv_p : pm.no_p;  // rows per vector (8-aligned)
+        const uint64_t bdims[2] = {(uint64_t)sz, (uint64_t)k * szp};
+        const uint64_t bstr[1] = {(uint64_t)ld * 2};
+        const int BN = tile_bn(c, 1, sz, k, szp);
+        const uint32_t bbox[2] = {64, (uint32_t)BN};
+        PP_TRY(make_tmap_bf16(&j.b_hi, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, bbox));
+        PP_TRY(make_tmap_bf16(&j.b_lo, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, bbox));
+        TcParams& p = j.p;
+        p.mode = 0;
+        p.BN = BN;
+        p.status = c->d_status;
+        p.M_rows = (int64_t)npc * np;
+        p.a_col_off = blk == 0 ? pm.no_p : 0;
+        p.n_per_j = szp;
+        p.n_total = k * szp;
+        p.t_col_off = blk == 0 ? pm.no_p : 0;
+        p.n_pad = (int)np;
+        p.k_vec = k;
+        p.t_hi = pr.t_hi;
+        p.t_lo = pr.t_lo;
+        p.kb_total = (int)ceil_div(sz, 64);
+        p.tiles_n = (int)ceil_div(p.n_total, BN);
+        const int64_t items = ceil_div(p.M_rows, 128) * p.tiles_n;
+        if (items > INT32_MAX) return set_error(PPRPA_ERR_ARG, "sigma: too many stage-1 tiles");
+        p.total_items = (int)items;
+        h.kind = split ? 2 : 0;
+        h.flops = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
+        s1.push_back(h);
+    }
+    for (int blk = 0; blk < 2; ++blk) {  // stage 2: O += T L on the upper triangle of a block
+        const int sz = blk == 0 ? nv : no;
+        if (sz == 0) continue;
+        const int off = blk == 0 ? pm.no_p : 0;
+        const int BN = tile_bn(c, 2, sz, k, 0);
+        tiles.push_back(triangle_tiles(sz, BN));
+        const std::vector<int2>& tl = tiles.back();
+        TcJobHost h;
+        TcJob& j = h.job;
+        const uint64_t adims[4] = {(uint64_t)np, (uint64_t)k, (uint64_t)np, (uint64_t)npc};
+        const uint64_t astr[3] = {(uint64_t)np * 2, (uint64_t)k * np * 2, (uint64_t)np * k * np * 2};
+        const uint32_t abox[4] = {64, 1, 128, 1};
+        PP_TRY(make_tmap_bf16(&j.a_hi, pr.t_hi, 4, adims, astr, abox));
+        PP_TRY(make_tmap_bf16(&j.a_lo, split ? pr.t_lo : pr.t_hi, 4, adims, astr, abox));
+        const uint64_t bdims[3] = {(uint64_t)np, (uint64_t)np, (uint64_t)npc};
+        const uint64_t bstr[2] = {(uint64_t)np * 2, (uint64_t)np * np * 2};
+        const uint32_t bbox[3] = {64, (uint32_t)BN, 1};
+        PP_TRY(make_tmap_bf16(&j.b_hi, Lh, 3, bdims, bstr, bbox));
+        PP_TRY(make_tmap_bf16(&j.b_lo, Ll, 3, bdims, bstr, bbox));
+        TcParams& p = j.p;
+        p.mode = 1;
+        p.BN = BN;
+        p.status = c->d_status;
+        p.ntiles = (int)tl.size();
+        p.nbatch = k;
+        p.kq_blocks = (int)ceil_div(np, 64);
+        p.kb_total = npc * p.kq_blocks;
+        // enough K slices for about four waves of work items; in the split form also
+        // at most pcap auxiliary slices per accumulator, because the tensor-core FP32
+        // accumulation loses accuracy over very long reductions (partial sums of the
+        // slices are added in FP32 in L2)
+        const int64_t base_items = (int64_t)p.ntiles * k;
+        int64_t ns = ceil_div(4LL * c->num_sms, base_items);
+        ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max(1, p.kb_total / 8)));
+        const int pcap = env_int(split ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", split ? 2 : 128);
+        if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
+        // every K slice non-empty: recompute the count from the slice length
+        const int64_t per = ceil_div(p.kb_total, ns);
+        p.nsplit = (int)ceil_div(p.kb_total, per);
+        p.row_off = off;
+        p.col_off = off;
+        p.m_valid = sz;
+        p.n_valid = sz;
+        p.n_pad = (int)np;
+        p.O = pr.O;
+        p.total_items = (int)(base_items * p.nsplit);
+        h.kind = split ? 3 : 1;
+        h.flops = 1.0 * npc * (double)(no + nv) * (double)sz * sz * k;
+        s2.push_back(h);
+    }
+    return PPRPA_OK;
+}
+
+int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms) {
+    cudaStream_t st = c->stream;
+    TcPrepared pr;
+    PP_TRY(tc_prepare(c, mult, k, d_z, nterms, pr, st));
+    for (int P0 = 0; P0 < c->naux; P0 += pr.pc) {
+        const int npc = std::min(pr.pc, c->naux - P0);
+        std::vector<TcJobHost> s1, s2;
+        std::vector<std::vector<int2>> tiles;
+        PP_TRY(tc_jobs(c, pr, P0, npc, s1, s2, tiles));
+        for (auto& h : s1)
+            PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi, h.job.b_lo,
+                                h.job.p, nterms));
+        for (size_t b = 0; b < s2.size(); ++b) {
+            TcJobHost& h = s2[b];
             int2* d_tiles;
-            PP_TRY(ws_get(c, "tc_tiles" + std::to_string(blk), sizeof(int2) * tiles.size(), (void**)&d_tiles));
-            PP_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(),
+            PP_TRY(ws_get(c, "tc_tiles" + std::to_string(b), sizeof(int2) * tiles[b].size(), (void**)&d_tiles));
+            PP_CUDA(cudaMemcpyAsync(d_tiles, tiles[b].data(), sizeof(int2) * tiles[b].size(),
                                     cudaMemcpyHostToDevice, st));
-            CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-            const uint64_t adims[4] = {(uint64_t)np, (uint64_t)k, (uint64_t)np, (uint64_t)npc};
-            const uint64_t astr[3] = {(uint64_t)np * 2, (uint64_t)k * np * 2, (uint64_t)np * k * np * 2};
-            const uint32_t abox[4] = {64, 1, 128, 1};
-            PP_TRY(make_tmap_bf16(&ta_hi, t_hi, 4, adims, astr, abox));
-            PP_TRY(make_tmap_bf16(&ta_lo, split ? t_lo : t_hi, 4, adims, astr, abox));
-            const uint64_t bdims[3] = {(uint64_t)np, (uint64_t)np, (uint64_t)npc};
-            const uint64_t bstr[2] = {(uint64_t)np * 2, (uint64_t)np * np * 2};
-            const uint32_t bbox[3] = {64, (uint32_t)BN, 1};
-            PP_TRY(make_tmap_bf16(&tb_hi, Lh, 3, bdims, bstr, bbox));
-            PP_TRY(make_tmap_bf16(&tb_lo, Ll, 3, bdims, bstr, bbox));
-            TcParams p;
-            p.mode = 1;
-            p.BN = BN;
-            p.status = c->d_status;
-            p.tile_list = d_tiles;
-            p.ntiles = (int)tiles.size();
-            p.nbatch = k;
-            p.kq_blocks = (int)ceil_div(np, 64);
-            p.kb_total = npc * p.kq_blocks;
-            // enough K slices for about four waves of work items; in the split form also
-            // at most pcap auxiliary slices per accumulator, because the tensor-core FP32
-            // accumulation loses accuracy over very long reductions (partial sums of the
-            // slices are added in FP32 in L2)
-            const int64_t base_items = (int64_t)p.ntiles * k;
-            int64_t ns = ceil_div(4LL * c->num_sms, base_items);
-            ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max(1, p.kb_total / 8)));
-            const int pcap = env_int(split ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", split ? 2 : 128);
-            if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
-            // every K slice non-empty: recompute the count from the slice length
-            const int64_t per = ceil_div(p.kb_total, ns);
-            p.nsplit = (int)ceil_div(p.kb_total, per);
-            p.row_off = off;
-            p.col_off = off;
-            p.m_valid = sz;
-            p.n_valid = sz;
-            p.n_pad = (int)np;
-            p.O = O;
-            p.total_items = (int)(base_items * p.nsplit);
-            const double fl = 1.0 * npc * (double)(no + nv) * (double)sz * sz * k;
-            PP_TRY(timed_launch(c, split ? 3 : 1, fl, ta_hi, ta_lo, tb_hi, tb_lo, p, nterms));
+            h.job.p.tile_list = d_tiles;
+            PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi, h.job.b_lo,
+                                h.job.p, nterms));
         }
     }
-    PP_TRY(launch_pack_f32(O, d_z, k, pt->N, pt->nvv, pt->d_pp, pt->d_pq, pm, c->d_eps, mult,
-                           d_sigma, st));
+    PP_TRY(launch_pack_f32(pr.O, d_z, k, pr.pt->N, pr.pt->nvv, pr.pt->d_pp, pr.pt->d_pq, pr.pm,
+                           c->d_eps, mult, d_sigma, st));
     return PPRPA_OK;
+}
+
+// Work items of one job (the same decomposition the single launch decodes arithmetically).
+static void append_items(const TcParams& p, int job, const std::vector<int2>* tiles,
+                         std::vector<TcItem>& out) {
+    if (p.mode == 0) {
+        const int64_t mt = ceil_div(p.M_rows, 128);
+        for (int64_t mb = 0; mb < mt; ++mb)
+            for (int nb = 0; nb < p.tiles_n; ++nb)
+                out.push_back(TcItem{job, (int)(mb * 128), nb * p.BN, 0, 0, p.kb_total});
+    } else {
+        const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
+        for (int sp = 0; sp < p.nsplit; ++sp)
+            for (int b = 0; b < p.nbatch; ++b)
+                for (const int2& t : *tiles)
+                    out.push_back(TcItem{job, t.x * 128, t.y * p.BN, b, sp * per,
+                                         std::min(p.kb_total, (sp + 1) * per)});
+    }
+}
+
+// Batched sigma over molecules (each its own context, one device and stream).  The host
+// part (buffers, tensor maps, work items, their upload) runs once per batch signature; the
+// device part (operand packing, the two persistent GEMM launches, unpacking) is replayed
+// as a CUDA graph while the signature is unchanged.
+struct BatchPlan {
+    std::vector<pprpa_ctx*> ctxs;
+    std::vector<int> mults, ks;
+    std::vector<const double*> z;
+    std::vector<double*> sigma;
+    int nterms = 1;
+    cudaStream_t st = nullptr;
+    std::vector<TcPrepared> prs;
+    TcJob *dj1 = nullptr, *dj2 = nullptr;
+    TcItem *di1 = nullptr, *di2 = nullptr;
+    int n1 = 0, n2 = 0, bn1 = 16, bn2 = 16;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_kernels = 0;
+};
+
+static void free_plan_graph(BatchPlan* bp) {
+    if (bp->exec) cudaGraphExecDestroy(bp->exec);
+    if (bp->graph) cudaGraphDestroy(bp->graph);
+    bp->exec = nullptr;
+    bp->graph = nullptr;
+}
+
+void destroy_batch_plan(void* plan) {
+    BatchPlan* bp = (BatchPlan*)plan;
+    if (!bp) return;
+    free_plan_graph(bp);
+    delete bp;
+}
+
+static int batch_exec(BatchPlan& bp, pprpa_ctx* owner) {
+    for (size_t m = 0; m < bp.ctxs.size(); ++m) PP_TRY(tc_device_prep(bp.ctxs[m], bp.prs[m], bp.st));
+    PP_TRY(tc_gemm_launch_batched(bp.dj1, bp.di1, bp.n1, bp.bn1, bp.nterms, owner->num_sms,
+                                  owner->d_status, bp.st));
+    PP_TRY(tc_gemm_launch_batched(bp.dj2, bp.di2, bp.n2, bp.bn2, bp.nterms, owner->num_sms,
+                                  owner->d_status, bp.st));
+    for (size_t m = 0; m < bp.ctxs.size(); ++m) {
+        const TcPrepared& pr = bp.prs[m];
+        PP_TRY(launch_pack_f32(pr.O, bp.z[m], pr.k, pr.pt->N, pr.pt->nvv, pr.pt->d_pp, pr.pt->d_pq,
+                               pr.pm, bp.ctxs[m]->d_eps, pr.mult, bp.sigma[m], bp.st));
+    }
+    return PPRPA_OK;
+}
+
+static bool same_signature(const BatchPlan& bp, int nmol, pprpa_ctx* const* ctxs, const int* mults,
+                           const int* ks, const double* const* z, double* const* sigma, int nterms,
+                           cudaStream_t st) {
+    if ((int)bp.ctxs.size() != nmol || bp.nterms != nterms || bp.st != st) return false;
+    for (int m = 0; m < nmol; ++m)
+        if (bp.ctxs[m] != ctxs[m] || bp.mults[m] != mults[m] || bp.ks[m] != ks[m] || bp.z[m] != z[m] ||
+            bp.sigma[m] != sigma[m])
+            return false;
+    return true;
+}
+
+int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
+                   const double* const* z, double* const* sigma, int nterms, cudaStream_t st,
+                   pprpa_ctx* owner, bool use_graph) {
+    BatchPlan* bp = (BatchPlan*)owner->batch_plan;
+    if (bp && use_graph && bp->exec && same_signature(*bp, nmol, ctxs, mults, ks, z, sigma, nterms, st)) {
+        PP_CUDA(cudaGraphLaunch(bp->exec, st));
+        count_launch(bp->graph_kernels);
+        return PPRPA_OK;
+    }
+    destroy_batch_plan(bp);
+    bp = new BatchPlan();
+    owner->batch_plan = bp;
+    bp->ctxs.assign(ctxs, ctxs + nmol);
+    bp->mults.assign(mults, mults + nmol);
+    bp->ks.assign(ks, ks + nmol);
+    bp->z.assign(z, z + nmol);
+    bp->sigma.assign(sigma, sigma + nmol);
+    bp->nterms = nterms;
+    bp->st = st;
+    bp->prs.resize(nmol);
+    std::vector<TcJobHost> s1, s2;
+    std::vector<std::vector<int2>> tiles;
+    std::vector<int> s2_tile_index;
+    for (int m = 0; m < nmol; ++m) {
+        pprpa_ctx* c = ctxs[m];
+        PP_TRY(tc_alloc(c, mults[m], ks[m], z[m], nterms, bp->prs[m], st));
+        if (bp->prs[m].pc < c->naux)
+            return set_error(PPRPA_ERR_ARG, "sigma_batch: a molecule's intermediate exceeds the T budget");
+        const size_t before = tiles.size(), s2_before = s2.size();
+        PP_TRY(tc_jobs(c, bp->prs[m], 0, c->naux, s1, s2, tiles));
+        for (size_t t = s2_before; t < s2.size(); ++t) s2_tile_index.push_back((int)(before + (t - s2_before)));
+    }
+    std::vector<TcJob> j1, j2;
+    std::vector<TcItem> i1, i2;
+    for (size_t j = 0; j < s1.size(); ++j) {
+        j1.push_back(s1[j].job);
+        append_items(s1[j].job.p, (int)j, nullptr, i1);
+        bp->bn1 = std::max(bp->bn1, s1[j].job.p.BN);
+    }
+    for (size_t j = 0; j < s2.size(); ++j) {
+        j2.push_back(s2[j].job);
+        append_items(s2[j].job.p, (int)j, &tiles[s2_tile_index[j]], i2);
+        bp->bn2 = std::max(bp->bn2, s2[j].job.p.BN);
+    }
+    bp->n1 = (int)i1.size();
+    bp->n2 = (int)i2.size();
+    PP_TRY(ws_get(owner, "batch_j1", sizeof(TcJob) * std::max<size_t>(1, j1.size()), (void**)&bp->dj1));
+    PP_TRY(ws_get(owner, "batch_j2", sizeof(TcJob) * std::max<size_t>(1, j2.size()), (void**)&bp->dj2));
+    PP_TRY(ws_get(owner, "batch_i1", sizeof(TcItem) * std::max<size_t>(1, i1.size()), (void**)&bp->di1));
+    PP_TRY(ws_get(owner, "batch_i2", sizeof(TcItem) * std::max<size_t>(1, i2.size()), (void**)&bp->di2));
+    if (!j1.empty()) {
+        PP_CUDA(cudaMemcpyAsync(bp->dj1, j1.data(), sizeof(TcJob) * j1.size(), cudaMemcpyHostToDevice, st));
+        PP_CUDA(cudaMemcpyAsync(bp->di1, i1.data(), sizeof(TcItem) * i1.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (!j2.empty()) {
+        PP_CUDA(cudaMemcpyAsync(bp->dj2, j2.data(), sizeof(TcJob) * j2.size(), cudaMemcpyHostToDevice, st));
+        PP_CUDA(cudaMemcpyAsync(bp->di2, i2.data(), sizeof(TcItem) * i2.size(), cudaMemcpyHostToDevice, st));
+    }
+    PP_CUDA(cudaStreamSynchronize(st));  // host vectors must outlive the copies
+    if (!use_graph) return batch_exec(*bp, owner);
+    const long long captured0 = pprpa_kernel_launches();
+    PP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_exec(*bp, owner);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    count_launch(captured0 - pprpa_kernel_launches());  // captured launches have not run
+    if (rc != PPRPA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return set_error(PPRPA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    bp->graph = g;
+    PP_CUDA(cudaGraphInstantiate(&bp->exec, g, 0));
+    size_t nnodes = 0;
+    PP_CUDA(cudaGraphGetNodes(g, nullptr, &nnodes));
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    PP_CUDA(cudaGraphGetNodes(g, nodes.data(), &nnodes));
+    int kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    bp->graph_kernels = kernels;
+    PP_CUDA(cudaGraphLaunch(bp->exec, st));
+    count_launch(kernels);
+    return PPRPA_OK;
+}
+
+// Autotuner: time the candidate tile widths of both stages on the context's own problem
+// (one sigma of k vectors each) and keep the fastest.
+int autotune_tiles(pprpa_ctx* c, int mult, int k, int nterms, int* bn_out) {
+    PairTable* pt;
+    PP_TRY(ensure_pairs(c, mult, &pt));
+    double *z, *sg;
+    PP_TRY(ws_get(c, "tune_z", sizeof(double) * (size_t)k * pt->N, (void**)&z));
+    PP_TRY(ws_get(c, "tune_s", sizeof(double) * (size_t)k * pt->N, (void**)&sg));
+    PP_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)k * pt->N, c->stream));
+    cudaEvent_t a, b;
+    PP_CUDA(cudaEventCreate(&a));
+    PP_CUDA(cudaEventCreate(&b));
+    const int sizes[2] = {c->nv, c->no};
+    int result[4] = {0, 0, 0, 0};
+    for (int stage = 1; stage <= 2; ++stage) {
+        for (int blk = 0; blk < 2; ++blk) {
+            const int sz = sizes[blk];
+            if (sz == 0) continue;
+            std::vector<int> cand;
+            const int szp = blk == 0 ? (int)round_up(c->nv, 8) : (int)round_up(c->no, 8);
+            if (stage == 1) {
+                for (int bn : {128, 192, 256}) cand.push_back(std::min(bn, (int)round_up((int64_t)k * szp, 16)));
+            } else {
+                cand.push_back(stage2_bn(sz));
+                for (int bn : {128, 192, 256}) cand.push_back(std::min(bn, (int)round_up(sz, 16)));
+            }
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            const std::string key = tune_key(stage, sz, k);
+            float best = 1e30f;
+            int best_bn = cand[0];
+            for (int bn : cand) {
+                c->tuned_bn[key] = bn;
+                PP_TRY(sigma_tc(c, mult, k, z, sg, nterms));  // warm
+                PP_CUDA(cudaEventRecord(a, c->stream));
+                PP_TRY(sigma_tc(c, mult, k, z, sg, nterms));
+                PP_CUDA(cudaEventRecord(b, c->stream));
+                PP_CUDA(cudaEventSynchronize(b));
+                float ms = 0.f;
+                PP_CUDA(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) { best = ms; best_bn = bn; }
+            }
+            c->tuned_bn[key] = best_bn;
+            result[(stage - 1) * 2 + blk] = best_bn;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (bn_out)
+        for (int i = 0; i < 4; ++i) bn_out[i] = result[i];
+    return check_status(c);
 }
 
 }  // namespace pprpa

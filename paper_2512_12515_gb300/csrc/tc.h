@@ -12,6 +12,7 @@ struct TcParams {
     int mode = 0;      // 0: stage 1 (BF16 T output), 1: stage 2 (FP32 atomic O output)
     int BN = 256;      // N tile (multiple of 16, <= 256)
     int stages = 0;    // set by the launcher
+    int slot_bn = 0;   // B-tile width the shared-memory slots and TMEM accumulators are sized for
     int tmem_cols = 0; // set by the launcher
     int total_items = 0;
     int kb_total = 0;  // 64-wide K blocks per work item before splitting
@@ -36,11 +37,23 @@ struct TcParams {
     float* O = nullptr;  // [k][n_pad][n_pad]
 };
 
+// Batched form: one job per (molecule, stage block); tensor maps and parameters in global
+// memory (64-byte aligned), one work item per output tile (and K slice).
+struct __align__(64) TcJob {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    TcParams p;
+};
+struct TcItem {
+    int job, m0, n0, batch, kb0, kb1;
+};
+
 int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
                    const uint64_t* strides_bytes, const uint32_t* box);
 int tc_stages_for(int BN, int nterms);
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms,
                    cudaStream_t st);
+int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_items, int max_bn,
+                           int nterms, int num_sms, int* status, cudaStream_t st);
 
 }  // namespace pprpa

@@ -102,3 +102,42 @@ def test_fp64_sigma_chunking_over_aux_index(pp, monkeypatch):
     ref = Z @ M.T
     assert np.abs(results[0] - ref).max() <= 1e-12 * np.abs(ref).max()
     assert np.abs(results[1] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_adjoint_gradient_full_size(pp, mult):
+    """FP64 adjoint at the 1500-function gradient workload: for a fixed pair vector z
+    (z^T W z = 1), d(z^T M z)/dL along random symmetric directions against the
+    oracle's central difference of the Rayleigh quotient (quadratic in L, so the
+    central difference is exact up to rounding), and d/d eps against its closed form
+    (the two-electron density diagonal, Sec. Density Matrix)."""
+    spec = synth.CONFIGS["c4"]
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], spec.nocc_act, spec.nvir_act)
+    eps = s["eps"][orb]
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    no, nv = spec.nocc_act, spec.nvir_act
+    nvv = len(oracle.pair_list(nv, mult))
+    noo = len(oracle.pair_list(no, mult))
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    z = synth.random_trial_vectors(nvv + noo, 1, 5)[0]
+    z[nvv:] *= 0.1
+    z /= np.sqrt(z @ (w * z))
+    with pp.Context(0) as c:
+        c.set_orbitals(s["occ"], s["eps"])
+        c.set_active(no, nv)
+        c.set_ao(s["C"], s["ao3c"])
+        dL, de = c.grad_vector(mult, z)
+    de_ref = oracle.two_e_density_diag(z, no, nv, mult)
+    assert np.abs(de - de_ref).max() <= 1e-12 * max(1.0, np.abs(de_ref).max())
+    rng = np.random.default_rng(9)
+    h = 1e-3
+    for _ in range(2):
+        D = rng.standard_normal(L.shape)
+        D = D + D.transpose(0, 2, 1)
+        D /= np.linalg.norm(D)
+        qp = z @ oracle.ri_sigma(eps, no, L + h * D, mult, z[None])[0]
+        qm = z @ oracle.ri_sigma(eps, no, L - h * D, mult, z[None])[0]
+        fd = (qp - qm) / (2 * h)
+        an = float(np.sum(dL * D))
+        assert abs(fd - an) <= 1e-8 * max(1.0, abs(an))
