@@ -218,6 +218,14 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
  * be NULL.  Host or device per `where`. */
 int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
 
+/* pprpa_grad_ec: gradient of the correlation energy E_c = sum(Omega^{N+2}) - Tr A
+ * (Eq. correlation_energy) of the last solve's multiplicity, with respect to L^P_pq
+ * (dL[naux][n][n], entries independent) and eps_p (deps[n]): the sum of every addition
+ * root's Hellmann-Feynman gradient minus the derivative of Tr A.  Needs a preceding FULL
+ * solve that returned every addition root (nroots = nvv); PPRPA_ERR_STATE otherwise.
+ * FP64 on the device; outputs host or device per `where`, either may be NULL. */
+int pprpa_grad_ec(pprpa_ctx* ctx, double* dL, double* deps, int where);
+
 /* pprpa_grad_vector: the same Hellmann-Feynman contraction for an explicit pair vector
  * z[N] of multiplicity `mult` (Sec. "Analytic Gradient": d(z^T M z)/d theta = z^T (dM/d theta) z),
  * i.e. the gradient of the Rayleigh quotient at fixed z; for a converged root normalised to

@@ -86,6 +86,7 @@ SIGNATURES = {
     "pprpa_solve": (_I, [_P, ctypes.POINTER(Options), _P, _P, _P, _P, ctypes.POINTER(Info)]),
     "pprpa_grad": (_I, [_P, _I, _P, _P, _I]),
     "pprpa_grad_vector": (_I, [_P, _I, _P, _P, _P, _I]),
+    "pprpa_grad_ec": (_I, [_P, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
@@ -294,6 +295,18 @@ class Context:
         t = (_I * 4)()
         _check(self.lib.pprpa_autotune(self._h, int(mult), int(k), int(precision), t))
         return list(t)
+
+    def grad_ec(self, dL=None, deps=None):
+        """dE_c/dL^P_pq and dE_c/d eps_p after a FULL solve with every addition root."""
+        n, naux, _, _ = self.dims(1)
+        if dL is None:
+            dL = np.empty((naux, n, n))
+        if deps is None:
+            deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        p1, w1 = _ptr(dL, True)
+        p2, w2 = _ptr(deps, True)
+        _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
+        return dL, deps
 
     def grad_vector(self, mult, z, dL=None, deps=None):
         """d(z^T M z)/dL^P_pq and d(z^T M z)/d eps_p for an explicit pair vector z."""

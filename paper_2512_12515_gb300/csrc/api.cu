@@ -455,6 +455,74 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
     return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, 1.0, dL, deps, where);
 }
 
+int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    PairTable* t;
+    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad_ec: no solve to differentiate");
+    PP_TRY(ensure_pairs(c, c->last_mult, &t));
+    if (!c->last_all_roots)
+        return set_error(PPRPA_ERR_STATE, "grad_ec: needs every addition root (a FULL solve with nroots = nvv)");
+    const int mult = c->last_mult, n = c->n(), naux = c->naux, nr = c->last_nroots;
+    const int64_t n2 = (int64_t)n * n;
+    cudaStream_t st = c->stream;
+    const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // d E_c = sum over addition roots of z^T (dM) z  -  d Tr A
+    if (deps) {
+        double* d;
+        PP_TRY(ws_get(c, "gec_eps", sizeof(double) * n, (void**)&d));
+        PP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
+        for (int r = 0; r < nr; ++r)
+            PP_TRY(launch_grad_eps(c->d_lastZ + (size_t)r * t->N, t->N, t->nvv, t->d_pp, t->d_pq, n, 1.0, d, st));
+        PP_TRY(launch_trace_a_grad(c->d_L, 0, n, c->no, mult, nullptr, d, st));
+        PP_CUDA(cudaMemcpyAsync(deps, d, sizeof(double) * n, kind, st));
+    }
+    if (dL) {
+        if ((double)nr * n2 * 8 > (double)(2LL << 30))
+            return set_error(PPRPA_ERR_ARG, "grad_ec: too many roots for the packed pair matrices");
+        double *Zt, *T, *out;
+        PP_TRY(ws_get(c, "gec_Zt", sizeof(double) * n2 * nr, (void**)&Zt));
+        PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2 * nr, st));
+        PP_TRY(launch_unpack_f64(c->d_lastZ, nr, t->N, t->d_pp, t->d_pq, n, mult, Zt, st));
+        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * n2)));
+        PP_TRY(ws_get(c, "gec_T", sizeof(double) * n2 * pc, (void**)&T));
+        if (where == PPRPA_DEVICE) out = dL;
+        else PP_TRY(ws_get(c, "gec_dL", sizeof(double) * n2 * pc, (void**)&out));
+        const double tsign = mult == 1 ? 1.0 : -1.0;
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = std::min(pc, naux - P0);
+            double* dst = where == PPRPA_DEVICE ? out + (size_t)P0 * n2 : out;
+            for (int r = 0; r < nr; ++r) {
+                const double* Zr = Zt + (size_t)r * n2;
+                Dgemm g1;  // T^P = L^P Zt_r
+                g1.M = n; g1.N = n; g1.K = n;
+                g1.A = c->d_L + (size_t)P0 * n2; g1.lda = n; g1.sA1 = n2;
+                g1.B = Zr; g1.ldb = n;
+                g1.C = T; g1.ldc = n; g1.sC1 = n2;
+                g1.nb1 = np;
+                PP_TRY(dgemm(g1, st));
+                Dgemm g2;  // dL^P (+)= t Zt_r T^P
+                g2.M = n; g2.N = n; g2.K = n;
+                g2.A = Zr; g2.lda = n;
+                g2.B = T; g2.ldb = n; g2.sB1 = n2;
+                g2.C = dst; g2.ldc = n; g2.sC1 = n2;
+                g2.nb1 = np;
+                g2.alpha = tsign;
+                g2.beta = r == 0 ? 0.0 : 1.0;
+                PP_TRY(dgemm(g2, st));
+            }
+            PP_TRY(launch_trace_a_grad(c->d_L + (size_t)P0 * n2, np, n, c->no, mult, dst, nullptr, st));
+            if (where == PPRPA_HOST) {
+                PP_CUDA(cudaMemcpyAsync(dL + (size_t)P0 * n2, out, sizeof(double) * n2 * np,
+                                        cudaMemcpyDeviceToHost, st));
+                PP_CUDA(cudaStreamSynchronize(st));
+            }
+        }
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
 int pprpa_grad_vector(pprpa_ctx* c, int mult, const double* z, double* dL, double* deps, int where) {
     PP_TRY(check_ctx(c));
     PP_TRY(need_L(c));

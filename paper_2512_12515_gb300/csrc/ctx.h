@@ -69,6 +69,7 @@ struct pprpa_ctx {
     int last_mult = 0;
     int last_nroots = 0;
     int last_N = 0;
+    bool last_all_roots = false;  // the last solve returned every addition root (FULL)
     double* d_lastZ = nullptr;
 
     int n() const { return no + nv; }

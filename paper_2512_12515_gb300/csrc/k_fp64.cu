@@ -573,3 +573,51 @@ int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st) {
 }
 
 }  // namespace pprpa
+
+namespace pprpa {
+
+// Derivatives of the two-electron part of Tr A (Sec. "ppRPA Equation"), subtracted from the
+// sum of root gradients to give d E_c (Eq. correlation_energy).  With
+// Tr A_2e = 1/2 sum_P [(tr_v L^P)^2 +- sum_{ab} (L^P_ab)^2] (+ singlet, - triplet):
+//   d Tr A / d L^P_xy = d_xy tr_v L^P +- L^P_xy  (x, y virtual), 0 otherwise;
+//   d Tr A / d eps_a  = nv + 1 (singlet) or nv - 1 (triplet) for virtual a.
+__global__ void trace_a_grad_kernel(const double* __restrict__ L, int n, int no, int mult,
+                                    double* __restrict__ dL) {
+    __shared__ double sh[32];
+    const int64_t P = blockIdx.x;
+    const double* Lp = L + P * (int64_t)n * n;
+    double* dp = dL + P * (int64_t)n * n;
+    double tr = 0.0;
+    for (int a = no + threadIdx.x; a < n; a += blockDim.x) tr += Lp[(int64_t)a * n + a];
+    tr = block_sum(tr, sh);
+    __shared__ double trv;
+    if (threadIdx.x == 0) trv = tr;
+    __syncthreads();
+    const double sg = mult == 1 ? 1.0 : -1.0;
+    const int nv = n - no;
+    for (int t = threadIdx.x; t < nv * nv; t += blockDim.x) {
+        const int x = no + t / nv, y = no + t % nv;
+        const int64_t o = (int64_t)x * n + y;
+        dp[o] -= (x == y ? trv : 0.0) + sg * Lp[o];
+    }
+}
+
+__global__ void trace_a_eps_kernel(int n, int no, int mult, double* deps) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= no && p < n) deps[p] -= (double)(n - no) + (mult == 1 ? 1.0 : -1.0);
+}
+
+int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, double* dL,
+                        double* deps, cudaStream_t st) {
+    if (dL && naux > 0) {
+        trace_a_grad_kernel<<<naux, 256, 0, st>>>(L, n, no, mult, dL);
+        PP_CHECK_LAUNCH();
+    }
+    if (deps) {
+        trace_a_eps_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, no, mult, deps);
+        PP_CHECK_LAUNCH();
+    }
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa

@@ -75,6 +75,8 @@ int launch_build_matrix(const double* eri, int n, const int* pp, const int* pq, 
 int launch_ec_sum(const double* omega, int nw, const double* D, int nvv, double* out,
                   cudaStream_t st);
 int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st);
+int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, double* dL,
+                        double* deps, cudaStream_t st);
 int launch_grad_eps(const double* z, int N, int nvv, const int* pp, const int* pq, int n,
                     double s, double* deps, cudaStream_t st);
 

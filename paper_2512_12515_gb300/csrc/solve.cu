@@ -213,6 +213,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     }
     PP_CUDA(cudaStreamSynchronize(st));
     PP_TRY(write_outputs(c, pt, o->nroots, coef, h_om.data(), omega, X, Y));
+    c->last_all_roots = o->nroots == nvv;
     tt.stop();
     if (info) {
         std::memset(info, 0, sizeof(*info));
@@ -509,6 +510,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     }
     if (mixed && stage == 1) stage = 2;  // not reached normally
     PP_TRY(write_outputs(c, pt, nroots, Zr, h_om.data(), omega, X, Y));
+    c->last_all_roots = false;
     t_all.stop();
     if (info) {
         info->iters = std::min(it, o->max_iter);

@@ -229,3 +229,34 @@ def test_davidson_unstable_problem(pp, mult, no, nv, naux, nb, seed, prec, tol):
     Z = np.hstack([res["X"], res["Y"]])
     resid = Z @ M.T - res["omega"][:, None] * (w[None, :] * Z)
     assert np.linalg.norm(resid, axis=1).max() <= (1e-6 if prec == "PREC_FP64" else 1e-4)
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_correlation_energy_gradient(pp, mult):
+    """dE_c/dL and dE_c/d eps (all addition roots of a full solve, minus d Tr A) against
+    the oracle's central difference of E_c (Eq. correlation_energy), h = 1e-4."""
+    spec, s, L, eps = make(3, 8, 12, 13)
+    no = 3
+    with gpu_ctx(pp, spec, s) as c:
+        _, _, nvv, noo = c.dims(mult)
+        c.solve(mult=mult, nroots=nvv, method=pp.METHOD_FULL, want_ec=True)
+        dL, de = c.grad_ec()
+
+    def ec(e, LL):
+        M, a, b = oracle.build_matrix(e, no, LL, mult)
+        return oracle.correlation_energy(M, a, b)[0]
+
+    h = 1e-4
+    for p in (0, 2, 5, 9):
+        ep, em = eps.copy(), eps.copy()
+        ep[p] += h
+        em[p] -= h
+        fd = (ec(ep, L) - ec(em, L)) / (2 * h)
+        assert abs(fd - de[p]) < 1e-6 * max(1.0, abs(fd))
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        D = rng.standard_normal(L.shape)
+        D = D + D.transpose(0, 2, 1)
+        D /= np.linalg.norm(D)
+        fd = (ec(eps, L + h * D) - ec(eps, L - h * D)) / (2 * h)
+        assert abs(fd - float(np.sum(dL * D))) < 1e-6 * max(1.0, abs(fd))
