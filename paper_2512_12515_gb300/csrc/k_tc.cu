@@ -120,6 +120,34 @@ __device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* m, int x
         : "memory");
 }
 
+// Multicast form: the box lands at the same shared-memory offset in every CTA of `mask`
+// and completes bytes on the mbarrier at the same offset in each of them.
+__device__ __forceinline__ void tma_2d_mc(uint32_t dst, const CUtensorMap* m, int x, int y,
+                                          uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
+        "cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (tcgen05 descriptor format, version 1).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -210,7 +238,9 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
 // items[i]; it names a job (one molecule and stage block) whose tensor maps and epilogue
 // parameters live in global memory, so molecules of different sizes and tile widths share
 // one persistent launch.  p.slot_bn sizes the shared-memory slots (the widest B tile).
-template <int NTERMS, bool BATCHED>
+// CL = 2 (stage 1, single launch only): the two CTAs of a cluster take neighbouring M
+// tiles of one N tile; each loads half of the shared B tile and multicasts it to both.
+template <int NTERMS, bool BATCHED, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                    const __grid_constant__ CUtensorMap tmA_lo,
@@ -235,11 +265,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + 2 + a); };
     const uint32_t done_bar = bar0 + 8u * (2 * TC_MAX_STAGES + 4);
 
+    const uint32_t crank = CL == 2 ? cluster_rank() : 0u;
+    // persistent loop bounds: work items, or item pairs (one per cluster) when CL = 2
+    const int first = CL == 2 ? (int)(blockIdx.x / 2) : (int)blockIdx.x;
+    const int stride = CL == 2 ? (int)(gridDim.x / 2) : (int)gridDim.x;
+    const int count = p.total_items;
     // work item -> (coordinates, parameters, tensor maps)
     auto fetch = [&](int item, ItemCoord& c, const TcParams*& q, const CUtensorMap*& mA_hi,
                      const CUtensorMap*& mA_lo, const CUtensorMap*& mB_hi,
                      const CUtensorMap*& mB_lo) {
-        if constexpr (BATCHED) {
+        if constexpr (CL == 2) {
+            q = &p;
+            mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
+            const int nb = item % p.tiles_n;
+            const int mp = item / p.tiles_n;
+            c.m0 = (2 * mp + (int)crank) * TC_BM;
+            c.n0 = nb * p.BN;
+            c.batch = 0;
+            c.kb0 = 0;
+            c.kb1 = p.kb_total;
+        } else if constexpr (BATCHED) {
             const TcItem it = items[item];
             const TcJob* jb = jobs + it.job;
             q = &jb->p;
@@ -256,7 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         abort_flag = 0;
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), 1);
+            mbar_init(empty_bar(s), CL);  // every CTA of the cluster releases a slot
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull_bar(a), 1);
@@ -276,6 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before multicast
     const uint32_t tmem_base = tmem_slot;
 
     if (warp == 4) {
@@ -286,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // last issued parity per slot (for draining on abort)
             uint32_t issued_mask = 0, issued_par = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
+            for (int item = first; item < count && ok; item += stride) {
                 ItemCoord c;
                 const TcParams* q;
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
@@ -307,10 +353,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (q->mode == 0) {
                         const int x = q->a_col_off + kb * TC_BK;
                         tma_2d(a_hi, mA_hi, x, c.m0, fb);
-                        tma_2d(b_hi, mB_hi, kb * TC_BK, c.n0, fb);
-                        if (NTERMS == 3) {
-                            tma_2d(a_lo, mA_lo, x, c.m0, fb);
-                            tma_2d(b_lo, mB_lo, kb * TC_BK, c.n0, fb);
+                        if constexpr (CL == 2) {
+                            // this CTA's half of the B tile, written into both CTAs
+                            const int hrows = q->BN / 2;
+                            const uint32_t hoff = crank * (uint32_t)hrows * (TC_BK * 2);
+                            tma_2d_mc(b_hi + hoff, mB_hi, kb * TC_BK, c.n0 + (int)crank * hrows, fb, 3);
+                            if (NTERMS == 3) {
+                                tma_2d(a_lo, mA_lo, x, c.m0, fb);
+                                tma_2d_mc(b_lo + hoff, mB_lo, kb * TC_BK, c.n0 + (int)crank * hrows, fb, 3);
+                            }
+                        } else {
+                            tma_2d(b_hi, mB_hi, kb * TC_BK, c.n0, fb);
+                            if (NTERMS == 3) {
+                                tma_2d(a_lo, mA_lo, x, c.m0, fb);
+                                tma_2d(b_lo, mB_lo, kb * TC_BK, c.n0, fb);
+                            }
                         }
                     } else {
                         const int P = kb / q->kq_blocks;
@@ -349,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < p.total_items && ok; item += gridDim.x) {
+            for (int item = first; item < count && ok; item += stride) {
                 ItemCoord c;
                 const TcParams* q;
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
@@ -379,7 +436,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             mma_bf16(dt, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
                         }
                     }
-                    mma_commit(empty_bar(stage));
+                    if constexpr (CL == 2) mma_commit_mc(empty_bar(stage), 3);
+                    else mma_commit(empty_bar(stage));
                     if (++stage == S) {
                         stage = 0;
                         phase ^= 1u;
@@ -401,7 +459,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         const int row = warp * 32 + lane;
-        for (int item = blockIdx.x; item < p.total_items; item += gridDim.x) {
+        for (int item = first; item < count; item += stride) {
             ItemCoord c;
             const TcParams* q;
             const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
@@ -485,6 +543,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // no CTA leaves while its peer may still write into its shared memory or barriers
+    if constexpr (CL == 2) cluster_sync_all();
     if (warp == 5) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -564,12 +624,68 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
     const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
     const int grid = p.total_items < num_sms ? p.total_items : num_sms;
     if (nterms == 3) {
-        cudaFuncSetAttribute(tc_gemm_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<3, false><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+        cudaFuncSetAttribute(tc_gemm_kernel<3, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<3, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
     } else {
-        cudaFuncSetAttribute(tc_gemm_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1, false><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+        cudaFuncSetAttribute(tc_gemm_kernel<1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
     }
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// Stage 1 on clusters of two CTAs sharing the B tile (TMA multicast).  Items are pairs of M
+// tiles; p.total_items is set here to the pair count.
+int tc_gemm_launch_cluster2(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
+                            const CUtensorMap& b_hi_half, const CUtensorMap& b_lo_half, TcParams p,
+                            int nterms, int num_sms, cudaStream_t st) {
+    if (p.mode != 0) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: stage 1 only");
+    if (p.BN < 32 || p.BN > 256 || (p.BN % 32) != 0)
+        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: BN must be a multiple of 32 in [32, 256]");
+    const int64_t mtiles = ceil_div(p.M_rows, TC_BM);
+    const int64_t pairs = ceil_div(mtiles, 2) * p.tiles_n;
+    if (pairs <= 0) return PPRPA_OK;
+    if (pairs > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: too many tiles");
+    p.total_items = (int)pairs;
+    p.slot_bn = p.BN;
+    p.stages = tc_stages_for(p.BN, nterms);
+    int cols = 32;
+    while (cols < 2 * p.BN) cols <<= 1;
+    p.tmem_cols = cols;
+    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
+    int clusters = (int)std::min<int64_t>(pairs, num_sms / 2);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const TcJob* nj = nullptr;
+    const TcItem* ni = nullptr;
+    cudaError_t e;
+    if (nterms == 3) {
+        cudaFuncSetAttribute(tc_gemm_kernel<3, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cfg.gridDim = dim3(2 * clusters);
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<3, false, 2>, &cfg) == cudaSuccess && maxc > 0)
+            clusters = std::min(clusters, maxc);
+        cfg.gridDim = dim3(2 * clusters);
+        e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<3, false, 2>, a_hi, a_lo, b_hi_half, b_lo_half, p, nj, ni);
+    } else {
+        cudaFuncSetAttribute(tc_gemm_kernel<1, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cfg.gridDim = dim3(2 * clusters);
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<1, false, 2>, &cfg) == cudaSuccess && maxc > 0)
+            clusters = std::min(clusters, maxc);
+        cfg.gridDim = dim3(2 * clusters);
+        e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, false, 2>, a_hi, a_lo, b_hi_half, b_lo_half, p, nj, ni);
+    }
+    if (e != cudaSuccess) return set_error(PPRPA_ERR_CUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
@@ -593,11 +709,11 @@ int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_ite
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     if (nterms == 3) {
-        cudaFuncSetAttribute(tc_gemm_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<3, true><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
+        cudaFuncSetAttribute(tc_gemm_kernel<3, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<3, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
     } else {
-        cudaFuncSetAttribute(tc_gemm_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1, true><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
+        cudaFuncSetAttribute(tc_gemm_kernel<1, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
     }
     PP_CHECK_LAUNCH();
     return PPRPA_OK;

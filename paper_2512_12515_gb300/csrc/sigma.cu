@@ -142,7 +142,7 @@ int stage2_bn(int valid) {
 // Launch with optional event timing (pprpa_profile).
 static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap& a_hi,
                         const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-                        const TcParams& p, int nterms) {
+                        const TcParams& p, int nterms, bool cluster = false) {
     ProfRec r;
     const bool rec = c->profile && c->prof.size() < 200000;
     if (rec) {
@@ -152,7 +152,8 @@ static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap&
         PP_CUDA(cudaEventCreate(&r.b));
         PP_CUDA(cudaEventRecord(r.a, c->stream));
     }
-    PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
+    if (cluster) PP_TRY(tc_gemm_launch_cluster2(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
+    else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
     if (rec) {
         PP_CUDA(cudaEventRecord(r.b, c->stream));
         c->prof.push_back(r);
@@ -188,6 +189,8 @@ struct TcJobHost {
     TcJob job;
     int kind = 0;        // profile row
     double flops = 0.0;  // algorithmic
+    bool cluster = false;                // stage 1 on two-CTA clusters sharing B (multicast)
+    CUtensorMap b_hi_half, b_lo_half;    // half-height B boxes for the cluster form
 };
 
 // Buffers (allocated on first use, sized for k vectors).
@@ -318,6 +321,13 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         p.total_items = (int)items;
         h.kind = split ? 2 : 0;
         h.flops = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
+        // two-CTA clusters share the B tile when there are enough M tiles to pair up
+        h.cluster = env_int("PPRPA_CLUSTER", 1) != 0 && BN % 32 == 0 && ceil_div(p.M_rows, 128) >= 2;
+        if (h.cluster) {
+            const uint32_t hbox[2] = {64, (uint32_t)(BN / 2)};
+            PP_TRY(make_tmap_bf16(&h.b_hi_half, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, hbox));
+            PP_TRY(make_tmap_bf16(&h.b_lo_half, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, hbox));
+        }
         s1.push_back(h);
     }
     for (int blk = 0; blk < 2; ++blk) {  // stage 2: O += T L on the upper triangle of a block
@@ -382,9 +392,14 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
         std::vector<TcJobHost> s1, s2;
         std::vector<std::vector<int2>> tiles;
         PP_TRY(tc_jobs(c, pr, P0, npc, s1, s2, tiles));
-        for (auto& h : s1)
-            PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi, h.job.b_lo,
-                                h.job.p, nterms));
+        for (auto& h : s1) {
+            if (h.cluster)
+                PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
+                                    h.b_lo_half, h.job.p, nterms, true));
+            else
+                PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
+                                    h.job.b_lo, h.job.p, nterms));
+        }
         for (size_t b = 0; b < s2.size(); ++b) {
             TcJobHost& h = s2[b];
             int2* d_tiles;
