@@ -238,8 +238,8 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
 // items[i]; it names a job (one molecule and stage block) whose tensor maps and epilogue
 // parameters live in global memory, so molecules of different sizes and tile widths share
 // one persistent launch.  p.slot_bn sizes the shared-memory slots (the widest B tile).
-// CL = 2 (stage 1, single launch only): the two CTAs of a cluster take neighbouring M
-// tiles of one N tile; each loads half of the shared B tile and multicasts it to both.
+// CL > 1 (stage 1, single launch only): the CL CTAs of a cluster take neighbouring M tiles
+// of one N tile; each loads 1/CL of the shared B tile and multicasts it to all of them.
 template <int NTERMS, bool BATCHED, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
@@ -265,21 +265,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * TC_MAX_STAGES + 2 + a); };
     const uint32_t done_bar = bar0 + 8u * (2 * TC_MAX_STAGES + 4);
 
-    const uint32_t crank = CL == 2 ? cluster_rank() : 0u;
-    // persistent loop bounds: work items, or item pairs (one per cluster) when CL = 2
-    const int first = CL == 2 ? (int)(blockIdx.x / 2) : (int)blockIdx.x;
-    const int stride = CL == 2 ? (int)(gridDim.x / 2) : (int)gridDim.x;
+    const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
+    // persistent loop bounds: work items, or groups of CL items (one per cluster)
+    const int first = (int)(blockIdx.x / CL);
+    const int stride = (int)(gridDim.x / CL);
     const int count = p.total_items;
     // work item -> (coordinates, parameters, tensor maps)
     auto fetch = [&](int item, ItemCoord& c, const TcParams*& q, const CUtensorMap*& mA_hi,
                      const CUtensorMap*& mA_lo, const CUtensorMap*& mB_hi,
                      const CUtensorMap*& mB_lo) {
-        if constexpr (CL == 2) {
+        if constexpr (CL > 1) {
             q = &p;
             mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
             const int nb = item % p.tiles_n;
             const int mp = item / p.tiles_n;
-            c.m0 = (2 * mp + (int)crank) * TC_BM;
+            c.m0 = (CL * mp + (int)crank) * TC_BM;
             c.n0 = nb * p.BN;
             c.batch = 0;
             c.kb0 = 0;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if constexpr (CL == 2) cluster_sync_all();  // peer barriers initialised before multicast
+    if constexpr (CL > 1) cluster_sync_all();  // peer barriers initialised before multicast
     const uint32_t tmem_base = tmem_slot;
 
     if (warp == 4) {
@@ -353,14 +353,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (q->mode == 0) {
                         const int x = q->a_col_off + kb * TC_BK;
                         tma_2d(a_hi, mA_hi, x, c.m0, fb);
-                        if constexpr (CL == 2) {
-                            // this CTA's half of the B tile, written into both CTAs
-                            const int hrows = q->BN / 2;
+                        if constexpr (CL > 1) {
+                            // this CTA's 1/CL of the B tile, written into every CTA of the cluster
+                            const int hrows = q->BN / CL;
                             const uint32_t hoff = crank * (uint32_t)hrows * (TC_BK * 2);
-                            tma_2d_mc(b_hi + hoff, mB_hi, kb * TC_BK, c.n0 + (int)crank * hrows, fb, 3);
+                            const uint16_t all = (uint16_t)((1u << CL) - 1u);
+                            tma_2d_mc(b_hi + hoff, mB_hi, kb * TC_BK, c.n0 + (int)crank * hrows, fb, all);
                             if (NTERMS == 3) {
                                 tma_2d(a_lo, mA_lo, x, c.m0, fb);
-                                tma_2d_mc(b_lo + hoff, mB_lo, kb * TC_BK, c.n0 + (int)crank * hrows, fb, 3);
+                                tma_2d_mc(b_lo + hoff, mB_lo, kb * TC_BK, c.n0 + (int)crank * hrows, fb, all);
                             }
                         } else {
                             tma_2d(b_hi, mB_hi, kb * TC_BK, c.n0, fb);
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             mma_bf16(dt, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
                         }
                     }
-                    if constexpr (CL == 2) mma_commit_mc(empty_bar(stage), 3);
+                    if constexpr (CL > 1) mma_commit_mc(empty_bar(stage), (uint16_t)((1u << CL) - 1u));
                     else mma_commit(empty_bar(stage));
                     if (++stage == S) {
                         stage = 0;
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     // no CTA leaves while its peer may still write into its shared memory or barriers
-    if constexpr (CL == 2) cluster_sync_all();
+    if constexpr (CL > 1) cluster_sync_all();
     if (warp == 5) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -634,30 +635,18 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
     return PPRPA_OK;
 }
 
-// Stage 1 on clusters of two CTAs sharing the B tile (TMA multicast).  Items are pairs of M
-// tiles; p.total_items is set here to the pair count.
-int tc_gemm_launch_cluster2(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
-                            const CUtensorMap& b_hi_half, const CUtensorMap& b_lo_half, TcParams p,
-                            int nterms, int num_sms, cudaStream_t st) {
-    if (p.mode != 0) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: stage 1 only");
-    if (p.BN < 32 || p.BN > 256 || (p.BN % 32) != 0)
-        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: BN must be a multiple of 32 in [32, 256]");
-    const int64_t mtiles = ceil_div(p.M_rows, TC_BM);
-    const int64_t pairs = ceil_div(mtiles, 2) * p.tiles_n;
-    if (pairs <= 0) return PPRPA_OK;
-    if (pairs > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster2: too many tiles");
-    p.total_items = (int)pairs;
-    p.slot_bn = p.BN;
-    p.stages = tc_stages_for(p.BN, nterms);
-    int cols = 32;
-    while (cols < 2 * p.BN) cols <<= 1;
-    p.tmem_cols = cols;
-    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
-    int clusters = (int)std::min<int64_t>(pairs, num_sms / 2);
+// Stage 1 on clusters of CL CTAs sharing the B tile (TMA multicast).  Items are groups of
+// CL M tiles; p.total_items is set here to the group count.  The B tensor maps must have
+// boxes of BN / CL rows.
+template <int NT, int CL>
+static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
+                                  const CUtensorMap& b_hi, const CUtensorMap& b_lo, const TcParams& p,
+                                  size_t smem, int groups, int num_sms, cudaStream_t st) {
+    cudaFuncSetAttribute(tc_gemm_kernel<NT, false, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(TC_THREADS);
@@ -665,25 +654,42 @@ int tc_gemm_launch_cluster2(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    int clusters = std::min(groups, num_sms / CL);
+    cfg.gridDim = dim3(CL * clusters);
+    int maxc = 0;
+    if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<NT, false, CL>, &cfg) == cudaSuccess && maxc > 0)
+        clusters = std::min(clusters, maxc);
+    cfg.gridDim = dim3(CL * clusters);
     const TcJob* nj = nullptr;
     const TcItem* ni = nullptr;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<NT, false, CL>, a_hi, a_lo, b_hi, b_lo, p, nj, ni);
+}
+
+int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
+                           const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
+                           int nterms, int cl, int num_sms, cudaStream_t st) {
+    if (p.mode != 0) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: stage 1 only");
+    if (cl != 2 && cl != 4) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: cluster size 2 or 4");
+    if (p.BN < 16 * cl || p.BN > 256 || (p.BN % (16 * cl)) != 0)
+        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: BN must be a multiple of 16 * cluster size");
+    const int64_t mtiles = ceil_div(p.M_rows, TC_BM);
+    const int64_t groups = ceil_div(mtiles, cl) * p.tiles_n;
+    if (groups <= 0) return PPRPA_OK;
+    if (groups > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: too many tiles");
+    p.total_items = (int)groups;
+    p.slot_bn = p.BN;
+    p.stages = tc_stages_for(p.BN, nterms);
+    int cols = 32;
+    while (cols < 2 * p.BN) cols <<= 1;
+    p.tmem_cols = cols;
+    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
     cudaError_t e;
     if (nterms == 3) {
-        cudaFuncSetAttribute(tc_gemm_kernel<3, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cfg.gridDim = dim3(2 * clusters);
-        int maxc = 0;
-        if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<3, false, 2>, &cfg) == cudaSuccess && maxc > 0)
-            clusters = std::min(clusters, maxc);
-        cfg.gridDim = dim3(2 * clusters);
-        e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<3, false, 2>, a_hi, a_lo, b_hi_half, b_lo_half, p, nj, ni);
+        e = cl == 2 ? launch_cluster<3, 2>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<3, 4>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
     } else {
-        cudaFuncSetAttribute(tc_gemm_kernel<1, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cfg.gridDim = dim3(2 * clusters);
-        int maxc = 0;
-        if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<1, false, 2>, &cfg) == cudaSuccess && maxc > 0)
-            clusters = std::min(clusters, maxc);
-        cfg.gridDim = dim3(2 * clusters);
-        e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<1, false, 2>, a_hi, a_lo, b_hi_half, b_lo_half, p, nj, ni);
+        e = cl == 2 ? launch_cluster<1, 2>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<1, 4>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
     }
     if (e != cudaSuccess) return set_error(PPRPA_ERR_CUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
     PP_CHECK_LAUNCH();

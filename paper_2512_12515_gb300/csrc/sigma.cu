@@ -142,7 +142,7 @@ int stage2_bn(int valid) {
 // Launch with optional event timing (pprpa_profile).
 static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap& a_hi,
                         const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-                        const TcParams& p, int nterms, bool cluster = false) {
+                        const TcParams& p, int nterms, int cluster = 1) {
     ProfRec r;
     const bool rec = c->profile && c->prof.size() < 200000;
     if (rec) {
@@ -152,7 +152,8 @@ static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap&
         PP_CUDA(cudaEventCreate(&r.b));
         PP_CUDA(cudaEventRecord(r.a, c->stream));
     }
-    if (cluster) PP_TRY(tc_gemm_launch_cluster2(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
+    if (cluster > 1)
+        PP_TRY(tc_gemm_launch_cluster(a_hi, a_lo, b_hi, b_lo, p, nterms, cluster, c->num_sms, c->stream));
     else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
     if (rec) {
         PP_CUDA(cudaEventRecord(r.b, c->stream));
@@ -189,8 +190,8 @@ struct TcJobHost {
     TcJob job;
     int kind = 0;        // profile row
     double flops = 0.0;  // algorithmic
-    bool cluster = false;                // stage 1 on two-CTA clusters sharing B (multicast)
-    CUtensorMap b_hi_half, b_lo_half;    // half-height B boxes for the cluster form
+    int cluster = 1;                     // stage 1 on clusters of this many CTAs sharing B
+    CUtensorMap b_hi_half, b_lo_half;    // B boxes of BN / cluster rows for the cluster form
 };
 
 // Buffers (allocated on first use, sized for k vectors).
@@ -321,10 +322,12 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         p.total_items = (int)items;
         h.kind = split ? 2 : 0;
         h.flops = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
-        // two-CTA clusters share the B tile when there are enough M tiles to pair up
-        h.cluster = env_int("PPRPA_CLUSTER", 1) != 0 && BN % 32 == 0 && ceil_div(p.M_rows, 128) >= 2;
-        if (h.cluster) {
-            const uint32_t hbox[2] = {64, (uint32_t)(BN / 2)};
+        // clusters of CTAs share the B tile when there are enough M tiles to group
+        int cl = env_int("PPRPA_CLUSTER", 4);
+        while (cl > 1 && (BN % (16 * cl) != 0 || ceil_div(p.M_rows, 128) < cl)) cl /= 2;
+        h.cluster = cl == 2 || cl == 4 ? cl : 1;
+        if (h.cluster > 1) {
+            const uint32_t hbox[2] = {64, (uint32_t)(BN / h.cluster)};
             PP_TRY(make_tmap_bf16(&h.b_hi_half, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, hbox));
             PP_TRY(make_tmap_bf16(&h.b_lo_half, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, hbox));
         }
@@ -393,9 +396,9 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
         std::vector<std::vector<int2>> tiles;
         PP_TRY(tc_jobs(c, pr, P0, npc, s1, s2, tiles));
         for (auto& h : s1) {
-            if (h.cluster)
+            if (h.cluster > 1)
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
-                                    h.b_lo_half, h.job.p, nterms, true));
+                                    h.b_lo_half, h.job.p, nterms, h.cluster));
             else
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
                                     h.job.b_lo, h.job.p, nterms));

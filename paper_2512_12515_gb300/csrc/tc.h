@@ -53,9 +53,9 @@ int tc_stages_for(int BN, int nterms);
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms,
                    cudaStream_t st);
-int tc_gemm_launch_cluster2(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
-                            const CUtensorMap& b_hi_half, const CUtensorMap& b_lo_half, TcParams p,
-                            int nterms, int num_sms, cudaStream_t st);
+int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
+                           const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
+                           int nterms, int cl, int num_sms, cudaStream_t st);
 int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_items, int max_bn,
                            int nterms, int num_sms, int* status, cudaStream_t st);
 
