@@ -222,6 +222,22 @@ def batch_bench(pp, torch, stream, nmol, nvec, steps, warmup):
             "autotuned_tiles_first4": tiles}
 
 
+def reduce_max(x, dist, device):
+    """Largest value of x over all ranks (the whole job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world, steps, k, f_vec, elapsed):
+    """Whole-job sigma TFLOP/s: every replica applies sigma to k vectors per step."""
+    return world * steps * k * f_vec / elapsed / 1e12
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,13 +316,9 @@ def main():
     clocks = clk.stop()
     launches = pp.kernel_launches() - launches0
     prof = c.profile(False)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([elapsed], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = reduce_max(ev0.elapsed_time(ev1) / 1e3, dist, device)
     ms_per_step = elapsed / args.steps * 1e3
-    value = world * args.steps * k * f_vec / elapsed / 1e12
+    value = replica_rate(world, args.steps, k, f_vec, elapsed)
 
     # roofline of the tensor-core GEMM (all its launches in the timed region)
     tot_ms = float(prof[:, 1].sum())

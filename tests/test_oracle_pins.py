@@ -307,3 +307,34 @@ def test_ao_to_mo_rows_matches_full_transform():
 
     got = oracle.ri_sigma_rows(eps, 3, None, 1, z, [0, 5, nvv + 1], Lrow=Lrow)
     assert np.allclose(got, (M @ z)[[0, 5, nvv + 1]], atol=1e-13)
+
+
+def test_synthetic_generator_becomes_unstable_as_nv_over_sqrt_naux_grows():
+    """The random part of <ab|cd> has variance ~0.0225/naux, so the A block spreads like
+    a semicircle of radius ~0.3 nv / sqrt(naux).  The small full-diagonalisation workload
+    (nv / sqrt(naux) = 1.8) is stable; analogues at 6.9 and 11.5 have complex roots, and at
+    11.5 the lowest real addition roots lie below every complex pair."""
+    def spectrum(no, nv, naux, nb, seed, mult=1):
+        spec = synth.SystemSpec("u", nb, no + 2, naux, no, nv, seed)
+        s = synth.make_system(spec)
+        orb = oracle.active_orbitals(s["occ"], no, nv)
+        L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+        M, nvv, noo = oracle.build_matrix(s["eps"][orb], no, L, mult)
+        w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+        vals, vecs = np.linalg.eig(w[:, None] * M)
+        nrm = np.einsum("ik,i,ik->k", vecs.real, w, vecs.real)
+        return vals, nrm
+
+    c0 = synth.CONFIGS["c0"]
+    s = synth.make_system(c0)
+    orb = oracle.active_orbitals(s["occ"], c0.nocc_act, c0.nvir_act)
+    L = oracle.ao_to_mo(s["ao3c"], s["C"], orb)
+    M, nvv, noo = oracle.build_matrix(s["eps"][orb], c0.nocc_act, L, 1)
+    assert not oracle.solve_full(M, nvv, noo)["unstable"]
+    vals, _ = spectrum(4, 24, 12, 32, 1)  # nv / sqrt(naux) = 6.9
+    assert np.abs(vals.imag).max() > 1e-3
+    vals, nrm = spectrum(4, 40, 12, 50, 1)  # nv / sqrt(naux) = 11.5
+    real = np.abs(vals.imag) < 1e-9
+    assert (~real).sum() >= 4
+    pp_real = np.sort(vals.real[real & (nrm > 0)])
+    assert pp_real[0] < vals.real[~real].min()
