@@ -167,16 +167,19 @@ def small_solve(pp, torch, stream):
         c.set_orbitals(s["occ"], s["eps"])
         c.set_active(spec.nocc_act, spec.nvir_act)
         c.set_ao(s["C"], s["ao3c"])
-        for name, prec, tol in (("fp64", pp.PREC_FP64, 1e-7), ("mixed", pp.PREC_BF16, 1e-5)):
+        for name, prec, tol in (("fp64", pp.PREC_FP64, 1e-7), ("mixed", pp.PREC_BF16, 1e-5),
+                                ("mixed_fp8", pp.PREC_FP8, 1e-5)):
             c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
             t0 = time.perf_counter()
             r = c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
             out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "omega": r["omega"],
                          "iters": r["info"]["iters"], "converged": r["info"]["converged"]}
     d = float(np.abs(out["mixed"]["omega"] - out["fp64"]["omega"]).max())
+    d8 = float(np.abs(out["mixed_fp8"]["omega"] - out["fp64"]["omega"]).max())
     for v in out.values():
         v["omega"] = [float(x) for x in v["omega"]]
     out["max_abs_domega_mixed_vs_fp64"] = d
+    out["max_abs_domega_mixed_fp8_vs_fp64"] = d8
     out["workload"] = "nbasis=40 nocc=5 nvir_act=20 naux=120 (stable), lowest 10 singlet N+2 roots"
     return out
 
@@ -249,6 +252,8 @@ def main():
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / solve side measurements")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
+                    help="form of the timed sigma: BF16 both stages, or E4M3 first stage")
     ap.add_argument("--batch-molecules", type=int, default=0,
                     help="also time the batched multi-molecule sigma over this many molecules")
     args = ap.parse_args()
@@ -289,8 +294,9 @@ def main():
     def step(prec):
         c.sigma(1, zd, prec, out=sd)
 
+    timed_prec = pp.PREC_FP8 if args.precision == "fp8" else pp.PREC_BF16
     for _ in range(max(3, args.warmup)):
-        step(pp.PREC_BF16)
+        step(timed_prec)
 
     def barrier():
         if dist is not None:
@@ -308,7 +314,7 @@ def main():
     torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for _ in range(args.steps):
-        step(pp.PREC_BF16)
+        step(timed_prec)
     ev1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -333,6 +339,14 @@ def main():
     peak_src = "of measured (sustained bf16)"
     if peak is None:
         peak, peak_src = 1700.0, "of fallback (sustained bf16)"
+    if args.precision == "fp8":
+        # stage 1 runs on E4M3 operands: its peak is the BF16 one times the nominal
+        # FP8/BF16 dense ratio (4.5 / 2.25); the step's peak is the rate at which both
+        # stages would finish at their own peaks
+        a1, a2 = float(prof[0, 2]), float(prof[1, 2])
+        if a1 + a2 > 0:
+            peak = (a1 + a2) / (a1 / (2.0 * peak) + a2 / peak)
+        peak_src += ", stage 1 x2 for E4M3 (nominal ratio)"
     achieved = alg / (tot_ms * 1e-3) / 1e12 if tot_ms > 0 else 0.0
     names = ["stage1 (T = L Zt)", "stage2 (O += T L)"]
     per_stage = {names[i]: {"launches": int(prof[i, 0]), "ms": float(prof[i, 1]),
@@ -342,12 +356,15 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "e4m3+bf16" if args.precision == "fp8" else "bf16",
         "data": "synthetic",
         "config": {"workload": f"{spec.name}: nbasis={spec.nbasis} nocc={spec.nocc} "
                                f"nocc_act={spec.nocc_act} nvir_act={spec.nvir_act} naux={spec.naux}; "
                                f"one step = sigma of a {k}-vector singlet Davidson block "
-                               "(BF16 tensor-core sandwich, FP32 accumulation, FP64 in/out)",
+                               + ("(E4M3 first stage, BF16 second stage" if args.precision == "fp8"
+                                  else "(BF16 tensor-core sandwich")
+                               + ", FP32 accumulation, FP64 in/out)",
                    "flops_per_vector": f_vec,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (BF16 L "
@@ -369,11 +386,11 @@ def main():
         zh = torch.from_numpy(z).pin_memory()
         sh = torch.empty_like(zh).pin_memory()
         for _ in range(1):
-            c.sigma(1, zh, pp.PREC_BF16, out=sh)
+            c.sigma(1, zh, timed_prec, out=sh)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            c.sigma(1, zh, pp.PREC_BF16, out=sh)
+            c.sigma(1, zh, timed_prec, out=sh)
             chk = float(sh[0, 0])  # the result is on the host
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         out["e2e"] = {"value": k * f_vec / e2e_s / 1e12, "unit": "TFLOP/s",
@@ -388,6 +405,14 @@ def main():
             torch.cuda.synchronize()
             t_split = time.perf_counter() - t0
             s_split = sd.cpu().numpy()
+            c.sigma(1, zd, pp.PREC_FP8, out=sd)  # first call quantises L to E4M3
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                c.sigma(1, zd, pp.PREC_FP8, out=sd)
+            torch.cuda.synchronize()
+            t_fp8 = (time.perf_counter() - t0) / 3
+            s_fp8 = sd.cpu().numpy()
             c.sigma(1, zd, pp.PREC_BF16, out=sd)
             s_bf16 = sd.cpu().numpy()
             z1 = zd[:1].contiguous()
@@ -401,10 +426,12 @@ def main():
             ref = np.abs(s64).max()
             out["precision_forms"] = {
                 "bf16x3_split_tflops": k * f_vec / t_split / 1e12,
+                "fp8_stage1_tflops": k * f_vec / t_fp8 / 1e12,
                 "fp64_tflops": f_vec / t64 / 1e12,
                 "fp64_ms_per_vector": t64 * 1e3,
                 "max_rel_err_vs_fp64": {"bf16": float(np.abs(s_bf16[0] - s64).max() / ref),
-                                        "bf16x3_split": float(np.abs(s_split[0] - s64).max() / ref)},
+                                        "bf16x3_split": float(np.abs(s_split[0] - s64).max() / ref),
+                                        "fp8_stage1": float(np.abs(s_fp8[0] - s64).max() / ref)},
             }
             out["solve_small"] = small_solve(pp, torch, lib_stream)
         if args.batch_molecules:

@@ -64,6 +64,7 @@ extern "C" {
 
 #define PPRPA_PREC_FP64 0       /* every contraction in FP64 */
 #define PPRPA_PREC_BF16 1       /* BF16 tensor-core sigma, then BF16x3 split sigma */
+#define PPRPA_PREC_FP8 2        /* FP8 (E4M3, per-P / per-vector scaled) first stage, then BF16x3 */
 
 #define PPRPA_CHANNEL_PP 0      /* lowest two-electron addition roots */
 
@@ -152,8 +153,10 @@ int pprpa_diag(pprpa_ctx* ctx, int mult, double* out, int where);
  * (the Davidson matrix-vector product of Sec. "ppRPA Equation", evaluated
  * as sum_P L^P Zt L^P with the pair packing of Zt).  precision selects
  * the contraction arithmetic: PPRPA_PREC_FP64, PPRPA_PREC_BF16 (BF16
- * operands, FP32 accumulation), or PPRPA_PREC_BF16 + 16 (BF16x3 split:
- * hi*hi + hi*lo + lo*hi).  Result is FP64.  Device or host per `where`. */
+ * operands, FP32 accumulation), PPRPA_PREC_BF16 + 16 (BF16x3 split:
+ * hi*hi + hi*lo + lo*hi), or PPRPA_PREC_FP8 (first product L^P Zt with E4M3
+ * operands scaled per P and per vector, second in BF16).  Result is FP64.
+ * Device or host per `where`. */
 int pprpa_sigma(pprpa_ctx* ctx, int mult, int precision, int k, const double* z,
                 double* sigma, int where);
 

@@ -14,6 +14,7 @@ from ._lib import (  # noqa: F401
     PREC_BF16,
     PREC_BF16_SPLIT,
     PREC_FP64,
+    PREC_FP8,
     PprpaError,
     SINGLET,
     TRIPLET,

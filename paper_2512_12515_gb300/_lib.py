@@ -22,7 +22,7 @@ ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE, ER
 HOST, DEVICE = 0, 1
 SINGLET, TRIPLET = 1, 3
 METHOD_FULL, METHOD_DAVIDSON = 0, 1
-PREC_FP64, PREC_BF16 = 0, 1
+PREC_FP64, PREC_BF16, PREC_FP8 = 0, 1, 2
 PREC_BF16_SPLIT = PREC_BF16 + 16  # sigma only: BF16x3 split products
 CHANNEL_PP = 0
 

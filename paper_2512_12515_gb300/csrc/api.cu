@@ -71,6 +71,11 @@ static void reset_integrals(pprpa_ctx* c) {
     if (c->d_Lhi) cudaFree(c->d_Lhi);
     if (c->d_Llo) cudaFree(c->d_Llo);
     if (c->d_lastZ) cudaFree(c->d_lastZ);
+    if (c->d_L8) cudaFree(c->d_L8);
+    if (c->d_L8scale) cudaFree(c->d_L8scale);
+    c->d_L8 = nullptr;
+    c->d_L8scale = nullptr;
+    c->fp8_ready = false;
     c->d_L = nullptr;
     c->d_Lhi = c->d_Llo = nullptr;
     c->d_lastZ = nullptr;
@@ -373,6 +378,7 @@ int pprpa_sigma(pprpa_ctx* c, int mult, int precision, int k, const double* z, d
     if (precision == PPRPA_PREC_FP64) rc = sigma_f64(c, mult, k, dz, ds);
     else if (precision == PPRPA_PREC_BF16) rc = sigma_tc(c, mult, k, dz, ds, 1);
     else if (precision == PPRPA_PREC_BF16 + 16) rc = sigma_tc(c, mult, k, dz, ds, 3);
+    else if (precision == PPRPA_PREC_FP8) rc = sigma_tc(c, mult, k, dz, ds, 1, true);
     else return set_error(PPRPA_ERR_ARG, "sigma: unknown precision");
     if (rc != PPRPA_OK) return rc;
     if (precision != PPRPA_PREC_FP64) PP_TRY(check_status(c));

@@ -53,6 +53,11 @@ struct pprpa_ctx {
     __nv_bfloat16* d_Lhi = nullptr;
     __nv_bfloat16* d_Llo = nullptr;
     bool bf16_ready = false;
+    // E4M3 copy of L (stage 1 of the FP8 form) and its per-P scales
+    void* d_L8 = nullptr;
+    float* d_L8scale = nullptr;
+    int ncol8 = 0, c_off8 = 0;
+    bool fp8_ready = false;
 
     int* d_status = nullptr;
     std::map<std::string, pprpa::DevBuf> ws;  // grow-only named workspaces
@@ -81,7 +86,9 @@ int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out);
 int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out);
 int ensure_bf16(pprpa_ctx* c);
 int sigma_f64(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma);
-int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms);
+int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms,
+             bool f8 = false);
+int ensure_fp8(pprpa_ctx* c);
 int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
                    const double* const* z, double* const* sigma, int nterms, cudaStream_t st,
                    pprpa_ctx* owner, bool use_graph);

@@ -3,6 +3,8 @@
 // GB300 has a small FP64 pipe, so these kernels aim at keeping it busy with
 // simple register tiling; everything here is either latency-bound (small
 // shapes) or HBM-bound (pair packing, diagonal, residuals).
+#include <cuda_fp8.h>
+
 #include "kernels.h"
 
 namespace pprpa {
@@ -617,6 +619,117 @@ int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, doub
         trace_a_eps_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, no, mult, deps);
         PP_CHECK_LAUNCH();
     }
+    return PPRPA_OK;
+}
+
+}  // namespace pprpa
+
+namespace pprpa {
+
+// ---------------------------------------------------------------------------
+// FP8 (E4M3) operands of the first sandwich stage.
+// L8[P][r][c8]: rows as the BF16 padded layout; columns occupied at [0, no), virtual at
+// [c_off8, c_off8 + nv) with c_off8 a multiple of 16 (so every TMA box starts 16-byte
+// aligned); scale[P] = max|L^P| / 448, L8 = e4m3(L / scale).
+__global__ void quantize_fp8_kernel(const double* __restrict__ L, int n, PadMap pm, int ncol8,
+                                    int c_off8, __nv_fp8_e4m3* __restrict__ L8,
+                                    float* __restrict__ scale) {
+    __shared__ double sh[32];
+    __shared__ double inv_sh;
+    const int64_t P = blockIdx.x;
+    const double* Lp = L + P * (int64_t)n * n;
+    double m = 0.0;
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) m = fmax(m, fabs(Lp[t]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, sh[w]);
+        const double sc = a > 0.0 ? a / 448.0 : 1.0;
+        scale[P] = (float)sc;
+        inv_sh = 1.0 / (double)(float)sc;
+    }
+    __syncthreads();
+    const double inv = inv_sh;
+    const int np = pm.n_pad;
+    __nv_fp8_e4m3* out = L8 + P * (int64_t)np * ncol8;
+    for (int64_t t = threadIdx.x; t < (int64_t)np * ncol8; t += blockDim.x) {
+        const int r = (int)(t / ncol8), c8 = (int)(t % ncol8);
+        const int p = r < pm.no ? r : ((r >= pm.no_p && r < pm.no_p + pm.nv) ? pm.no + r - pm.no_p : -1);
+        const int q = c8 < pm.no ? c8 : ((c8 >= c_off8 && c8 < c_off8 + pm.nv) ? pm.no + c8 - c_off8 : -1);
+        const double x = (p >= 0 && q >= 0) ? Lp[(int64_t)p * n + q] * inv : 0.0;
+        out[t] = __nv_fp8_e4m3((float)x);
+    }
+}
+
+int launch_quantize_fp8(const double* L, int naux, int n, PadMap pm, int ncol8, int c_off8,
+                        void* L8, float* scale, cudaStream_t st) {
+    if (naux <= 0) return PPRPA_OK;
+    quantize_fp8_kernel<<<naux, 256, 0, st>>>(L, n, pm, ncol8, c_off8, (__nv_fp8_e4m3*)L8, scale);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// zscale[j] = max over the packed pair matrix of vector j (sqrt(2) on singlet diagonals) / 448.
+__global__ void zscale_kernel(const double* __restrict__ z, int N, const int* __restrict__ pp,
+                              const int* __restrict__ pq, int mult, float* __restrict__ zscale) {
+    __shared__ double sh[32];
+    const int64_t j = blockIdx.x;
+    double m = 0.0;
+    for (int I = threadIdx.x; I < N; I += blockDim.x) {
+        double v = fabs(z[j * N + I]);
+        if (mult == 1 && pp[I] == pq[I]) v *= 1.4142135623730951;
+        m = fmax(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, sh[w]);
+        zscale[j] = a > 0.0 ? (float)(a / 448.0) : 1.0f;
+    }
+}
+
+// Same stacks as unpack_bf16 (Xs[j][c][d] = Zt_j[d][c], nv_p / no_p rows per vector) in E4M3,
+// each vector divided by its scale.  The caller zeroes the stacks.
+__global__ void unpack_fp8_kernel(const double* __restrict__ z, int k, int N, int nvv,
+                                  const int* __restrict__ pp, const int* __restrict__ pq,
+                                  PadMap pm, int mult, const float* __restrict__ zscale,
+                                  __nv_fp8_e4m3* __restrict__ xs, int ldx,
+                                  __nv_fp8_e4m3* __restrict__ ys, int ldy) {
+    const int64_t total = (int64_t)k * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int I = t % N;
+        const int64_t j = t / N;
+        const double inv = 1.0 / (double)zscale[j];
+        const double v = z[t] * inv;
+        int p = pp[I], q = pq[I];
+        __nv_fp8_e4m3* st;
+        int64_t rows, ld;
+        if (I < nvv) { p -= pm.no; q -= pm.no; st = xs; rows = pm.nv_p; ld = ldx; }
+        else { st = ys; rows = pm.no_p; ld = ldy; }
+        const int64_t base = j * rows * ld;
+        double zpq, zqp;
+        if (mult == 1) { zpq = (p == q) ? 1.4142135623730951 * v : v; zqp = zpq; }
+        else { zpq = v; zqp = -v; }
+        st[base + (int64_t)q * ld + p] = __nv_fp8_e4m3((float)zpq);
+        if (p != q) st[base + (int64_t)p * ld + q] = __nv_fp8_e4m3((float)zqp);
+    }
+}
+
+int launch_unpack_fp8(const double* z, int k, int N, int nvv, const int* pp, const int* pq,
+                      PadMap pm, int mult, float* zscale, void* xs, int ldx, void* ys, int ldy,
+                      cudaStream_t st) {
+    if (!k || !N) return PPRPA_OK;
+    zscale_kernel<<<k, 256, 0, st>>>(z, N, pp, pq, mult, zscale);
+    PP_CHECK_LAUNCH();
+    const int64_t total = (int64_t)k * N;
+    unpack_fp8_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(
+        z, k, N, nvv, pp, pq, pm, mult, zscale, (__nv_fp8_e4m3*)xs, ldx, (__nv_fp8_e4m3*)ys, ldy);
+    PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
 

@@ -36,8 +36,14 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;  // one 128-byte swizzle row of BF16
-constexpr int TC_THREADS = 192;
+// Warp roles: warps 0-7 epilogue (warp w reads TMEM lanes 32 * (w % 4) and one half of the
+// tile's columns), warp 8 TMA producer, warp 9 MMA issuer and TMEM owner.
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_PRODUCER_WARP = 8;
+constexpr int TC_MMA_WARP = 9;
+constexpr int TC_THREADS = 32 * (TC_EPI_WARPS + 2);
 constexpr int TC_SMEM_LIMIT = 227 * 1024;
+constexpr int TC_EPI_BYTES = TC_EPI_WARPS * 32 * 128;  // stage-1 output staging
 constexpr unsigned long long TC_WAIT_NS = 4000000000ull;  // 4 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -174,6 +180,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 x E4M3 -> FP32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -187,8 +208,9 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// Two 16-column loads in flight before one wait (the second only when `two`; warp-uniform).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, bool two, float (&v)[32]) {
+    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
         "%11, %12, %13, %14, %15}, [%16];"
@@ -196,9 +218,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+    if (two) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + 16u));
+    } else {
+#pragma unroll
+        for (int i = 16; i < 32; ++i) r[i] = 0u;
+    }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 struct ItemCoord {
@@ -240,7 +274,9 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
 // one persistent launch.  p.slot_bn sizes the shared-memory slots (the widest B tile).
 // CL > 1 (stage 1, single launch only): the CL CTAs of a cluster take neighbouring M tiles
 // of one N tile; each loads 1/CL of the shared B tile and multicasts it to all of them.
-template <int NTERMS, bool BATCHED, int CL>
+// F8: stage-1 operands are E4M3 (kind::f8f6f4, 128 elements per 128-byte row); the
+// epilogue multiplies by the row (per auxiliary index) and column (per vector) scales.
+template <int NTERMS, bool BATCHED, int CL, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                    const __grid_constant__ CUtensorMap tmA_lo,
@@ -253,6 +289,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ volatile int abort_flag;
 
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int BKE = F8 ? 2 * TC_BK : TC_BK;  // elements per 128-byte K block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.stages;
     const uint32_t a_bytes = TC_BM * TC_BK * 2;
@@ -305,12 +342,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull_bar(a), 1);
-            mbar_init(tempty_bar(a), 128);
+            mbar_init(tempty_bar(a), 32 * TC_EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == TC_MMA_WARP) {
         const uint32_t ncols = p.tmem_cols;
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
@@ -324,7 +361,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if constexpr (CL > 1) cluster_sync_all();  // peer barriers initialised before multicast
     const uint32_t tmem_base = tmem_slot;
 
-    if (warp == 4) {
+    if (warp == TC_PRODUCER_WARP) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             int stage = 0;
@@ -351,23 +388,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t a_lo = sbase + a_bytes + b_slot,
                                    b_lo = sbase + 2 * a_bytes + b_slot;
                     if (q->mode == 0) {
-                        const int x = q->a_col_off + kb * TC_BK;
+                        const int x = q->a_col_off + kb * BKE;
                         tma_2d(a_hi, mA_hi, x, c.m0, fb);
                         if constexpr (CL > 1) {
                             // this CTA's 1/CL of the B tile, written into every CTA of the cluster
                             const int hrows = q->BN / CL;
                             const uint32_t hoff = crank * (uint32_t)hrows * (TC_BK * 2);
                             const uint16_t all = (uint16_t)((1u << CL) - 1u);
-                            tma_2d_mc(b_hi + hoff, mB_hi, kb * TC_BK, c.n0 + (int)crank * hrows, fb, all);
+                            tma_2d_mc(b_hi + hoff, mB_hi, kb * BKE, c.n0 + (int)crank * hrows, fb, all);
                             if (NTERMS == 3) {
                                 tma_2d(a_lo, mA_lo, x, c.m0, fb);
-                                tma_2d_mc(b_lo + hoff, mB_lo, kb * TC_BK, c.n0 + (int)crank * hrows, fb, all);
+                                tma_2d_mc(b_lo + hoff, mB_lo, kb * BKE, c.n0 + (int)crank * hrows, fb, all);
                             }
                         } else {
-                            tma_2d(b_hi, mB_hi, kb * TC_BK, c.n0, fb);
+                            tma_2d(b_hi, mB_hi, kb * BKE, c.n0, fb);
                             if (NTERMS == 3) {
                                 tma_2d(a_lo, mA_lo, x, c.m0, fb);
-                                tma_2d(b_lo, mB_lo, kb * TC_BK, c.n0, fb);
+                                tma_2d(b_lo, mB_lo, kb * BKE, c.n0, fb);
                             }
                         }
                     } else {
@@ -399,7 +436,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == TC_MMA_WARP) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             int stage = 0;
@@ -413,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
                 fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
                 const int bn = q->BN;
-                const uint32_t idesc = idesc_bf16(bn);
+                const uint32_t idesc = F8 ? idesc_e4m3(bn) : idesc_bf16(bn);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(acc * p.slot_bn);
@@ -431,6 +468,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int k = 0; k < TC_BK / 16; ++k) {
                         const uint32_t off = k * 32;
                         const uint32_t first = (kb == c.kb0 && k == 0) ? 0u : 1u;
+                        if constexpr (F8) {
+                            mma_e4m3(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
+                            continue;
+                        }
                         mma_bf16(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
                         if (NTERMS == 3) {
                             mma_bf16(dt, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
@@ -456,64 +497,164 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue (warps 0-3, TMEM lanes 32*warp ..) ----------------
+        // ---------------- epilogue (warps 0-7) ----------------
+        // warp w reads TMEM lanes 32 * (w % 4) .. + 31 (one output row per thread) and the
+        // columns [cbeg, cend) of its half of the tile
+        const int quarter = warp & 3, half = warp >> 2;
         int acc = 0;
         uint32_t acc_phase = 0;
-        const int row = warp * 32 + lane;
+        const int row = quarter * 32 + lane;
         for (int item = first; item < count; item += stride) {
             ItemCoord c;
             const TcParams* q;
             const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
             fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
             const int bn = q->BN;
+            const int bn2 = ((bn / 2) + 15) / 16 * 16;  // half-tile split on a 16-column boundary
+            const int cbeg = half == 0 ? 0 : bn2, cend = half == 0 ? min(bn2, bn) : bn;
             if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status)) break;
             tc_fence_after();
             const uint32_t tbase =
-                tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * p.slot_bn);
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * p.slot_bn);
             if (q->mode == 0) {
                 const int64_t R = (int64_t)c.m0 + row;
                 const bool rok = R < q->M_rows;
                 const int n_per_j = q->n_per_j, n_total = q->n_total, k_vec = q->k_vec;
-                const int t_col_off = q->t_col_off;
                 const int64_t n_pad = q->n_pad;
-                __nv_bfloat16* t_hi = q->t_hi;
-                __nv_bfloat16* t_lo = q->t_lo;
-                for (int c0 = 0; c0 < bn; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tbase + c0, v);
+                // this row's output: T[R][j][t_col_off + cc]
+                __nv_bfloat16* t_hi = q->t_hi + R * k_vec * n_pad + q->t_col_off;
+                __nv_bfloat16* t_lo = NTERMS == 3 ? q->t_lo + R * k_vec * n_pad + q->t_col_off : nullptr;
+                const float rs = (F8 && rok) ? q->row_scale[R / n_pad] : 1.0f;
+                const bool aligned = (q->t_col_off & 7) == 0 && (n_per_j & 7) == 0;
+                // 8-column groups never straddle two vectors (n_per_j is a multiple of 8), so
+                // the vector j and the column cc inside it advance group by group
+                int n = c.n0 + cbeg;
+                int j = n / n_per_j;
+                int cc = n - j * n_per_j;
+                if (p.epi_stage && aligned) {
+                    // Coalesced form.  Per 64-column chunk each lane packs its row into the
+                    // warp's staging tile (32 rows x 128 bytes, 16-byte slot g of row r at
+                    // slot g ^ (r & 7), so that neither pass has bank conflicts), then the warp
+                    // writes 4 rows x 128 contiguous bytes per store instruction.
+                    uint8_t* stg = smem + (size_t)S * slot_bytes + (size_t)warp * (32 * 128);
+                    const int64_t R0 = (int64_t)c.m0 + quarter * 32;
+                    const int gl = lane & 7;  // the 16-byte group this lane stores in the row pass
+                    __nv_bfloat16* t_hi0 = q->t_hi + q->t_col_off;
+                    __nv_bfloat16* t_lo0 = NTERMS == 3 ? q->t_lo + q->t_col_off : nullptr;
+                    for (int c0 = cbeg; c0 < cend; c0 += 64) {
+                        uint32_t lo_w[NTERMS == 3 ? 8 : 1][4];
+#pragma unroll
+                        for (int hc = 0; hc < 2; ++hc) {
+                            const int cb = c0 + 32 * hc;
+                            float v[32];
+                            if (cb < cend) tmem_ld32(tbase + cb, cb + 16 < cend, v);
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const int g = 4 * hc + h;
+                                const float sc = (F8 && n < n_total) ? rs * q->col_scale[j] : 1.0f;
+                                uint4 hv;
+                                uint32_t* hw = (uint32_t*)&hv;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    float x0 = v[8 * h + 2 * e], x1 = v[8 * h + 2 * e + 1];
+                                    if (F8) {
+                                        x0 *= sc;
+                                        x1 *= sc;
+                                    }
+                                    const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+                                    hw[e] = *(const uint32_t*)&hb;
+                                    if constexpr (NTERMS == 3) {
+                                        const float2 hf = __bfloat1622float2(hb);
+                                        const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                                        lo_w[g][e] = *(const uint32_t*)&lb;
+                                    }
+                                }
+                                if (cb < cend)
+                                    *(uint4*)(stg + lane * 128 + ((g ^ (lane & 7)) << 4)) = hv;
+                                n += 8;
+                                cc += 8;
+                                if (cc >= n_per_j) {
+                                    cc -= n_per_j;
+                                    ++j;
+                                }
+                            }
+                        }
+                        // row pass: lane writes group gl of rows 4 i + lane / 8
+                        const int ng = c.n0 + c0 + 8 * gl;
+                        const bool gok = c0 + 8 * gl < cend && ng < n_total;
+                        const int jg = ng / n_per_j;
+                        const int64_t cg = (int64_t)jg * n_pad + (ng - jg * n_per_j);
+#pragma unroll
+                        for (int t = 0; t < (NTERMS == 3 ? 2 : 1); ++t) {
+                            if (t == 1) {
+#pragma unroll
+                                for (int g = 0; g < 8; ++g)
+                                    if constexpr (NTERMS == 3)
+                                        *(uint4*)(stg + lane * 128 + ((g ^ (lane & 7)) << 4)) =
+                                            make_uint4(lo_w[g][0], lo_w[g][1], lo_w[g][2], lo_w[g][3]);
+                            }
+                            __syncwarp();
+                            __nv_bfloat16* dst = t == 0 ? t_hi0 : t_lo0;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int r = 4 * i + (lane >> 3);
+                                const uint4 val = *(const uint4*)(stg + r * 128 + ((gl ^ (r & 7)) << 4));
+                                const int64_t R = R0 + r;
+                                if (gok && R < q->M_rows) *(uint4*)(dst + R * k_vec * n_pad + cg) = val;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                } else
+                for (int c0 = cbeg; c0 < cend; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tbase + c0, c0 + 16 < cend, v);
                     if (!rok) continue;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int n = c.n0 + c0 + 8 * h;
-                        if (n >= n_total) continue;
-                        const int j = n / n_per_j;
-                        const int cc = n - j * n_per_j;
-                        const int qc = t_col_off + cc;
-                        const int64_t base = (R * k_vec + j) * n_pad;
-                        const bool vec = (cc + 8 <= n_per_j) && (n + 8 <= n_total) && ((qc & 7) == 0);
-                        if (vec) {
-                            __align__(16) __nv_bfloat16 hb[8];
-                            __align__(16) __nv_bfloat16 lb[8];
+                    for (int h = 0; h < 4; ++h) {
+                        if (c0 + 8 * h < cend && n < n_total) {
+                            const float sc = F8 ? rs * q->col_scale[j] : 1.0f;
+                            const int64_t off = (int64_t)j * n_pad + cc;
+                            if (aligned) {
+                                uint4 hv, lv;
+                                uint32_t* hw = (uint32_t*)&hv;
+                                uint32_t* lw = (uint32_t*)&lv;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const float x = v[8 * h + e];
-                                hb[e] = __float2bfloat16_rn(x);
-                                lb[e] = __float2bfloat16_rn(x - __bfloat162float(hb[e]));
+                                for (int e = 0; e < 4; ++e) {
+                                    float x0 = v[8 * h + 2 * e], x1 = v[8 * h + 2 * e + 1];
+                                    if (F8) {
+                                        x0 *= sc;
+                                        x1 *= sc;
+                                    }
+                                    const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+                                    hw[e] = *(const uint32_t*)&hb;
+                                    if (NTERMS == 3) {
+                                        const float2 hf = __bfloat1622float2(hb);
+                                        const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                                        lw[e] = *(const uint32_t*)&lb;
+                                    }
+                                }
+                                *(uint4*)(t_hi + off) = hv;
+                                if (NTERMS == 3) *(uint4*)(t_lo + off) = lv;
+                            } else {
+                                for (int e = 0; e < 8; ++e) {
+                                    const int ne = n + e;
+                                    if (ne >= n_total) break;
+                                    const int je = ne / n_per_j;
+                                    const int ce = ne - je * n_per_j;
+                                    const int64_t o = (int64_t)je * n_pad + ce;
+                                    const float x = F8 ? v[8 * h + e] * rs * q->col_scale[je] : v[8 * h + e];
+                                    const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+                                    t_hi[o] = hb;
+                                    if (NTERMS == 3) t_lo[o] = __float2bfloat16_rn(x - __bfloat162float(hb));
+                                }
                             }
-                            *(uint4*)(t_hi + base + qc) = *(const uint4*)hb;
-                            if (NTERMS == 3) *(uint4*)(t_lo + base + qc) = *(const uint4*)lb;
-                        } else {
-                            for (int e = 0; e < 8; ++e) {
-                                const int ne = n + e;
-                                if (ne >= n_total) break;
-                                const int je = ne / n_per_j;
-                                const int ce = ne - je * n_per_j;
-                                const int64_t off = (R * k_vec + je) * n_pad + t_col_off + ce;
-                                const float x = v[8 * h + e];
-                                const __nv_bfloat16 hv = __float2bfloat16_rn(x);
-                                t_hi[off] = hv;
-                                if (NTERMS == 3) t_lo[off] = __float2bfloat16_rn(x - __bfloat162float(hv));
-                            }
+                        }
+                        n += 8;
+                        cc += 8;
+                        if (cc >= n_per_j) {
+                            cc -= n_per_j;
+                            ++j;
                         }
                     }
                 }
@@ -523,14 +664,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int n_valid = q->n_valid;
                 float* Ob = q->O + (int64_t)c.batch * q->n_pad * q->n_pad +
                             (int64_t)(q->row_off + a) * q->n_pad + q->col_off;
-                for (int c0 = 0; c0 < bn; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tbase + c0, v);
+                for (int c0 = cbeg; c0 < cend; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tbase + c0, c0 + 16 < cend, v);
                     if (!rok) continue;
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
+                    for (int e = 0; e < 32; ++e) {
                         const int b = c.n0 + c0 + e;
-                        if (b < n_valid) atomicAdd(Ob + b, v[e]);
+                        if (c0 + e < cend && b < n_valid) atomicAdd(Ob + b, v[e]);
                     }
                 }
             }
@@ -546,7 +687,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     // no CTA leaves while its peer may still write into its shared memory or barriers
     if constexpr (CL > 1) cluster_sync_all();
-    if (warp == 5) {
+    if (warp == TC_MMA_WARP) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                      "r"((uint32_t)p.tmem_cols)
@@ -579,6 +720,11 @@ EncodeTiledFn encode_fn() {
 
 int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
                    const uint64_t* strides_bytes, const uint32_t* box) {
+    return make_tmap(map, ptr, rank, dims, strides_bytes, box, 2);
+}
+
+int make_tmap(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
+              const uint64_t* strides_bytes, const uint32_t* box, int elt_bytes) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return set_error(PPRPA_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if (((uintptr_t)ptr & 15) != 0) return set_error(PPRPA_ERR_ARG, "tensor map base not 16-byte aligned");
@@ -593,16 +739,17 @@ int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* 
             if (s[i] % 16 != 0) return set_error(PPRPA_ERR_ARG, "tensor map stride not a multiple of 16 bytes");
         }
     }
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(ptr),
+    const CUtensorMapDataType dt = elt_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(map, dt, (cuuint32_t)rank, const_cast<void*>(ptr),
                     d, s, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(PPRPA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return PPRPA_OK;
 }
 
-int tc_stages_for(int BN, int nterms) {
+int tc_stages_for(int BN, int nterms, bool epi_stage) {
     const int slot = (TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
-    int s = (TC_SMEM_LIMIT - 2048) / slot;
+    int s = (TC_SMEM_LIMIT - 2048 - (epi_stage ? TC_EPI_BYTES : 0)) / slot;
     if (s > TC_MAX_STAGES) s = TC_MAX_STAGES;
     return s;
 }
@@ -611,20 +758,32 @@ static int slot_bytes_for(int BN, int nterms) {
     return (TC_BM * TC_BK * 2 + BN * TC_BK * 2) * (nterms == 3 ? 2 : 1);
 }
 
+// Pipeline depth and dynamic shared memory of a launch; the stage-1 staging tiles are
+// reserved when `want_epi` and at least two pipeline slots still fit.
+static size_t plan_smem(TcParams& p, int bn, int nterms, bool want_epi) {
+    p.epi_stage = want_epi && tc_stages_for(bn, nterms, true) >= 2 ? 1 : 0;
+    p.stages = tc_stages_for(bn, nterms, p.epi_stage != 0);
+    return (size_t)slot_bytes_for(bn, nterms) * p.stages + 1024 + (p.epi_stage ? TC_EPI_BYTES : 0);
+}
+
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
-                   const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st) {
+                   const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st,
+                   bool f8) {
     if (p.total_items <= 0) return PPRPA_OK;
     if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0)
         return set_error(PPRPA_ERR_ARG, "tc_gemm: BN must be a multiple of 16 in [16, 256]");
     p.slot_bn = p.BN;
-    p.stages = tc_stages_for(p.BN, nterms);
+    const size_t smem = plan_smem(p, p.BN, nterms, p.mode == 0);
     if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * p.BN) cols <<= 1;
     p.tmem_cols = cols;
-    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
     const int grid = p.total_items < num_sms ? p.total_items : num_sms;
-    if (nterms == 3) {
+    if (f8) {
+        if (p.mode != 0 || nterms != 1) return set_error(PPRPA_ERR_ARG, "tc_gemm: FP8 is stage 1, one term");
+        cudaFuncSetAttribute(tc_gemm_kernel<1, false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc_gemm_kernel<1, false, 1, true><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+    } else if (nterms == 3) {
         cudaFuncSetAttribute(tc_gemm_kernel<3, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         tc_gemm_kernel<3, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
     } else {
@@ -638,11 +797,11 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
 // Stage 1 on clusters of CL CTAs sharing the B tile (TMA multicast).  Items are groups of
 // CL M tiles; p.total_items is set here to the group count.  The B tensor maps must have
 // boxes of BN / CL rows.
-template <int NT, int CL>
+template <int NT, int CL, bool F8 = false>
 static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                                   const CUtensorMap& b_hi, const CUtensorMap& b_lo, const TcParams& p,
                                   size_t smem, int groups, int num_sms, cudaStream_t st) {
-    cudaFuncSetAttribute(tc_gemm_kernel<NT, false, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(tc_gemm_kernel<NT, false, CL, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -657,17 +816,17 @@ static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_
     int clusters = std::min(groups, num_sms / CL);
     cfg.gridDim = dim3(CL * clusters);
     int maxc = 0;
-    if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<NT, false, CL>, &cfg) == cudaSuccess && maxc > 0)
+    if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<NT, false, CL, F8>, &cfg) == cudaSuccess && maxc > 0)
         clusters = std::min(clusters, maxc);
     cfg.gridDim = dim3(CL * clusters);
     const TcJob* nj = nullptr;
     const TcItem* ni = nullptr;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<NT, false, CL>, a_hi, a_lo, b_hi, b_lo, p, nj, ni);
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<NT, false, CL, F8>, a_hi, a_lo, b_hi, b_lo, p, nj, ni);
 }
 
 int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
-                           int nterms, int cl, int num_sms, cudaStream_t st) {
+                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8) {
     if (p.mode != 0) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: stage 1 only");
     if (cl != 2 && cl != 4) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: cluster size 2 or 4");
     if (p.BN < 16 * cl || p.BN > 256 || (p.BN % (16 * cl)) != 0)
@@ -678,13 +837,17 @@ int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
     if (groups > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: too many tiles");
     p.total_items = (int)groups;
     p.slot_bn = p.BN;
-    p.stages = tc_stages_for(p.BN, nterms);
+    const size_t smem = plan_smem(p, p.BN, nterms, true);
+    if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * p.BN) cols <<= 1;
     p.tmem_cols = cols;
-    const size_t smem = (size_t)slot_bytes_for(p.BN, nterms) * p.stages + 1024;
     cudaError_t e;
-    if (nterms == 3) {
+    if (f8) {
+        if (nterms != 1) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: FP8 is one term");
+        e = cl == 2 ? launch_cluster<1, 2, true>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<1, 4, true>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
+    } else if (nterms == 3) {
         e = cl == 2 ? launch_cluster<3, 2>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
                     : launch_cluster<3, 4>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
     } else {
@@ -706,11 +869,11 @@ int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_ite
     p.status = status;
     p.slot_bn = max_bn;
     p.BN = max_bn;
-    p.stages = tc_stages_for(max_bn, nterms);
+    const size_t smem = plan_smem(p, max_bn, nterms, true);
+    if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm_batched: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * max_bn) cols <<= 1;
     p.tmem_cols = cols;
-    const size_t smem = (size_t)slot_bytes_for(max_bn, nterms) * p.stages + 1024;
     const int grid = total_items < num_sms ? total_items : num_sms;
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));

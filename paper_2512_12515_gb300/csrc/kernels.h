@@ -59,6 +59,11 @@ int launch_unpack_bf16(const double* z, int k, int N, int nvv, const int* pp, co
                        PadMap pm, int mult, __nv_bfloat16* xs_hi, __nv_bfloat16* xs_lo,
                        int ldx, __nv_bfloat16* ys_hi, __nv_bfloat16* ys_lo, int ldy,
                        cudaStream_t st);
+int launch_quantize_fp8(const double* L, int naux, int n, PadMap pm, int ncol8, int c_off8,
+                        void* L8, float* scale, cudaStream_t st);
+int launch_unpack_fp8(const double* z, int k, int N, int nvv, const int* pp, const int* pq,
+                      PadMap pm, int mult, float* zscale, void* xs, int ldx, void* ys, int ldy,
+                      cudaStream_t st);
 int launch_pack_f32(const float* O, const double* z, int k, int N, int nvv, const int* pp,
                     const int* pq, PadMap pm, const double* eps, int mult, double* sigma,
                     cudaStream_t st);

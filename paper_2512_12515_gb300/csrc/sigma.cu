@@ -115,6 +115,24 @@ int ensure_bf16(pprpa_ctx* c) {
     return PPRPA_OK;
 }
 
+int ensure_fp8(pprpa_ctx* c) {
+    if (c->fp8_ready) return PPRPA_OK;
+    PP_TRY(ensure_bf16(c));
+    const PadMap pm = c->pm;
+    c->c_off8 = (int)round_up(c->no, 16);
+    c->ncol8 = (int)round_up(c->c_off8 + c->nv, 16);
+    if (c->d_L8) cudaFree(c->d_L8);
+    if (c->d_L8scale) cudaFree(c->d_L8scale);
+    c->d_L8 = nullptr;
+    c->d_L8scale = nullptr;
+    PP_CUDA(cudaMalloc(&c->d_L8, (size_t)c->naux * pm.n_pad * c->ncol8));
+    PP_CUDA(cudaMalloc(&c->d_L8scale, sizeof(float) * c->naux));
+    PP_TRY(launch_quantize_fp8(c->d_L, c->naux, c->n(), pm, c->ncol8, c->c_off8, c->d_L8,
+                               c->d_L8scale, c->stream));
+    c->fp8_ready = true;
+    return PPRPA_OK;
+}
+
 static std::vector<int2> triangle_tiles(int valid, int BN) {
     std::vector<int2> t;
     const int mt = (int)ceil_div(valid, 128), nt = (int)ceil_div(valid, BN);
@@ -142,7 +160,7 @@ int stage2_bn(int valid) {
 // Launch with optional event timing (pprpa_profile).
 static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap& a_hi,
                         const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-                        const TcParams& p, int nterms, int cluster = 1) {
+                        const TcParams& p, int nterms, int cluster = 1, bool f8 = false) {
     ProfRec r;
     const bool rec = c->profile && c->prof.size() < 200000;
     if (rec) {
@@ -153,8 +171,8 @@ static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap&
         PP_CUDA(cudaEventRecord(r.a, c->stream));
     }
     if (cluster > 1)
-        PP_TRY(tc_gemm_launch_cluster(a_hi, a_lo, b_hi, b_lo, p, nterms, cluster, c->num_sms, c->stream));
-    else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream));
+        PP_TRY(tc_gemm_launch_cluster(a_hi, a_lo, b_hi, b_lo, p, nterms, cluster, c->num_sms, c->stream, f8));
+    else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream, f8));
     if (rec) {
         PP_CUDA(cudaEventRecord(r.b, c->stream));
         c->prof.push_back(r);
@@ -184,6 +202,11 @@ struct TcPrepared {
     __nv_bfloat16 *t_hi = nullptr, *t_lo = nullptr;
     float* O = nullptr;
     const double* d_z = nullptr;
+    // FP8 first stage
+    bool f8 = false;
+    int ld8x = 0, ld8y = 0;
+    void *xs8 = nullptr, *ys8 = nullptr;
+    float* zscale = nullptr;
 };
 
 struct TcJobHost {
@@ -191,14 +214,24 @@ struct TcJobHost {
     int kind = 0;        // profile row
     double flops = 0.0;  // algorithmic
     int cluster = 1;                     // stage 1 on clusters of this many CTAs sharing B
+    bool f8 = false;                     // E4M3 operands (stage 1 of the FP8 form)
     CUtensorMap b_hi_half, b_lo_half;    // B boxes of BN / cluster rows for the cluster form
 };
 
 // Buffers (allocated on first use, sized for k vectors).
 static int tc_alloc(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms, TcPrepared& pr,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool f8 = false) {
     PP_TRY(ensure_pairs(c, mult, &pr.pt));
     PP_TRY(ensure_bf16(c));
+    pr.f8 = f8;
+    if (f8) {
+        PP_TRY(ensure_fp8(c));
+        pr.ld8x = (int)round_up(std::max(c->nv, 1), 16);
+        pr.ld8y = (int)round_up(std::max(c->no, 1), 16);
+        PP_TRY(ws_get(c, "tc_xs8", (size_t)k * round_up(c->nv, 8) * pr.ld8x + 16, &pr.xs8));
+        PP_TRY(ws_get(c, "tc_ys8", (size_t)k * round_up(std::max(c->no, 1), 8) * pr.ld8y + 16, &pr.ys8));
+        PP_TRY(ws_get(c, "tc_zscale", sizeof(float) * k, (void**)&pr.zscale));
+    }
     pr.pm = c->pm;
     pr.k = k;
     pr.mult = mult;
@@ -238,6 +271,17 @@ static int tc_alloc(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms
 // Device work before the GEMMs: the packed B operands of stage 1 and a zeroed O.
 static int tc_device_prep(pprpa_ctx* c, const TcPrepared& pr, cudaStream_t st) {
     const bool split = pr.nterms == 3;
+    if (pr.f8) {
+        const size_t b8x = (size_t)pr.k * round_up(c->nv, 8) * pr.ld8x;
+        const size_t b8y = (size_t)pr.k * round_up(std::max(c->no, 1), 8) * pr.ld8y;
+        PP_CUDA(cudaMemsetAsync(pr.xs8, 0, b8x, st));
+        PP_CUDA(cudaMemsetAsync(pr.ys8, 0, b8y, st));
+        PP_TRY(launch_unpack_fp8(pr.d_z, pr.k, pr.pt->N, pr.pt->nvv, pr.pt->d_pp, pr.pt->d_pq,
+                                 pr.pm, pr.mult, pr.zscale, pr.xs8, pr.ld8x, pr.ys8, pr.ld8y, st));
+        const int64_t np = pr.pm.n_pad;
+        PP_CUDA(cudaMemsetAsync(pr.O, 0, sizeof(float) * (size_t)pr.k * np * np, st));
+        return PPRPA_OK;
+    }
     const size_t xs_bytes = sizeof(__nv_bfloat16) * (size_t)pr.k * pr.ldx * pr.ldx;
     const size_t ys_bytes = sizeof(__nv_bfloat16) * (size_t)pr.k * pr.ldy * pr.ldy;
     PP_CUDA(cudaMemsetAsync(pr.xs_hi, 0, xs_bytes, st));
@@ -256,8 +300,8 @@ static int tc_device_prep(pprpa_ctx* c, const TcPrepared& pr, cudaStream_t st) {
 }
 
 static int tc_prepare(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms,
-                      TcPrepared& pr, cudaStream_t st) {
-    PP_TRY(tc_alloc(c, mult, k, d_z, nterms, pr, st));
+                      TcPrepared& pr, cudaStream_t st, bool f8 = false) {
+    PP_TRY(tc_alloc(c, mult, k, d_z, nterms, pr, st, f8));
     return tc_device_prep(c, pr, st);
 }
 
@@ -289,25 +333,44 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         if (sz == 0) continue;
         TcJobHost h;
         TcJob& j = h.job;
-        const uint64_t adims[2] = {(uint64_t)np, (uint64_t)npc * np};
-        const uint64_t astr[1] = {(uint64_t)np * 2};
-        const uint32_t abox[2] = {64, 128};
-        PP_TRY(make_tmap_bf16(&j.a_hi, Lh, 2, adims, astr, abox));
-        PP_TRY(make_tmap_bf16(&j.a_lo, Ll, 2, adims, astr, abox));
-        const int ld = blk == 0 ? pr.ldx : pr.ldy;
+        const int eb = pr.f8 ? 1 : 2;            // element bytes
+        const uint32_t bke = pr.f8 ? 128 : 64;   // elements per 128-byte K block
         const int szp = blk == 0 ? pm.nv_p : pm.no_p;  // rows per vector (8-aligned)
-        const uint64_t bdims[2] = {(uint64_t)sz, (uint64_t)k * szp};
-        const uint64_t bstr[1] = {(uint64_t)ld * 2};
         const int BN = tile_bn(c, 1, sz, k, szp);
-        const uint32_t bbox[2] = {64, (uint32_t)BN};
-        PP_TRY(make_tmap_bf16(&j.b_hi, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, bbox));
-        PP_TRY(make_tmap_bf16(&j.b_lo, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, bbox));
+        const uint64_t bdims[2] = {(uint64_t)sz, (uint64_t)k * szp};
+        const uint32_t bbox[2] = {bke, (uint32_t)BN};
+        uint64_t bstr[1];
+        if (pr.f8) {
+            const uint8_t* L8 = (const uint8_t*)c->d_L8 + (int64_t)P0 * np * c->ncol8;
+            const uint64_t adims[2] = {(uint64_t)c->ncol8, (uint64_t)npc * np};
+            const uint64_t astr[1] = {(uint64_t)c->ncol8};
+            const uint32_t abox[2] = {bke, 128};
+            PP_TRY(make_tmap(&j.a_hi, L8, 2, adims, astr, abox, 1));
+            j.a_lo = j.a_hi;
+            bstr[0] = (uint64_t)(blk == 0 ? pr.ld8x : pr.ld8y);
+            PP_TRY(make_tmap(&j.b_hi, blk == 0 ? pr.xs8 : pr.ys8, 2, bdims, bstr, bbox, 1));
+            j.b_lo = j.b_hi;
+        } else {
+            const uint64_t adims[2] = {(uint64_t)np, (uint64_t)npc * np};
+            const uint64_t astr[1] = {(uint64_t)np * 2};
+            const uint32_t abox[2] = {64, 128};
+            PP_TRY(make_tmap_bf16(&j.a_hi, Lh, 2, adims, astr, abox));
+            PP_TRY(make_tmap_bf16(&j.a_lo, Ll, 2, adims, astr, abox));
+            const int ld = blk == 0 ? pr.ldx : pr.ldy;
+            bstr[0] = (uint64_t)ld * 2;
+            PP_TRY(make_tmap_bf16(&j.b_hi, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, bbox));
+            PP_TRY(make_tmap_bf16(&j.b_lo, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, bbox));
+        }
         TcParams& p = j.p;
         p.mode = 0;
         p.BN = BN;
         p.status = c->d_status;
         p.M_rows = (int64_t)npc * np;
-        p.a_col_off = blk == 0 ? pm.no_p : 0;
+        p.a_col_off = blk == 0 ? (pr.f8 ? c->c_off8 : pm.no_p) : 0;
+        if (pr.f8) {
+            p.row_scale = c->d_L8scale + P0;
+            p.col_scale = pr.zscale;
+        }
         p.n_per_j = szp;
         p.n_total = k * szp;
         p.t_col_off = blk == 0 ? pm.no_p : 0;
@@ -315,21 +378,27 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         p.k_vec = k;
         p.t_hi = pr.t_hi;
         p.t_lo = pr.t_lo;
-        p.kb_total = (int)ceil_div(sz, 64);
+        p.kb_total = (int)ceil_div(sz, (int64_t)bke);
         p.tiles_n = (int)ceil_div(p.n_total, BN);
         const int64_t items = ceil_div(p.M_rows, 128) * p.tiles_n;
         if (items > INT32_MAX) return set_error(PPRPA_ERR_ARG, "sigma: too many stage-1 tiles");
         p.total_items = (int)items;
         h.kind = split ? 2 : 0;
+        h.f8 = pr.f8;
         h.flops = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
         // clusters of CTAs share the B tile when there are enough M tiles to group
         int cl = env_int("PPRPA_CLUSTER", 4);
         while (cl > 1 && (BN % (16 * cl) != 0 || ceil_div(p.M_rows, 128) < cl)) cl /= 2;
         h.cluster = cl == 2 || cl == 4 ? cl : 1;
         if (h.cluster > 1) {
-            const uint32_t hbox[2] = {64, (uint32_t)(BN / h.cluster)};
-            PP_TRY(make_tmap_bf16(&h.b_hi_half, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, hbox));
-            PP_TRY(make_tmap_bf16(&h.b_lo_half, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, hbox));
+            const uint32_t hbox[2] = {bke, (uint32_t)(BN / h.cluster)};
+            if (pr.f8) {
+                PP_TRY(make_tmap(&h.b_hi_half, blk == 0 ? pr.xs8 : pr.ys8, 2, bdims, bstr, hbox, 1));
+                h.b_lo_half = h.b_hi_half;
+            } else {
+                PP_TRY(make_tmap_bf16(&h.b_hi_half, blk == 0 ? pr.xs_hi : pr.ys_hi, 2, bdims, bstr, hbox));
+                PP_TRY(make_tmap_bf16(&h.b_lo_half, blk == 0 ? pr.xs_lo : pr.ys_lo, 2, bdims, bstr, hbox));
+            }
         }
         s1.push_back(h);
     }
@@ -386,10 +455,11 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
     return PPRPA_OK;
 }
 
-int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms) {
+int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms,
+             bool f8) {
     cudaStream_t st = c->stream;
     TcPrepared pr;
-    PP_TRY(tc_prepare(c, mult, k, d_z, nterms, pr, st));
+    PP_TRY(tc_prepare(c, mult, k, d_z, nterms, pr, st, f8));
     for (int P0 = 0; P0 < c->naux; P0 += pr.pc) {
         const int npc = std::min(pr.pc, c->naux - P0);
         std::vector<TcJobHost> s1, s2;
@@ -398,10 +468,10 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
         for (auto& h : s1) {
             if (h.cluster > 1)
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
-                                    h.b_lo_half, h.job.p, nterms, h.cluster));
+                                    h.b_lo_half, h.job.p, nterms, h.cluster, h.f8));
             else
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
-                                    h.job.b_lo, h.job.p, nterms));
+                                    h.job.b_lo, h.job.p, nterms, 1, h.f8));
         }
         for (size_t b = 0; b < s2.size(); ++b) {
             TcJobHost& h = s2[b];

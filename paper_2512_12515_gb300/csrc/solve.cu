@@ -290,13 +290,20 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_CUDA(cudaMemcpyAsync(idx, order.data(), sizeof(int) * nguess, cudaMemcpyHostToDevice, st));
     PP_TRY(launch_scatter_unit(V, N, idx, nguess, st));
 
-    const bool mixed = o->precision == PPRPA_PREC_BF16;
-    int stage = mixed ? 1 : 0;
-    const double tol1 = env_dbl("PPRPA_STAGE1_TOL", std::max(o->conv_tol * 10.0, 1e-2));
+    // stages: 0 FP64 throughout; 1 BF16 (or 3 FP8) until the low-precision noise level,
+    // then 2 BF16x3 to conv_tol
+    const bool mixed = o->precision == PPRPA_PREC_BF16 || o->precision == PPRPA_PREC_FP8;
+    int stage = o->precision == PPRPA_PREC_FP8 ? 3 : (mixed ? 1 : 0);
+    // residual level at which the low-precision stage hands over: about the sigma noise of
+    // its operands (BF16 unit roundoff 2^-8, E4M3 2^-4)
+    const double tol1 = env_dbl("PPRPA_STAGE1_TOL",
+                                std::max(o->conv_tol * 10.0,
+                                         o->precision == PPRPA_PREC_FP8 ? 8e-2 : 1e-2));
     auto run_sigma = [&](int k, const double* z, double* out) -> int {
         t_sig.start();
         int rc;
         if (stage == 0) rc = sigma_f64(c, o->mult, k, z, out);
+        else if (stage == 3) rc = sigma_tc(c, o->mult, k, z, out, 1, true);
         else rc = sigma_tc(c, o->mult, k, z, out, stage == 1 ? 1 : 3);
         t_sig.stop();
         if (rc != PPRPA_OK) return rc;
@@ -423,7 +430,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e\n", it, stage, m,
                     mu_prev, h_om[0], rmax);
         if (info) info->max_resid = rmax;
-        if (stage == 1) {
+        if (stage == 1 || stage == 3) {
             ++stage1_iters;
             best_hist.push_back(rmax);
             bool stalled = false;
@@ -508,7 +515,6 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_TRY(project_block(m, m + added));
         m += added;
     }
-    if (mixed && stage == 1) stage = 2;  // not reached normally
     PP_TRY(write_outputs(c, pt, nroots, Zr, h_om.data(), omega, X, Y));
     c->last_all_roots = false;
     t_all.stop();
@@ -539,7 +545,8 @@ extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, 
     if (o->channel != PPRPA_CHANNEL_PP) return set_error(PPRPA_ERR_ARG, "solve: only the pp channel is supported");
     if (o->method != PPRPA_METHOD_FULL && o->method != PPRPA_METHOD_DAVIDSON)
         return set_error(PPRPA_ERR_ARG, "solve: unknown method");
-    if (o->precision != PPRPA_PREC_FP64 && o->precision != PPRPA_PREC_BF16)
+    if (o->precision != PPRPA_PREC_FP64 && o->precision != PPRPA_PREC_BF16 &&
+        o->precision != PPRPA_PREC_FP8)
         return set_error(PPRPA_ERR_ARG, "solve: unknown precision");
     PairTable* pt;
     PP_TRY(ensure_pairs(c, o->mult, &pt));

@@ -35,11 +35,17 @@ struct TcParams {
     int row_off = 0, col_off = 0;
     int m_valid = 0, n_valid = 0;
     float* O = nullptr;  // [k][n_pad][n_pad]
+    // FP8 stage 1: T = row_scale[R / n_pad] * col_scale[j] * (L8 Z8)
+    const float* row_scale = nullptr;
+    const float* col_scale = nullptr;
+    // set by the launcher: shared memory past the pipeline slots holds one 32 x 128-byte
+    // staging tile per epilogue warp, used to write stage-1 output rows coalesced
+    int epi_stage = 0;
 };
 
 // Batched form: one job per (molecule, stage block); tensor maps and parameters in global
-// memory (64-byte aligned), one work item per output tile (and K slice).
-struct __align__(64) TcJob {
+// memory (aligned as CUtensorMap requires), one work item per output tile (and K slice).
+struct TcJob {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
     TcParams p;
 };
@@ -49,13 +55,15 @@ struct TcItem {
 
 int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
                    const uint64_t* strides_bytes, const uint32_t* box);
-int tc_stages_for(int BN, int nterms);
+int make_tmap(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
+              const uint64_t* strides_bytes, const uint32_t* box, int elt_bytes);
+int tc_stages_for(int BN, int nterms, bool epi_stage = false);
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms,
-                   cudaStream_t st);
+                   cudaStream_t st, bool f8 = false);
 int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
-                           int nterms, int cl, int num_sms, cudaStream_t st);
+                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8 = false);
 int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_items, int max_bn,
                            int nterms, int num_sms, int* status, cudaStream_t st);
 

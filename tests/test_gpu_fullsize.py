@@ -68,7 +68,7 @@ def test_sigma_sampled_rows_full_size(pp, name, mult):
         del s["ao3c"]
         zd = torch.from_numpy(Z).cuda()
         out = {}
-        for key, prec in (("bf16", pp.PREC_BF16), ("split", pp.PREC_BF16_SPLIT)):
+        for key, prec in (("bf16", pp.PREC_BF16), ("split", pp.PREC_BF16_SPLIT), ("fp8", pp.PREC_FP8)):
             out[key] = c.sigma(mult, zd, prec).cpu().numpy()[:, rows]
         out["fp64"] = c.sigma(mult, zd[:1].contiguous(), pp.PREC_FP64).cpu().numpy()[:, rows]
     err64 = np.abs(out["fp64"][0] - ref[0]).max()
@@ -80,6 +80,12 @@ def test_sigma_sampled_rows_full_size(pp, name, mult):
     # BF16x3 drops the lo*lo product (2^-16 ~ 1.5e-5 relative) and accumulates at most
     # two auxiliary slices per tensor-memory accumulator before the FP32 partial sums
     assert err48 <= 3e-5 * scale
+    # E4M3 operands in the first stage: about 4 % relative error (unit roundoff 2^-4)
+    two = ref - diag_part
+    e8 = out["fp8"] - ref
+    print(f"  fp8 max/scale {np.abs(e8).max() / scale:.4f} fro {np.linalg.norm(e8) / np.linalg.norm(two):.4f}")
+    assert np.linalg.norm(e8) <= 0.08 * np.linalg.norm(two)
+    assert np.abs(e8).max() <= 0.1 * scale
 
 
 def test_fp64_sigma_chunking_over_aux_index(pp, monkeypatch):

@@ -98,6 +98,30 @@ def test_sigma_all_precisions(pp, mult, no, nv, naux, seed):
     assert np.abs(s48 - ref).max() <= 2e-5 * scale
 
 
+@pytest.mark.parametrize("mult", [1, 3])
+@pytest.mark.parametrize("no,nv,naux,seed", CASES)
+def test_sigma_fp8(pp, mult, no, nv, naux, seed):
+    """E4M3 first stage (per-P and per-vector scales), BF16 second stage.
+
+    E4M3 keeps 3 mantissa bits (unit roundoff 2^-4); with both stage-1 operands rounded the
+    two-electron part carries a relative error of about 4 % in the Frobenius norm (a CPU
+    emulation with torch's float8_e4m3fn cast gives 0.033-0.038 on these cases, max/scale
+    up to 0.041).  The bounds leave 1.5-2x headroom for accumulation order.
+    """
+    spec, s, L, eps = make(no, nv, naux, seed)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    Z = synth.random_trial_vectors(nvv + noo, 5, 7 + seed)
+    ref = Z @ M.T
+    two_e = Z @ (M - np.diag(np.diag(M))).T
+    with gpu_ctx(pp, spec, s) as c:
+        s8 = c.sigma(mult, Z, pp.PREC_FP8)
+        s8b = c.sigma(mult, Z, pp.PREC_FP8)
+    err = s8 - ref
+    assert np.array_equal(s8, s8b) or np.abs(s8 - s8b).max() <= 1e-6 * np.abs(two_e).max()
+    assert np.linalg.norm(err) <= 0.06 * np.linalg.norm(two_e)
+    assert np.abs(err).max() <= 0.08 * np.abs(two_e).max()
+
+
 @pytest.mark.parametrize("k", [1, 3, 17])
 def test_sigma_batch_sizes_and_device_pointers(pp, k):
     import torch
@@ -138,7 +162,7 @@ def test_full_diagonalisation_small_workload(pp, mult):
 
 
 @pytest.mark.parametrize("mult", [1, 3])
-@pytest.mark.parametrize("prec,tol", [("PREC_FP64", 1e-8), ("PREC_BF16", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("PREC_FP64", 1e-8), ("PREC_BF16", 1e-5), ("PREC_FP8", 1e-5)])
 def test_davidson_small_workload(pp, mult, prec, tol):
     spec = synth.CONFIGS["c0"]
     s = synth.make_system(spec)
