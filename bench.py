@@ -34,6 +34,9 @@ WORKLOADS = {
     "c2": synth.CONFIGS["c2"],
     "c1": synth.CONFIGS["c1"],
     "c4": synth.CONFIGS["c4"],
+    # the c2 orbital space with a tenth of the auxiliary basis: the same tile structure in
+    # both stages with a few GB on the device (profiling captures)
+    "c2-naux270": synth.SystemSpec("c2-naux270", 900, 50, 270, 50, 600, 12515002),
 }
 
 

@@ -137,6 +137,15 @@ __device__ __forceinline__ void tma_2d_mc(uint32_t dst, const CUtensorMap* m, in
         : "memory");
 }
 
+__device__ __forceinline__ void tma_3d_mc(uint32_t dst, const CUtensorMap* m, int x, int y, int z,
+                                          uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::"
+        "cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
@@ -236,7 +245,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, bool two, float (&v)[3
 }
 
 struct ItemCoord {
-    int m0, n0, batch, kb0, kb1;
+    int m0, n0, batch, kb0, kb1, nw;  // nw: N of this item's MMAs and output columns
 };
 
 __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
@@ -246,6 +255,7 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
         const int mb = item / p.tiles_n;
         c.m0 = mb * TC_BM;
         c.n0 = nb * p.BN;
+        c.nw = p.BN;
         c.batch = 0;
         c.kb0 = 0;
         c.kb1 = p.kb_total;
@@ -256,9 +266,10 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
         const int rest = item / p.ntiles;
         const int batch = rest % p.nbatch;
         const int split = rest / p.nbatch;
-        const int2 t = p.tile_list[tile];
+        const int4 t = p.tile_list[tile];
         c.m0 = t.x * TC_BM;
-        c.n0 = t.y * p.BN;
+        c.n0 = t.y;
+        c.nw = t.z;
         c.batch = batch;
         const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
         c.kb0 = split * per;
@@ -272,8 +283,9 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
 // items[i]; it names a job (one molecule and stage block) whose tensor maps and epilogue
 // parameters live in global memory, so molecules of different sizes and tile widths share
 // one persistent launch.  p.slot_bn sizes the shared-memory slots (the widest B tile).
-// CL > 1 (stage 1, single launch only): the CL CTAs of a cluster take neighbouring M tiles
-// of one N tile; each loads 1/CL of the shared B tile and multicasts it to all of them.
+// CL > 1 (single launch only): the CL CTAs of a cluster share the B tile; each loads 1/CL of
+// it and multicasts it to all of them.  Stage 1: neighbouring M tiles of one N tile.
+// Stage 2: one output tile and K slice for CL neighbouring vectors.
 // F8: stage-1 operands are E4M3 (kind::f8f6f4, 128 elements per 128-byte row); the
 // epilogue multiplies by the row (per auxiliary index) and column (per vector) scales.
 template <int NTERMS, bool BATCHED, int CL, bool F8 = false>
@@ -314,19 +326,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if constexpr (CL > 1) {
             q = &p;
             mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
-            const int nb = item % p.tiles_n;
-            const int mp = item / p.tiles_n;
-            c.m0 = (CL * mp + (int)crank) * TC_BM;
-            c.n0 = nb * p.BN;
-            c.batch = 0;
-            c.kb0 = 0;
-            c.kb1 = p.kb_total;
+            if (p.mode == 0) {
+                // group = (CL neighbouring M tiles, N tile)
+                const int nb = item % p.tiles_n;
+                const int mp = item / p.tiles_n;
+                c.m0 = (CL * mp + (int)crank) * TC_BM;
+                c.n0 = nb * p.BN;
+                c.nw = p.BN;
+                c.batch = 0;
+                c.kb0 = 0;
+                c.kb1 = p.kb_total;
+            } else {
+                // group = (K slice, CL neighbouring vectors, output tile): the CTAs share the
+                // L^P tile; a CTA whose vector index passes nbatch computes on zero-filled A
+                // and writes nothing
+                const int nbg = (p.nbatch + CL - 1) / CL;
+                const int tile = item % p.ntiles;
+                const int rest = item / p.ntiles;
+                const int bg = rest % nbg;
+                const int split = rest / nbg;
+                const int4 t = p.tile_list[tile];
+                c.m0 = t.x * TC_BM;
+                c.n0 = t.y;
+                c.nw = t.z;
+                c.batch = bg * CL + (int)crank;
+                const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
+                c.kb0 = split * per;
+                c.kb1 = min(p.kb_total, c.kb0 + per);
+            }
         } else if constexpr (BATCHED) {
             const TcItem it = items[item];
             const TcJob* jb = jobs + it.job;
             q = &jb->p;
             mA_hi = &jb->a_hi; mA_lo = &jb->a_lo; mB_hi = &jb->b_hi; mB_lo = &jb->b_lo;
             c.m0 = it.m0; c.n0 = it.n0; c.batch = it.batch; c.kb0 = it.kb0; c.kb1 = it.kb1;
+            c.nw = it.nw;
         } else {
             q = &p;
             mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
@@ -411,10 +445,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const int P = kb / q->kq_blocks;
                         const int qq = (kb % q->kq_blocks) * TC_BK;
                         tma_4d(a_hi, mA_hi, qq, c.batch, q->row_off + c.m0, P, fb);
-                        tma_3d(b_hi, mB_hi, qq, q->col_off + c.n0, P, fb);
-                        if (NTERMS == 3) {
-                            tma_4d(a_lo, mA_lo, qq, c.batch, q->row_off + c.m0, P, fb);
-                            tma_3d(b_lo, mB_lo, qq, q->col_off + c.n0, P, fb);
+                        if (NTERMS == 3) tma_4d(a_lo, mA_lo, qq, c.batch, q->row_off + c.m0, P, fb);
+                        if constexpr (CL > 1) {
+                            // this CTA's 1/CL of the L^P tile, written into every CTA
+                            const int hrows = q->BN / CL;
+                            const uint32_t hoff = crank * (uint32_t)hrows * (TC_BK * 2);
+                            const uint16_t all = (uint16_t)((1u << CL) - 1u);
+                            const int y = q->col_off + c.n0 + (int)crank * hrows;
+                            tma_3d_mc(b_hi + hoff, mB_hi, qq, y, P, fb, all);
+                            if (NTERMS == 3) tma_3d_mc(b_lo + hoff, mB_lo, qq, y, P, fb, all);
+                        } else {
+                            tma_3d(b_hi, mB_hi, qq, q->col_off + c.n0, P, fb);
+                            if (NTERMS == 3) tma_3d(b_lo, mB_lo, qq, q->col_off + c.n0, P, fb);
                         }
                     }
                     issued_mask |= 1u << stage;
@@ -449,7 +491,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const TcParams* q;
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
                 fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
-                const int bn = q->BN;
+                const int bn = c.nw;
                 const uint32_t idesc = F8 ? idesc_e4m3(bn) : idesc_bf16(bn);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
                 tc_fence_after();
@@ -509,7 +551,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const TcParams* q;
             const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
             fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
-            const int bn = q->BN;
+            const int bn = c.nw;
             const int bn2 = ((bn / 2) + 15) / 16 * 16;  // half-tile split on a 16-column boundary
             const int cbeg = half == 0 ? 0 : bn2, cend = half == 0 ? min(bn2, bn) : bn;
             if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status)) break;
@@ -660,7 +702,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             } else {
                 const int a = c.m0 + row;
-                const bool rok = a < q->m_valid;
+                const bool rok = a < q->m_valid && c.batch < q->nbatch;
                 const int n_valid = q->n_valid;
                 float* Ob = q->O + (int64_t)c.batch * q->n_pad * q->n_pad +
                             (int64_t)(q->row_off + a) * q->n_pad + q->col_off;
@@ -827,17 +869,24 @@ static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_
 int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
                            int nterms, int cl, int num_sms, cudaStream_t st, bool f8) {
-    if (p.mode != 0) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: stage 1 only");
     if (cl != 2 && cl != 4) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: cluster size 2 or 4");
-    if (p.BN < 16 * cl || p.BN > 256 || (p.BN % (16 * cl)) != 0)
-        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: BN must be a multiple of 16 * cluster size");
-    const int64_t mtiles = ceil_div(p.M_rows, TC_BM);
-    const int64_t groups = ceil_div(mtiles, cl) * p.tiles_n;
+    // each CTA loads BN / cl rows of the B tile: a whole number of 8-row swizzle atoms
+    if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0 || (p.BN % (8 * cl)) != 0)
+        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: BN must be a multiple of 16 and of 8 * cluster size");
+    int64_t groups;
+    if (p.mode == 0) {
+        const int64_t mtiles = ceil_div(p.M_rows, TC_BM);
+        groups = ceil_div(mtiles, cl) * p.tiles_n;
+    } else {
+        if (!p.tile_list || p.ntiles <= 0 || p.nbatch <= 0 || p.nsplit <= 0)
+            return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: stage-2 parameters missing");
+        groups = (int64_t)p.ntiles * ceil_div(p.nbatch, cl) * p.nsplit;
+    }
     if (groups <= 0) return PPRPA_OK;
     if (groups > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: too many tiles");
     p.total_items = (int)groups;
     p.slot_bn = p.BN;
-    const size_t smem = plan_smem(p, p.BN, nterms, true);
+    const size_t smem = plan_smem(p, p.BN, nterms, p.mode == 0);
     if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * p.BN) cols <<= 1;

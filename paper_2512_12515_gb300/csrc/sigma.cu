@@ -133,20 +133,28 @@ int ensure_fp8(pprpa_ctx* c) {
     return PPRPA_OK;
 }
 
-static std::vector<int2> triangle_tiles(int valid, int BN) {
-    std::vector<int2> t;
-    const int mt = (int)ceil_div(valid, 128), nt = (int)ceil_div(valid, BN);
-    for (int mb = 0; mb < mt; ++mb)
-        for (int nb = 0; nb < nt; ++nb) {
-            const int col_max = std::min((nb + 1) * BN, valid) - 1;
-            if (mb * 128 <= col_max) t.push_back(make_int2(mb, nb));
-        }
+// Output tiles of the second stage over the upper triangle (row <= column) of a block of
+// `valid` rows: each 128-row M tile starting at row r0 covers the columns [r0, valid) in
+// near-equal widths, multiples of 16 and at most BN, so that only the diagonal 128 x 128
+// corner and the 16-column rounding are computed beyond the triangle.
+static std::vector<int4> triangle_tiles(int valid, int BN) {
+    std::vector<int4> t;
+    const int mt = (int)ceil_div(valid, 128);
+    for (int mb = 0; mb < mt; ++mb) {
+        const int r0 = mb * 128, len = valid - r0;
+        const int nch = (int)ceil_div(len, BN);
+        const int w = std::min(BN, (int)round_up(ceil_div(len, nch), 16));
+        for (int n0 = r0; n0 < valid; n0 += w)
+            t.push_back(make_int4(mb, n0, std::min(w, (int)round_up(valid - n0, 16)), 0));
+    }
     return t;
 }
 
-// N tile of the second stage: tensor-core efficiency needs wide tiles, so among the
-// multiples of 16 in [64, 256] (or up to the block when it is narrower) take the one
-// that pads the block least, the wider one on ties.  The autotuner may override it.
+// Widest tile of the second stage.  The stage is bound by operand traffic from L2 (each
+// output tile re-reads its A rows; B tiles are shared by a cluster), not by the MMAs, so
+// among the multiples of 16 in [64, 256] (or up to the block when it is narrower) take the
+// one that pads the block least, the wider one on ties; triangle_tiles then balances the
+// widths within it.  The autotuner may override it.
 int stage2_bn(int valid) {
     const int lo = valid >= 64 ? 64 : 16;
     int best = 256, best_pad = INT32_MAX;
@@ -213,7 +221,7 @@ struct TcJobHost {
     TcJob job;
     int kind = 0;        // profile row
     double flops = 0.0;  // algorithmic
-    int cluster = 1;                     // stage 1 on clusters of this many CTAs sharing B
+    int cluster = 1;                     // clusters of this many CTAs sharing the B tile
     bool f8 = false;                     // E4M3 operands (stage 1 of the FP8 form)
     CUtensorMap b_hi_half, b_lo_half;    // B boxes of BN / cluster rows for the cluster form
 };
@@ -321,7 +329,7 @@ static int tile_bn(pprpa_ctx* c, int stage, int sz, int k, int szp) {
 
 // Jobs of one P chunk [P0, P0 + npc).
 static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vector<TcJobHost>& s1,
-                   std::vector<TcJobHost>& s2, std::vector<std::vector<int2>>& tiles) {
+                   std::vector<TcJobHost>& s2, std::vector<std::vector<int4>>& tiles) {
     const PadMap pm = pr.pm;
     const int no = c->no, nv = c->nv, k = pr.k;
     const int64_t np = pm.n_pad;
@@ -408,7 +416,7 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         const int off = blk == 0 ? pm.no_p : 0;
         const int BN = tile_bn(c, 2, sz, k, 0);
         tiles.push_back(triangle_tiles(sz, BN));
-        const std::vector<int2>& tl = tiles.back();
+        const std::vector<int4>& tl = tiles.back();
         TcJobHost h;
         TcJob& j = h.job;
         const uint64_t adims[4] = {(uint64_t)np, (uint64_t)k, (uint64_t)np, (uint64_t)npc};
@@ -448,6 +456,16 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         p.n_pad = (int)np;
         p.O = pr.O;
         p.total_items = (int)(base_items * p.nsplit);
+        // clusters over neighbouring vectors sharing the L^P tile (TMA multicast): 4 when it
+        // divides k and BN / 4 is whole swizzle atoms, else 2
+        int cl2 = env_int("PPRPA_CLUSTER2", -1);
+        if (cl2 < 0) cl2 = (k % 4 == 0 && BN % 32 == 0) ? 4 : (k >= 2 ? 2 : 1);
+        if ((cl2 == 2 || cl2 == 4) && BN % 16 == 0 && BN % (8 * cl2) == 0 && k >= 2) {
+            h.cluster = cl2;
+            const uint32_t hbox[3] = {64, (uint32_t)(BN / cl2), 1};
+            PP_TRY(make_tmap_bf16(&h.b_hi_half, Lh, 3, bdims, bstr, hbox));
+            PP_TRY(make_tmap_bf16(&h.b_lo_half, Ll, 3, bdims, bstr, hbox));
+        }
         h.kind = split ? 3 : 1;
         h.flops = 1.0 * npc * (double)(no + nv) * (double)sz * sz * k;
         s2.push_back(h);
@@ -463,7 +481,7 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
     for (int P0 = 0; P0 < c->naux; P0 += pr.pc) {
         const int npc = std::min(pr.pc, c->naux - P0);
         std::vector<TcJobHost> s1, s2;
-        std::vector<std::vector<int2>> tiles;
+        std::vector<std::vector<int4>> tiles;
         PP_TRY(tc_jobs(c, pr, P0, npc, s1, s2, tiles));
         for (auto& h : s1) {
             if (h.cluster > 1)
@@ -475,13 +493,17 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
         }
         for (size_t b = 0; b < s2.size(); ++b) {
             TcJobHost& h = s2[b];
-            int2* d_tiles;
-            PP_TRY(ws_get(c, "tc_tiles" + std::to_string(b), sizeof(int2) * tiles[b].size(), (void**)&d_tiles));
-            PP_CUDA(cudaMemcpyAsync(d_tiles, tiles[b].data(), sizeof(int2) * tiles[b].size(),
+            int4* d_tiles;
+            PP_TRY(ws_get(c, "tc_tiles" + std::to_string(b), sizeof(int4) * tiles[b].size(), (void**)&d_tiles));
+            PP_CUDA(cudaMemcpyAsync(d_tiles, tiles[b].data(), sizeof(int4) * tiles[b].size(),
                                     cudaMemcpyHostToDevice, st));
             h.job.p.tile_list = d_tiles;
-            PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi, h.job.b_lo,
-                                h.job.p, nterms));
+            if (h.cluster > 1)
+                PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
+                                    h.b_lo_half, h.job.p, nterms, h.cluster));
+            else
+                PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
+                                    h.job.b_lo, h.job.p, nterms));
         }
     }
     PP_TRY(launch_pack_f32(pr.O, d_z, k, pr.pt->N, pr.pt->nvv, pr.pt->d_pp, pr.pt->d_pq, pr.pm,
@@ -490,20 +512,20 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
 }
 
 // Work items of one job (the same decomposition the single launch decodes arithmetically).
-static void append_items(const TcParams& p, int job, const std::vector<int2>* tiles,
+static void append_items(const TcParams& p, int job, const std::vector<int4>* tiles,
                          std::vector<TcItem>& out) {
     if (p.mode == 0) {
         const int64_t mt = ceil_div(p.M_rows, 128);
         for (int64_t mb = 0; mb < mt; ++mb)
             for (int nb = 0; nb < p.tiles_n; ++nb)
-                out.push_back(TcItem{job, (int)(mb * 128), nb * p.BN, 0, 0, p.kb_total});
+                out.push_back(TcItem{job, (int)(mb * 128), nb * p.BN, 0, 0, p.kb_total, p.BN, 0});
     } else {
         const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
         for (int sp = 0; sp < p.nsplit; ++sp)
             for (int b = 0; b < p.nbatch; ++b)
-                for (const int2& t : *tiles)
-                    out.push_back(TcItem{job, t.x * 128, t.y * p.BN, b, sp * per,
-                                         std::min(p.kb_total, (sp + 1) * per)});
+                for (const int4& t : *tiles)
+                    out.push_back(TcItem{job, t.x * 128, t.y, b, sp * per,
+                                         std::min(p.kb_total, (sp + 1) * per), t.z, 0});
     }
 }
 
@@ -587,7 +609,7 @@ int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int
     bp->st = st;
     bp->prs.resize(nmol);
     std::vector<TcJobHost> s1, s2;
-    std::vector<std::vector<int2>> tiles;
+    std::vector<std::vector<int4>> tiles;
     std::vector<int> s2_tile_index;
     for (int m = 0; m < nmol; ++m) {
         pprpa_ctx* c = ctxs[m];

@@ -29,7 +29,7 @@ struct TcParams {
     __nv_bfloat16* t_hi = nullptr;
     __nv_bfloat16* t_lo = nullptr;
     // stage 2
-    const int2* tile_list = nullptr;  // (m tile, n tile) pairs to compute
+    const int4* tile_list = nullptr;  // (m tile, first column, width, 0) of each output tile
     int ntiles = 0, nbatch = 0, nsplit = 1;
     int kq_blocks = 0;   // ceil(n_pad / 64)
     int row_off = 0, col_off = 0;
@@ -50,7 +50,7 @@ struct TcJob {
     TcParams p;
 };
 struct TcItem {
-    int job, m0, n0, batch, kb0, kb1;
+    int job, m0, n0, batch, kb0, kb1, nw, pad;  // nw: MMA N of the item (<= its job's BN)
 };
 
 int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
