@@ -66,16 +66,17 @@ extern "C" {
 #define PPRPA_PREC_BF16 1       /* BF16 tensor-core sigma, then BF16x3 split sigma */
 #define PPRPA_PREC_FP8 2        /* FP8 (E4M3, per-P / per-vector scaled) first stage, then BF16x3 */
 
-#define PPRPA_CHANNEL_PP 0      /* lowest two-electron addition roots */
+#define PPRPA_CHANNEL_PP 0      /* lowest two-electron addition roots (N+2) */
+#define PPRPA_CHANNEL_HH 1      /* highest two-electron removal roots (N-2) */
 
 typedef struct pprpa_ctx pprpa_ctx;
 
 typedef struct pprpa_options {
     int mult;          /* PPRPA_SINGLET or PPRPA_TRIPLET */
-    int channel;       /* PPRPA_CHANNEL_PP */
+    int channel;       /* PPRPA_CHANNEL_PP or PPRPA_CHANNEL_HH */
     int method;        /* PPRPA_METHOD_FULL or PPRPA_METHOD_DAVIDSON */
     int precision;     /* PPRPA_PREC_* (Davidson only; FULL is always FP64) */
-    int nroots;        /* number of lowest N+2 roots wanted (>= 1) */
+    int nroots;        /* roots wanted: 1..nvv lowest N+2 roots (pp), 1..noo highest N-2 roots (hh) */
     double conv_tol;   /* residual 2-norm ||M z - omega W z|| for converged roots */
     int max_iter;      /* Davidson iteration cap */
     int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic */
@@ -203,11 +204,16 @@ int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int naux, const do
                         void* cuda_stream);
 
 /* ---- solve -----------------------------------------------------------------
- * pprpa_solve: lowest opts->nroots two-electron addition roots.
- * omega[nroots] ascending; X[nroots][nvv] and Y[nroots][noo] (either may be
- * NULL) with X^T X - Y^T Y = 1 and the largest-magnitude component positive;
- * ec (may be NULL, FULL only): correlation energy sum(Omega^{N+2}) - Tr A
- * of Eq. correlation_energy for this multiplicity; info may be NULL.
+ * pprpa_solve: pp channel (opts->channel = PPRPA_CHANNEL_PP): the lowest
+ * opts->nroots two-electron addition roots, omega ascending, X^T X - Y^T Y = +1.
+ * hh channel (PPRPA_CHANNEL_HH): the highest opts->nroots two-electron removal
+ * roots, omega descending, X^T X - Y^T Y = -1 (the lower sign of Eq. xy_norm);
+ * they are found as the lowest positive-norm roots of the pencil (M, -W).
+ * X[nroots][nvv] and Y[nroots][noo] (either may be NULL), largest-magnitude
+ * component positive; ec (may be NULL, FULL only): correlation energy of Eq.
+ * correlation_energy for this multiplicity, sum(Omega^{N+2}) - Tr A from every
+ * addition root (pp) or -sum(Omega^{N-2}) - Tr C from every removal root (hh);
+ * the two agree for a stable problem.  info may be NULL.
  * Host output pointers.  Returns PPRPA_ERR_NOCONV (outputs filled with the
  * last iterate) or PPRPA_ERR_UNSTABLE when no positive-definite shift
  * exists.  The converged eigenvectors stay on the device for pprpa_grad. */
@@ -215,7 +221,8 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
                 double* Y, double* ec, pprpa_info* info);
 
 /* pprpa_grad: Hellmann-Feynman gradient (Sec. "Analytic Gradient") of root
- * `root` of the last pprpa_solve: d omega / d L^P_pq -> dL[naux][n][n]
+ * `root` of the last pprpa_solve (either channel; the sign z^T W z = -1 of a
+ * removal root is applied): d omega / d L^P_pq -> dL[naux][n][n]
  * (entries treated as independent) and d omega / d eps_p -> deps[n]
  * (active orbitals).  Computed in FP64 on the device.  Either output may
  * be NULL.  Host or device per `where`. */
@@ -225,7 +232,8 @@ int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
  * (Eq. correlation_energy) of the last solve's multiplicity, with respect to L^P_pq
  * (dL[naux][n][n], entries independent) and eps_p (deps[n]): the sum of every addition
  * root's Hellmann-Feynman gradient minus the derivative of Tr A.  Needs a preceding FULL
- * solve that returned every addition root (nroots = nvv); PPRPA_ERR_STATE otherwise.
+ * solve of the pp channel that returned every addition root (nroots = nvv);
+ * PPRPA_ERR_STATE otherwise.
  * FP64 on the device; outputs host or device per `where`, either may be NULL. */
 int pprpa_grad_ec(pprpa_ctx* ctx, double* dL, double* deps, int where);
 

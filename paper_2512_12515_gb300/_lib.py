@@ -24,7 +24,7 @@ SINGLET, TRIPLET = 1, 3
 METHOD_FULL, METHOD_DAVIDSON = 0, 1
 PREC_FP64, PREC_BF16, PREC_FP8 = 0, 1, 2
 PREC_BF16_SPLIT = PREC_BF16 + 16  # sigma only: BF16x3 split products
-CHANNEL_PP = 0
+CHANNEL_PP, CHANNEL_HH = 0, 1  # lowest N+2 roots / highest N-2 roots
 
 
 class Options(ctypes.Structure):
@@ -273,9 +273,12 @@ class Context:
 
     # ---- solve / gradient ----
     def solve(self, mult=SINGLET, nroots=10, method=METHOD_DAVIDSON, precision=PREC_FP64,
-              conv_tol=1e-6, max_iter=200, max_subspace=0, want_ec=False, raise_noconv=True):
+              conv_tol=1e-6, max_iter=200, max_subspace=0, want_ec=False, raise_noconv=True,
+              channel=CHANNEL_PP):
+        """pp channel: the lowest N+2 roots, ascending, X^T X - Y^T Y = +1.
+        hh channel: the highest N-2 roots, descending, X^T X - Y^T Y = -1."""
         _, _, nvv, noo = self.dims(mult)
-        o = Options(mult, CHANNEL_PP, method, precision, nroots, conv_tol, max_iter, max_subspace,
+        o = Options(mult, channel, method, precision, nroots, conv_tol, max_iter, max_subspace,
                     int(want_ec))
         omega = np.empty(nroots)
         X = np.empty((nroots, nvv))

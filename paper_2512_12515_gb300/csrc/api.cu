@@ -457,8 +457,9 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
     if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
     PairTable* t;
     PP_TRY(ensure_pairs(c, c->last_mult, &t));
-    // two-electron addition roots: z^T W z = +1
-    return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, 1.0, dL, deps, where);
+    // addition roots have z^T W z = +1, removal roots (hh channel) -1
+    const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
+    return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, s, dL, deps, where);
 }
 
 int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {

@@ -72,6 +72,7 @@ struct pprpa_ctx {
 
     // last solve (for gradients)
     int last_mult = 0;
+    int last_channel = 0;  // PPRPA_CHANNEL_* of the last solve (sign of z^T W z)
     int last_nroots = 0;
     int last_N = 0;
     bool last_all_roots = false;  // the last solve returned every addition root (FULL)

@@ -398,7 +398,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // R = SZ - omega * W * Zr; norms2[j] += ||R_j||^2 (norms2 zeroed by the caller).
 __global__ void residual_kernel(const double* __restrict__ SZ, const double* __restrict__ Zr,
-                                const double* __restrict__ omega, int N, int nvv,
+                                const double* __restrict__ omega, int N, int nvv, double wsign,
                                 double* __restrict__ R, double* __restrict__ norms2) {
     __shared__ double sh[32];
     const int j = blockIdx.y;
@@ -407,7 +407,7 @@ __global__ void residual_kernel(const double* __restrict__ SZ, const double* __r
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = (int64_t)j * N + i;
-        const double w = i < nvv ? 1.0 : -1.0;
+        const double w = i < nvv ? wsign : -wsign;
         const double r = SZ[t] - om * w * Zr[t];
         R[t] = r;
         acc = fma(r, r, acc);
@@ -417,10 +417,10 @@ __global__ void residual_kernel(const double* __restrict__ SZ, const double* __r
 }
 
 int launch_residual(const double* SZ, const double* Zr, const double* omega, int k, int N,
-                    int nvv, double* R, double* norms2, cudaStream_t st) {
+                    int nvv, double* R, double* norms2, cudaStream_t st, double wsign) {
     if (!k || !N) return PPRPA_OK;
     dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), k);
-    residual_kernel<<<grid, 256, 0, st>>>(SZ, Zr, omega, N, nvv, R, norms2);
+    residual_kernel<<<grid, 256, 0, st>>>(SZ, Zr, omega, N, nvv, wsign, R, norms2);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
@@ -428,13 +428,13 @@ int launch_residual(const double* SZ, const double* Zr, const double* omega, int
 // Diagonal preconditioner: out_t = R_sel[t] / (D - omega_sel[t] * w), |denominator| >= 1e-4.
 __global__ void correction_kernel(const double* __restrict__ R, const double* __restrict__ D,
                                   const double* __restrict__ omega, const int* __restrict__ sel,
-                                  int N, int nvv, double* __restrict__ out) {
+                                  int N, int nvv, double wsign, double* __restrict__ out) {
     const int t = blockIdx.y;
     const int j = sel[t];
     const double om = omega[j];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double w = i < nvv ? 1.0 : -1.0;
+        const double w = i < nvv ? wsign : -wsign;
         double den = D[i] - om * w;
         if (fabs(den) < 1e-4) den = den < 0.0 ? -1e-4 : 1e-4;
         out[(int64_t)t * N + i] = R[(int64_t)j * N + i] / den;
@@ -442,10 +442,10 @@ __global__ void correction_kernel(const double* __restrict__ R, const double* __
 }
 
 int launch_correction(const double* R, const double* D, const double* omega, const int* sel,
-                      int kn, int N, int nvv, double* out, cudaStream_t st) {
+                      int kn, int N, int nvv, double* out, cudaStream_t st, double wsign) {
     if (!kn || !N) return PPRPA_OK;
     dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), kn);
-    correction_kernel<<<grid, 256, 0, st>>>(R, D, omega, sel, N, nvv, out);
+    correction_kernel<<<grid, 256, 0, st>>>(R, D, omega, sel, N, nvv, wsign, out);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
@@ -562,14 +562,14 @@ int launch_ec_sum(const double* omega, int nw, const double* D, int nvv, double*
     return PPRPA_OK;
 }
 
-__global__ void set_diag_kernel(double* M, int N, int nvv) {
+__global__ void set_diag_kernel(double* M, int N, int nvv, double wsign) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) M[(int64_t)i * N + i] = i < nvv ? 1.0 : -1.0;
+    if (i < N) M[(int64_t)i * N + i] = i < nvv ? wsign : -wsign;
 }
 
-int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st) {
+int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st, double wsign) {
     PP_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)N * N, st));
-    set_diag_kernel<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(W, N, nvv);
+    set_diag_kernel<<<(unsigned)ceil_div(N, 256), 256, 0, st>>>(W, N, nvv, wsign);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }

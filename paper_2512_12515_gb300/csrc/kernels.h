@@ -70,16 +70,17 @@ int launch_pack_f32(const float* O, const double* z, int k, int N, int nvv, cons
 
 // Davidson vector kernels.
 int launch_residual(const double* SZ, const double* Zr, const double* omega, int k, int N,
-                    int nvv, double* R, double* norms2, cudaStream_t st);
+                    int nvv, double* R, double* norms2, cudaStream_t st, double wsign = 1.0);
 int launch_correction(const double* R, const double* D, const double* omega, const int* sel,
-                      int kn, int N, int nvv, double* out, cudaStream_t st);
+                      int kn, int N, int nvv, double* out, cudaStream_t st, double wsign = 1.0);
 int launch_row_norms2(const double* X, int k, int N, double* out, cudaStream_t st);
 int launch_scatter_unit(double* V, int ld, const int* idx, int k, cudaStream_t st);
 int launch_build_matrix(const double* eri, int n, const int* pp, const int* pq, int N,
                         int nvv, const double* eps, int mult, double* M, cudaStream_t st);
 int launch_ec_sum(const double* omega, int nw, const double* D, int nvv, double* out,
                   cudaStream_t st);
-int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st);
+// W = diag(wsign I_nvv, -wsign I_noo); wsign = -1 gives the metric of the removal channel
+int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st, double wsign = 1.0);
 int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, double* dL,
                         double* deps, cudaStream_t st);
 int launch_grad_eps(const double* z, int N, int nvv, const int* pp, const int* pq, int n,

@@ -341,7 +341,6 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         if (sz == 0) continue;
         TcJobHost h;
         TcJob& j = h.job;
-        const int eb = pr.f8 ? 1 : 2;            // element bytes
         const uint32_t bke = pr.f8 ? 128 : 64;   // elements per 128-byte K block
         const int szp = blk == 0 ? pm.nv_p : pm.no_p;  // rows per vector (8-aligned)
         const int BN = tile_bn(c, 1, sz, k, szp);

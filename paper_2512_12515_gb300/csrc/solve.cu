@@ -174,16 +174,26 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     PP_TRY(ws_get(c, "full_dwork", sizeof(double) * (size_t)c->naux * n, (void**)&dwork));
     PP_TRY(ws_get(c, "full_mus", sizeof(double) * 32, (void**)&mus));
     PP_TRY(ws_get(c, "full_ec", sizeof(double), (void**)&dec));
+    // pp channel: the lowest roots of positive norm of (M, W).  hh channel: the highest roots
+    // of negative norm, i.e. the lowest roots of positive norm of (M, -W) with omega = -mu.
+    const bool hh = o->channel == PPRPA_CHANNEL_HH;
+    const double ws = hh ? -1.0 : 1.0;
+    const int noo = pt->noo;
+    const int npos = hh ? noo : nvv;  // roots of positive norm in the solved pencil
     PP_TRY(build_explicit(c, pt, o->mult, eri, M));
-    PP_TRY(launch_metric_matrix(W, N, nvv, st));
+    PP_TRY(launch_metric_matrix(W, N, nvv, st, ws));
     PP_TRY(launch_diag(c->d_L, c->naux, n, c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     PP_CUDA(cudaStreamSynchronize(st));
+    // gap edges of the solved pencil from the diagonal: its positive-norm block (vv, or oo
+    // for hh) starts near min D there, its negative-norm block ends near max(-D)
     double hi = 1e300, lo = -1e300;
-    for (int i = 0; i < nvv; ++i) hi = std::min(hi, hD[i]);
-    for (int i = nvv; i < N; ++i) lo = std::max(lo, -hD[i]);
-    if (pt->noo == 0) lo = hi - 1.0;
+    for (int i = 0; i < N; ++i) {
+        if ((i < nvv) != hh) hi = std::min(hi, hD[i]);
+        else lo = std::max(lo, -hD[i]);
+    }
+    if (npos == N) lo = hi - 1.0;
     // wide scan: the diagonal only estimates the gap edges
     std::vector<double> cand = shift_candidates(lo, hi, 0.0, false);
     for (int t = 1; t <= 6; ++t) {
@@ -195,7 +205,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     RRArgs a;
     a.G = M; a.S = W; a.ld = N; a.m = N;
     a.mus = mus; a.nmu = (int)cand.size();
-    a.nwant = o->nroots; a.nkeep = nvv;
+    a.nwant = o->nroots; a.nkeep = npos;
     a.work = work; a.omega = om; a.coef = coef; a.info = rinfo;
     PP_TRY(launch_rayleigh_ritz(a, st));
     double hinfo[8];
@@ -203,17 +213,23 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     PP_CUDA(cudaStreamSynchronize(st));
     if ((int)hinfo[0] == DEV_NOTPD)
         return set_error(PPRPA_ERR_UNSTABLE, "full: no shift makes M - mu W positive definite");
-    if ((int)hinfo[2] != nvv)
+    if ((int)hinfo[2] != npos)
         return set_error(PPRPA_ERR_UNSTABLE, "full: root count by norm differs from the pair count");
-    std::vector<double> h_om(nvv);
-    PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * nvv, cudaMemcpyDeviceToHost, st));
+    std::vector<double> h_om(npos);
+    PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * npos, cudaMemcpyDeviceToHost, st));
     if (ec) {
-        PP_TRY(launch_ec_sum(om, nvv, D, nvv, dec, st));
+        // E_c = sum Omega^{+2e} - Tr A (pp), or -sum Omega^{-2e} - Tr C = sum mu - Tr C (hh)
+        // (Eq. correlation_energy); both need every root of the channel, which FULL has
+        if (hh) PP_TRY(launch_ec_sum(om, noo, D + nvv, noo, dec, st));
+        else PP_TRY(launch_ec_sum(om, nvv, D, nvv, dec, st));
         PP_CUDA(cudaMemcpyAsync(ec, dec, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     PP_CUDA(cudaStreamSynchronize(st));
+    if (hh)
+        for (double& v : h_om) v = -v;  // omega of the removal roots, highest first
     PP_TRY(write_outputs(c, pt, o->nroots, coef, h_om.data(), omega, X, Y));
-    c->last_all_roots = o->nroots == nvv;
+    c->last_all_roots = !hh && o->nroots == nvv;
+    c->last_channel = o->channel;
     tt.stop();
     if (info) {
         std::memset(info, 0, sizeof(*info));
@@ -231,7 +247,13 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     const int N = pt->N, nvv = pt->nvv, noo = pt->noo;
     const int nroots = o->nroots;
     cudaStream_t st = c->stream;
-    const int nguess = std::min(nvv, std::max(2 * nroots, nroots + 8));
+    // hh channel: solve (M, -W) for its lowest positive-norm roots mu (omega = -mu); every
+    // use of the metric below carries its sign ws, and the blocks of positive and negative
+    // norm trade places
+    const bool hh = o->channel == PPRPA_CHANNEL_HH;
+    const double ws = hh ? -1.0 : 1.0;
+    const int pos0 = hh ? nvv : 0, npos_blk = hh ? noo : nvv;  // positive-norm block
+    const int nguess = std::min(npos_blk, std::max(2 * nroots, nroots + 8));
     // subspace cap and thick-restart size: unstable problems (complex pairs near the
     // targets) need a restart that keeps many Ritz vectors, so both are generous
     int m_max = o->max_subspace > 0 ? o->max_subspace : 128;
@@ -281,11 +303,13 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     PP_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> order(nvv);
-    std::iota(order.begin(), order.end(), 0);
+    std::vector<int> order(npos_blk);
+    std::iota(order.begin(), order.end(), pos0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hD[a] < hD[b]; });
+    // lowest positive-norm estimate, highest negative-norm estimate
     double dv_min = hD[order[0]], oo_max = -1e300;
-    for (int i = nvv; i < N; ++i) oo_max = std::max(oo_max, -hD[i]);
+    for (int i = 0; i < N; ++i)
+        if ((i < pos0) || (i >= pos0 + npos_blk)) oo_max = std::max(oo_max, -hD[i]);
     PP_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)nguess * N, st));
     PP_CUDA(cudaMemcpyAsync(idx, order.data(), sizeof(int) * nguess, cudaMemcpyHostToDevice, st));
     PP_TRY(launch_scatter_unit(V, N, idx, nguess, st));
@@ -317,16 +341,19 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     };
     auto project_block = [&](int m0, int m) -> int {
         const int kn = m - m0;
-        // G = V_vv Sg_vv^T (virtual pairs) and Go = V_oo Sg_oo^T (occupied pairs), blocks
-        // [0:m, m0:m] and [m0:m, 0:m0]; V^T M V = G + Go and V^T W M V = G - Go.
-        PP_TRY(dots(V, N, m, Sg + (size_t)m0 * N, N, kn, nvv, G + m0, m_max, 1.0, true, st));
-        PP_TRY(dots(V + (size_t)m0 * N, N, kn, Sg, N, m0, nvv, G + (size_t)m0 * m_max, m_max, 1.0, true, st));
-        PP_TRY(dots(V + nvv, N, m, Sg + (size_t)m0 * N + nvv, N, kn, noo, Go + m0, m_max, 1.0, true, st));
-        PP_TRY(dots(V + (size_t)m0 * N + nvv, N, kn, Sg + nvv, N, m0, noo, Go + (size_t)m0 * m_max, m_max, 1.0,
+        // Gp = V Sg^T over the positive-norm pairs and Gn over the others (virtual and
+        // occupied pairs, swapped for hh), blocks [0:m, m0:m] and [m0:m, 0:m0]:
+        // V^T M V = Gp + Gn and V^T (ws W) M V = Gp - Gn.
+        double* Gv = hh ? Go : G;  // virtual-pair part
+        double* Gq = hh ? G : Go;  // occupied-pair part
+        PP_TRY(dots(V, N, m, Sg + (size_t)m0 * N, N, kn, nvv, Gv + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + (size_t)m0 * N, N, kn, Sg, N, m0, nvv, Gv + (size_t)m0 * m_max, m_max, 1.0, true, st));
+        PP_TRY(dots(V + nvv, N, m, Sg + (size_t)m0 * N + nvv, N, kn, noo, Gq + m0, m_max, 1.0, true, st));
+        PP_TRY(dots(V + (size_t)m0 * N + nvv, N, kn, Sg + nvv, N, m0, noo, Gq + (size_t)m0 * m_max, m_max, 1.0,
                     true, st));
-        // S[0:m, m0:m] = V W V^T (virtual pairs +, occupied pairs -)
-        PP_TRY(dots(V, N, m, V + (size_t)m0 * N, N, kn, nvv, S + m0, m_max, 1.0, true, st));
-        PP_TRY(dots(V + nvv, N, m, V + (size_t)m0 * N + nvv, N, kn, noo, S + m0, m_max, -1.0, false, st));
+        // S[0:m, m0:m] = V (ws W) V^T (virtual pairs ws, occupied pairs -ws)
+        PP_TRY(dots(V, N, m, V + (size_t)m0 * N, N, kn, nvv, S + m0, m_max, ws, true, st));
+        PP_TRY(dots(V + nvv, N, m, V + (size_t)m0 * N + nvv, N, kn, noo, S + m0, m_max, -ws, false, st));
         return PPRPA_OK;
     };
     // collapse the basis onto the first nk Ritz vectors (coef rows), orthonormalised
@@ -415,7 +442,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_TRY(combine(coef, m, ntg, m, V, N, Zr, 1.0, 0.0, st));
         PP_TRY(combine(coef, m, ntg, m, Sg, N, SZ, 1.0, 0.0, st));
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * ntg, st));
-        PP_TRY(launch_residual(SZ, Zr, om, ntg, N, nvv, R, nrm, st));
+        PP_TRY(launch_residual(SZ, Zr, om, ntg, N, nvv, R, nrm, st, ws));
         PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * ntg, cudaMemcpyDeviceToHost, st));
         PP_CUDA(cudaStreamSynchronize(st));
         double rmax = 0.0;
@@ -458,7 +485,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         // ---- correction vectors ----
         const int kn = (int)todo.size();
         PP_CUDA(cudaMemcpyAsync(sel, todo.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, st));
-        PP_TRY(launch_correction(R, D, om, sel, kn, N, nvv, Dn, st));
+        PP_TRY(launch_correction(R, D, om, sel, kn, N, nvv, Dn, st, ws));
         if (m + kn > m_max) {
             PP_TRY(collapse(nk_avail, m, false));
             m = nk_avail;
@@ -515,8 +542,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_TRY(project_block(m, m + added));
         m += added;
     }
+    if (hh)
+        for (int j = 0; j < nroots; ++j) h_om[j] = -h_om[j];  // omega of the removal roots
     PP_TRY(write_outputs(c, pt, nroots, Zr, h_om.data(), omega, X, Y));
     c->last_all_roots = false;
+    c->last_channel = o->channel;
     t_all.stop();
     if (info) {
         info->iters = std::min(it, o->max_iter);
@@ -542,7 +572,8 @@ extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, 
     PP_CUDA(cudaSetDevice(c->device));
     if (!c->have_L) return set_error(PPRPA_ERR_STATE, "solve: integrals not set");
     if (o->mult != 1 && o->mult != 3) return set_error(PPRPA_ERR_ARG, "solve: mult must be 1 or 3");
-    if (o->channel != PPRPA_CHANNEL_PP) return set_error(PPRPA_ERR_ARG, "solve: only the pp channel is supported");
+    if (o->channel != PPRPA_CHANNEL_PP && o->channel != PPRPA_CHANNEL_HH)
+        return set_error(PPRPA_ERR_ARG, "solve: channel must be PPRPA_CHANNEL_PP or PPRPA_CHANNEL_HH");
     if (o->method != PPRPA_METHOD_FULL && o->method != PPRPA_METHOD_DAVIDSON)
         return set_error(PPRPA_ERR_ARG, "solve: unknown method");
     if (o->precision != PPRPA_PREC_FP64 && o->precision != PPRPA_PREC_BF16 &&
@@ -550,7 +581,9 @@ extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, 
         return set_error(PPRPA_ERR_ARG, "solve: unknown precision");
     PairTable* pt;
     PP_TRY(ensure_pairs(c, o->mult, &pt));
-    if (o->nroots < 1 || o->nroots > pt->nvv) return set_error(PPRPA_ERR_ARG, "solve: nroots out of range");
+    const int nmax = o->channel == PPRPA_CHANNEL_HH ? pt->noo : pt->nvv;
+    if (o->nroots < 1 || o->nroots > nmax)
+        return set_error(PPRPA_ERR_ARG, "solve: nroots out of range (1..nvv for pp, 1..noo for hh)");
     if (info) std::memset(info, 0, sizeof(*info));
     if (o->method == PPRPA_METHOD_FULL) return solve_full(c, o, pt, omega, X, Y, ec, info);
     if (!(o->conv_tol > 0.0) || o->max_iter < 1) return set_error(PPRPA_ERR_ARG, "solve: bad tolerance / max_iter");
