@@ -228,6 +228,20 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
  * be NULL.  Host or device per `where`. */
 int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
 
+/* pprpa_grad_ao: adjoint of the AO->MO transform of pprpa_set_ao, the step from the
+ * MO-space gradient of pprpa_grad / pprpa_grad_ec / pprpa_grad_vector back to the AO inputs
+ * (the chain toward the nuclear gradients of Sec. "Analytic Gradient").  With
+ * L^P = C_act^T (P|..) C_act (entries independent):
+ *   dAO[P][mu][nu] = sum_pq C[mu][p] dL[P][p][q] C[nu][q]            (naux x nbasis x nbasis)
+ *   dC[mu][r]      = sum_P (H^P dL^P^T + H^P dL^P)[mu][r],  H^P = (P|..) C_act,
+ * for the active columns r of C (nbasis x nmo); every other column is zero.  The AO slices
+ * are taken as symmetric (as pprpa_set_ao requires).  Inputs: C[nbasis][nmo] and
+ * dL[naux][n][n] (n active orbitals, occupied first); ao3c[naux][nbasis][nbasis] is needed
+ * only for dC and may be NULL otherwise.  Either output may be NULL.  All arrays host or
+ * device per `where`; FP64 on the device, in slices of the auxiliary index. */
+int pprpa_grad_ao(pprpa_ctx* ctx, int nbasis, int naux, const double* C, const double* ao3c,
+                  const double* dL, double* dAO, double* dC, int where);
+
 /* pprpa_grad_ec: gradient of the correlation energy E_c = sum(Omega^{N+2}) - Tr A
  * (Eq. correlation_energy) of the last solve's multiplicity, with respect to L^P_pq
  * (dL[naux][n][n], entries independent) and eps_p (deps[n]): the sum of every addition

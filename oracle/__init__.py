@@ -19,6 +19,8 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   second-order (MP2-type) limit.
 * grad_omega: pinned by central finite differences and by the trace rule of
   the two-electron density matrix.
+* grad_ao: pinned by central finite differences of a root through the whole
+  chain (AO integrals or MO coefficients -> L -> M -> omega).
 * ri_sigma / davidson: pinned by the explicit matrix (sigma) and by full
   diagonalisation (Davidson roots).
 * eigenvector phase: fixed by convention (largest-magnitude component
@@ -28,6 +30,7 @@ from .pprpa_ref import (  # noqa: F401
     active_orbitals,
     ao_to_mo,
     ao_to_mo_rows,
+    grad_ao,
     pair_list,
     eri_phys,
     build_matrix,

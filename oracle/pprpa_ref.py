@@ -41,6 +41,32 @@ def ao_to_mo(ao3c, C, orb):
     return np.einsum("Pmn,mp,nq->Ppq", ao3c, ca, ca, optimize=True)
 
 
+def grad_ao(ao3c, C, orb, dL):
+    """Adjoint of the AO->MO transform: from d f / d L^P_pq to d f / d (P|mu nu) and d f / d C.
+
+    With L^P_pq = sum_{mu,nu} C_{mu p} (P|mu nu) C_{nu q} (the transform of
+    :func:`ao_to_mo`; Abstract, inputs of Sec. Implementation Details) and every
+    entry treated as independent, the chain rule gives
+      d f / d (P|mu nu) = sum_pq C_{mu p} (d f / d L^P_pq) C_{nu q},
+      d f / d C_{mu r}  = sum_P [ sum_q H^P_{mu q} (d f / d L^P_rq)
+                                 + sum_p H'^P_{mu p} (d f / d L^P_pr) ],
+    with H^P = (P|..) C_act and H'^P = (P|..)^T C_act (equal for the symmetric
+    AO tensor).  Columns of C outside ``orb`` get zero.  Returns (dAO, dC) with
+    the shapes of ``ao3c`` and ``C``.
+    """
+    ao = np.asarray(ao3c, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    ca = C[:, orb]
+    dL = np.asarray(dL, dtype=np.float64)
+    d_ao = np.einsum("mp,Ppq,nq->Pmn", ca, dL, ca, optimize=True)
+    h = np.einsum("Pmn,nq->Pmq", ao, ca, optimize=True)
+    ht = np.einsum("Pnm,nq->Pmq", ao, ca, optimize=True)
+    d_ca = np.einsum("Pmq,Prq->mr", h, dL, optimize=True) + np.einsum("Pmp,Ppr->mr", ht, dL, optimize=True)
+    d_c = np.zeros_like(C)
+    np.add.at(d_c, (slice(None), np.asarray(orb)), d_ca)
+    return d_ao, d_c
+
+
 def ao_to_mo_rows(ao3c, C, orb, rows):
     """L^P_{p q} for p in ``rows`` (indices into ``orb``) and all q in ``orb``.
 

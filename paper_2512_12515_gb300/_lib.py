@@ -87,6 +87,7 @@ SIGNATURES = {
     "pprpa_grad": (_I, [_P, _I, _P, _P, _I]),
     "pprpa_grad_vector": (_I, [_P, _I, _P, _P, _P, _I]),
     "pprpa_grad_ec": (_I, [_P, _P, _P, _I]),
+    "pprpa_grad_ao": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
@@ -310,6 +311,28 @@ class Context:
         p2, w2 = _ptr(deps, True)
         _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
         return dL, deps
+
+    def grad_ao(self, C, dL, ao3c=None, want_dao=True, want_dc=True):
+        """Adjoint of the AO->MO transform: (d/d(P|mu nu), d/dC) from d/dL^P_pq.
+
+        Arrays are all host (NumPy) or all device (torch); ``ao3c`` is needed for dC only."""
+        naux, n, _ = dL.shape
+        nb, nmo = C.shape
+        if want_dc and ao3c is None:
+            raise ValueError("dC needs ao3c")
+        host = isinstance(dL, np.ndarray)
+        new = (lambda shape: np.empty(shape)) if host else (lambda shape: dL.new_empty(shape))
+        d_ao = new((naux, nb, nb)) if want_dao else None
+        d_c = new((nb, nmo)) if want_dc else None
+        pc, wc = _ptr(C)
+        pl, wl = _ptr(dL)
+        pa, wa = _ptr(ao3c) if ao3c is not None else (None, wl)
+        po, wo = _ptr(d_ao, True) if d_ao is not None else (None, wl)
+        pq, wq = _ptr(d_c, True) if d_c is not None else (None, wl)
+        if len({wc, wl, wa, wo, wq}) != 1:
+            raise ValueError("every array must live on the same side")
+        _check(self.lib.pprpa_grad_ao(self._h, nb, naux, pc, pa, pl, po, pq, wl))
+        return d_ao, d_c
 
     def grad_vector(self, mult, z, dL=None, deps=None):
         """d(z^T M z)/dL^P_pq and d(z^T M z)/d eps_p for an explicit pair vector z."""

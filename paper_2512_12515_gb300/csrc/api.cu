@@ -277,6 +277,120 @@ int pprpa_set_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const doub
     return PPRPA_OK;
 }
 
+int pprpa_grad_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const double* ao3c,
+                  const double* dL, double* dAO, double* dC, int where) {
+    PP_TRY(check_ctx(c));
+    if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "grad_ao: call set_orbitals first");
+    if (nbasis <= 0 || naux <= 0 || !C || !dL || (where != PPRPA_HOST && where != PPRPA_DEVICE))
+        return set_error(PPRPA_ERR_ARG, "grad_ao: bad arguments");
+    if (dC && !ao3c) return set_error(PPRPA_ERR_ARG, "grad_ao: dC needs the AO integrals");
+    if (!dAO && !dC) return PPRPA_OK;
+    const int n = c->n(), nmo = c->nmo;
+    const int first = c->nocc - c->no;
+    cudaStream_t st = c->stream;
+    const bool host = where == PPRPA_HOST;
+    const int64_t nb2 = (int64_t)nbasis * nbasis, nbn = (int64_t)nbasis * n, n2 = (int64_t)n * n;
+    // active columns of C (nbasis x n)
+    double* d_Cact;
+    PP_TRY(ws_get(c, "gao_Cact", sizeof(double) * nbn, (void**)&d_Cact));
+    if (host) {
+        std::vector<double> ca((size_t)nbn);
+        for (int m = 0; m < nbasis; ++m)
+            for (int p = 0; p < n; ++p) ca[(size_t)m * n + p] = C[(size_t)m * nmo + first + p];
+        PP_CUDA(cudaMemcpyAsync(d_Cact, ca.data(), sizeof(double) * ca.size(), cudaMemcpyHostToDevice, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+    } else {
+        PP_CUDA(cudaMemcpy2DAsync(d_Cact, sizeof(double) * n, C + first, sizeof(double) * nmo,
+                                  sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
+    }
+    // chunk of P: dL slices, AO slices and the outputs staged on the device for host arguments,
+    // the half-transformed products always
+    const int64_t per_p = sizeof(double) * (nbn + (host ? n2 + (dAO ? nb2 : 0) + (dC ? nb2 : 0) : 0));
+    const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (2LL << 30) / per_p));
+    double *d_T, *d_dL = nullptr, *d_ao = nullptr, *d_out = nullptr, *d_dCact = nullptr;
+    PP_TRY(ws_get(c, "gao_T", sizeof(double) * nbn * pc, (void**)&d_T));
+    if (host) PP_TRY(ws_get(c, "gao_dL", sizeof(double) * n2 * pc, (void**)&d_dL));
+    if (host && dC) PP_TRY(ws_get(c, "gao_ao", sizeof(double) * nb2 * pc, (void**)&d_ao));
+    if (host && dAO) PP_TRY(ws_get(c, "gao_out", sizeof(double) * nb2 * pc, (void**)&d_out));
+    if (dC) PP_TRY(ws_get(c, "gao_dCact", sizeof(double) * nbn, (void**)&d_dCact));
+    for (int P0 = 0; P0 < naux; P0 += pc) {
+        const int np = std::min(pc, naux - P0);
+        const double* g;
+        if (host) {
+            PP_CUDA(cudaMemcpyAsync(d_dL, dL + (size_t)P0 * n2, sizeof(double) * n2 * np,
+                                    cudaMemcpyHostToDevice, st));
+            g = d_dL;
+        } else {
+            g = dL + (size_t)P0 * n2;
+        }
+        if (dAO) {
+            // d/d(P|mu nu) = C_act dL^P C_act^T
+            Dgemm g1;  // T^P = C_act dL^P  (nbasis x n)
+            g1.M = nbasis; g1.N = n; g1.K = n;
+            g1.A = d_Cact; g1.lda = n;
+            g1.B = g; g1.ldb = n; g1.sB1 = n2;
+            g1.C = d_T; g1.ldc = n; g1.sC1 = nbn;
+            g1.nb1 = np;
+            PP_TRY(dgemm(g1, st));
+            Dgemm g2;  // out^P = T^P C_act^T  (nbasis x nbasis)
+            g2.M = nbasis; g2.N = nbasis; g2.K = n;
+            g2.A = d_T; g2.lda = n; g2.sA1 = nbn;
+            g2.B = d_Cact; g2.ldb = n; g2.transB = 1;
+            g2.C = host ? d_out : dAO + (size_t)P0 * nb2; g2.ldc = nbasis; g2.sC1 = nb2;
+            g2.nb1 = np;
+            PP_TRY(dgemm(g2, st));
+            if (host)
+                PP_CUDA(cudaMemcpyAsync(dAO + (size_t)P0 * nb2, d_out, sizeof(double) * nb2 * np,
+                                        cudaMemcpyDeviceToHost, st));
+        }
+        if (dC) {
+            const double* src;
+            if (host) {
+                PP_CUDA(cudaMemcpyAsync(d_ao, ao3c + (size_t)P0 * nb2, sizeof(double) * nb2 * np,
+                                        cudaMemcpyHostToDevice, st));
+                src = d_ao;
+            } else {
+                src = ao3c + (size_t)P0 * nb2;
+            }
+            Dgemm g1;  // H^P = (P|mu nu) C_act  (nbasis x n)
+            g1.M = nbasis; g1.N = n; g1.K = nbasis;
+            g1.A = src; g1.lda = nbasis; g1.sA1 = nb2;
+            g1.B = d_Cact; g1.ldb = n;
+            g1.C = d_T; g1.ldc = n; g1.sC1 = nbn;
+            g1.nb1 = np;
+            PP_TRY(dgemm(g1, st));
+            // d/dC_act (+)= sum_P H^P (dL^P)^T + H^P dL^P  (the AO slices are symmetric)
+            for (int t = 0; t < 2; ++t) {
+                Dgemm g3;
+                g3.M = nbasis; g3.N = n; g3.K = n;
+                g3.A = d_T; g3.lda = n; g3.sAr = nbn;
+                g3.B = g; g3.ldb = n; g3.sBr = n2; g3.transB = t == 0 ? 1 : 0;
+                g3.C = d_dCact; g3.ldc = n;
+                g3.nr = np;
+                g3.beta = (P0 == 0 && t == 0) ? 0.0 : 1.0;
+                PP_TRY(dgemm(g3, st));
+            }
+        }
+        if (host) PP_CUDA(cudaStreamSynchronize(st));
+    }
+    if (dC) {
+        if (host) {
+            std::vector<double> da((size_t)nbn);
+            PP_CUDA(cudaMemcpyAsync(da.data(), d_dCact, sizeof(double) * nbn, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaStreamSynchronize(st));
+            std::fill(dC, dC + (size_t)nbasis * nmo, 0.0);
+            for (int m = 0; m < nbasis; ++m)
+                for (int p = 0; p < n; ++p) dC[(size_t)m * nmo + first + p] = da[(size_t)m * n + p];
+        } else {
+            PP_CUDA(cudaMemsetAsync(dC, 0, sizeof(double) * (size_t)nbasis * nmo, st));
+            PP_CUDA(cudaMemcpy2DAsync(dC + first, sizeof(double) * nmo, d_dCact, sizeof(double) * n,
+                                      sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
 int pprpa_set_mo(pprpa_ctx* c, int naux, const double* L, int where) {
     PP_TRY(check_ctx(c));
     if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "set_mo: call set_orbitals first");

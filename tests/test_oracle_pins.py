@@ -214,6 +214,67 @@ def test_gradient_matches_finite_differences(mult):
 
 
 @pytest.mark.parametrize("mult", [1, 3])
+def test_ao_side_adjoint_matches_finite_differences(mult):
+    """d omega / d (P|mu nu) and d omega / d C through the AO->MO transform, against central
+    differences of a root of the whole chain (AO integrals, C -> L -> M -> omega)."""
+    spec = synth.SystemSpec("t", 10, 3, 7, 2, 5, 41)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], 2, 5)
+    eps = s["eps"][orb]
+
+    def root(ao, C, key, r):
+        L = oracle.ao_to_mo(ao, C, orb)
+        M, nvv, noo = oracle.build_matrix(eps, 2, L, mult)
+        sol = oracle.solve_full(M, nvv, noo)
+        return sol["omega_" + key][r], sol["z_" + key][:, r], L
+
+    rng = np.random.default_rng(5)
+    h = 1e-5
+    for key, r in (("pp", 0), ("hh", -1)):
+        _, z, L = root(s["ao3c"], s["C"], key, r)
+        _, dL = oracle.grad_omega(eps, 2, L, mult, z)
+        d_ao, d_c = oracle.grad_ao(s["ao3c"], s["C"], orb, dL)
+        for _ in range(2):
+            E = rng.standard_normal(s["ao3c"].shape)
+            E = (E + E.transpose(0, 2, 1)) / np.linalg.norm(E)
+            fd = (root(s["ao3c"] + h * E, s["C"], key, r)[0] - root(s["ao3c"] - h * E, s["C"], key, r)[0]) / (2 * h)
+            an = float(np.sum(d_ao * E))
+            assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+            D = rng.standard_normal(s["C"].shape)
+            D /= np.linalg.norm(D)
+            fd = (root(s["ao3c"], s["C"] + h * D, key, r)[0] - root(s["ao3c"], s["C"] - h * D, key, r)[0]) / (2 * h)
+            an = float(np.sum(d_c * D))
+            assert abs(fd - an) < 1e-6 * max(1.0, abs(an))
+        # columns of C outside the active space do not enter L
+        inactive = np.setdiff1d(np.arange(spec.nmo), orb)
+        assert np.all(d_c[:, inactive] == 0.0)
+
+
+def test_ao_side_adjoint_of_a_general_functional():
+    """For f = sum_P,p,q G^P_pq L^P_pq with a non-symmetric G, f is linear in the AO tensor and
+    quadratic in C, so central differences are exact up to rounding; a transposed operand or
+    a dropped term in the adjoint changes the result."""
+    spec = synth.SystemSpec("t", 9, 3, 5, 2, 4, 43)
+    s = synth.make_system(spec)
+    orb = oracle.active_orbitals(s["occ"], 2, 4)
+    rng = np.random.default_rng(11)
+    G = rng.standard_normal((5, 6, 6))
+
+    def f(ao, C):
+        return float(np.sum(G * oracle.ao_to_mo(ao, C, orb)))
+
+    d_ao, d_c = oracle.grad_ao(s["ao3c"], s["C"], orb, G)
+    h = 1e-3
+    for _ in range(3):
+        E = rng.standard_normal(s["ao3c"].shape)  # entries independent, as in the adjoint
+        fd = (f(s["ao3c"] + h * E, s["C"]) - f(s["ao3c"] - h * E, s["C"])) / (2 * h)
+        assert abs(fd - float(np.sum(d_ao * E))) < 1e-9 * max(1.0, abs(fd))
+        D = rng.standard_normal(s["C"].shape)
+        fd = (f(s["ao3c"], s["C"] + h * D) - f(s["ao3c"], s["C"] - h * D)) / (2 * h)
+        assert abs(fd - float(np.sum(d_c * D))) < 1e-9 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("mult", [1, 3])
 def test_eps_gradient_is_density_diagonal_and_trace_rule(mult):
     """d omega / d eps_p = s D^2e_pp and Tr D^2e = +-2 (Sec. Density Matrix),
     so sum_p d omega / d eps_p = 2."""
