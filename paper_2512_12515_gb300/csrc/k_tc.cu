@@ -146,6 +146,90 @@ __device__ __forceinline__ void tma_3d_mc(uint32_t dst, const CUtensorMap* m, in
         : "memory");
 }
 
+// CTA-pair forms (tcgen05 cta_group::2): the copy lands in this CTA's shared memory and
+// completes its bytes on the mbarrier at cluster address `bar` (the pair leader's).
+__device__ __forceinline__ void tma_2d_pair(uint32_t dst, const CUtensorMap* m, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_3d_pair(uint32_t dst, const CUtensorMap* m, int x, int y, int z,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_4d_pair(uint32_t dst, const CUtensorMap* m, int x, int y, int z,
+                                            int w, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+        : "memory");
+}
+// Bulk tensor store of a shared-memory box to global memory (bulk-group completion), and
+// the waits on this thread's bulk groups: until their shared-memory reads are done, or
+// until their writes are complete.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     (uint64_t)m),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Address of the same shared variable in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+// Completion of the pair's MMAs arrives on the barrier at the same offset in every CTA of
+// `mask` (or only in this CTA for the unicast form).
+__device__ __forceinline__ void mma_commit_pair_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
@@ -174,10 +258,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128 (256 for a
+// CTA pair).
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, int m = TC_BM) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(TC_BM >> 4) << 24);
+           ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
@@ -189,10 +274,10 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
-// Instruction descriptor, kind::f8f6f4: E4M3 x E4M3 -> FP32, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int n) {
+// Instruction descriptor, kind::f8f6f4: E4M3 x E4M3 -> FP32, both K-major, M = 128 (256).
+__host__ __device__ constexpr uint32_t idesc_e4m3(int n, int m = TC_BM) {
     return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(TC_BM >> 4) << 24);
+           ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_e4m3(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
@@ -288,12 +373,19 @@ __device__ __forceinline__ ItemCoord decode_item(const TcParams& p, int item) {
 // Stage 2: one output tile and K slice for CL neighbouring vectors.
 // F8: stage-1 operands are E4M3 (kind::f8f6f4, 128 elements per 128-byte row); the
 // epilogue multiplies by the row (per auxiliary index) and column (per vector) scales.
-template <int NTERMS, bool BATCHED, int CL, bool F8 = false>
+// PAIR (CL = 2): the two CTAs compute one 256-row tile with tcgen05 cta_group::2 MMAs issued
+// by the leader (rank 0).  Each CTA holds its own 128 A rows and one half of the B tile
+// (N / 2 rows) and completes its copies on the leader's full barrier; the leader's commits
+// release the slots and publish the accumulators in both CTAs, and each epilogue warp of
+// either CTA releases an accumulator with one arrive on the leader's barrier.
+template <int NTERMS, bool BATCHED, int CL, bool F8 = false, bool PAIR = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA_hi,
                    const __grid_constant__ CUtensorMap tmA_lo,
                    const __grid_constant__ CUtensorMap tmB_hi,
-                   const __grid_constant__ CUtensorMap tmB_lo, const TcParams p,
+                   const __grid_constant__ CUtensorMap tmB_lo,
+                   const __grid_constant__ CUtensorMap tmT_hi,
+                   const __grid_constant__ CUtensorMap tmT_lo, const TcParams p,
                    const TcJob* __restrict__ jobs, const TcItem* __restrict__ items) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * TC_MAX_STAGES + 5];
@@ -305,7 +397,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.stages;
     const uint32_t a_bytes = TC_BM * TC_BK * 2;
-    const uint32_t b_slot = (uint32_t)p.slot_bn * TC_BK * 2;
+    static_assert(!PAIR || (CL == 2 && !BATCHED), "a CTA pair is a cluster of two");
+    const uint32_t b_slot = (uint32_t)(PAIR ? p.slot_bn / 2 : p.slot_bn) * TC_BK * 2;
     const uint32_t slot_bytes = (a_bytes + b_slot) * (NTERMS == 3 ? 2 : 1);
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
@@ -315,6 +408,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t done_bar = bar0 + 8u * (2 * TC_MAX_STAGES + 4);
 
     const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
+    const bool leader = !PAIR || crank == 0;
     // persistent loop bounds: work items, or groups of CL items (one per cluster)
     const int first = (int)(blockIdx.x / CL);
     const int stride = (int)(gridDim.x / CL);
@@ -326,7 +420,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if constexpr (CL > 1) {
             q = &p;
             mA_hi = &tmA_hi; mA_lo = &tmA_lo; mB_hi = &tmB_hi; mB_lo = &tmB_lo;
-            if (p.mode == 0) {
+            if (PAIR && p.mode == 1) {
+                // group = (K slice, vector, 256-row output tile); this CTA takes one half
+                const int tile = item % p.ntiles;
+                const int rest = item / p.ntiles;
+                const int batch = rest % p.nbatch;
+                const int split = rest / p.nbatch;
+                const int4 t = p.tile_list[tile];
+                c.m0 = t.x * (2 * TC_BM) + (int)crank * TC_BM;
+                c.n0 = t.y;
+                c.nw = t.z;
+                c.batch = batch;
+                const int per = (p.kb_total + p.nsplit - 1) / p.nsplit;
+                c.kb0 = split * per;
+                c.kb1 = min(p.kb_total, c.kb0 + per);
+            } else if (p.mode == 0) {
                 // group = (CL neighbouring M tiles, N tile)
                 const int nb = item % p.tiles_n;
                 const int mp = item / p.tiles_n;
@@ -372,22 +480,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         abort_flag = 0;
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
-            mbar_init(empty_bar(s), CL);  // every CTA of the cluster releases a slot
+            // every CTA of a multicast cluster releases a slot; a pair's leader releases both
+            mbar_init(empty_bar(s), PAIR ? 1 : CL);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull_bar(a), 1);
-            mbar_init(tempty_bar(a), 32 * TC_EPI_WARPS);
+            // pair: one arrive per epilogue warp of either CTA, on the leader's barrier
+            mbar_init(tempty_bar(a), PAIR ? 2 * TC_EPI_WARPS : 32 * TC_EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == TC_MMA_WARP) {
         const uint32_t ncols = p.tmem_cols;
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_slot)),
-                     "r"(ncols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            // one warp of each CTA of the pair allocates the same columns in both
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(ncols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tmem_slot)),
+                         "r"(ncols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -409,7 +528,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
                 fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
                 const uint32_t b_bytes = (uint32_t)q->BN * TC_BK * 2;
-                const uint32_t tx = (a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
+                // a pair's leader expects both CTAs' A rows and both halves of B
+                const uint32_t tx = ((PAIR ? 2 : 1) * a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
                 for (int kb = c.kb0; kb < c.kb1; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, &abort_flag, p.status)) {
                         ok = false;
@@ -417,11 +537,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t sbase = smem_u32(smem + (size_t)stage * slot_bytes);
                     const uint32_t fb = full_bar(stage);
-                    mbar_expect_tx(fb, tx);
+                    if (leader) mbar_expect_tx(fb, tx);
                     const uint32_t a_hi = sbase, b_hi = sbase + a_bytes;
                     const uint32_t a_lo = sbase + a_bytes + b_slot,
                                    b_lo = sbase + 2 * a_bytes + b_slot;
-                    if (q->mode == 0) {
+                    if constexpr (PAIR) {
+                        // own A rows and own half of B, completing on the leader's barrier
+                        const uint32_t fbl = mapa_rank(fb, 0);
+                        const int ybh = c.n0 + (int)crank * (c.nw / 2);
+                        if (q->mode == 0) {
+                            const int x = q->a_col_off + kb * BKE;
+                            tma_2d_pair(a_hi, mA_hi, x, c.m0, fbl);
+                            tma_2d_pair(b_hi, mB_hi, kb * BKE, ybh, fbl);
+                            if (NTERMS == 3) {
+                                tma_2d_pair(a_lo, mA_lo, x, c.m0, fbl);
+                                tma_2d_pair(b_lo, mB_lo, kb * BKE, ybh, fbl);
+                            }
+                        } else {
+                            const int P = kb / q->kq_blocks;
+                            const int qq = (kb % q->kq_blocks) * TC_BK;
+                            tma_4d_pair(a_hi, mA_hi, qq, c.batch, q->row_off + c.m0, P, fbl);
+                            tma_3d_pair(b_hi, mB_hi, qq, q->col_off + ybh, P, fbl);
+                            if (NTERMS == 3) {
+                                tma_4d_pair(a_lo, mA_lo, qq, c.batch, q->row_off + c.m0, P, fbl);
+                                tma_3d_pair(b_lo, mB_lo, qq, q->col_off + ybh, P, fbl);
+                            }
+                        }
+                    } else if (q->mode == 0) {
                         const int x = q->a_col_off + kb * BKE;
                         tma_2d(a_hi, mA_hi, x, c.m0, fb);
                         if constexpr (CL > 1) {
@@ -467,8 +609,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             }
-            if (abort_flag) {
-                // let every copy this thread issued land before the CTA exits
+            if (abort_flag && leader) {
+                // let every copy this thread issued land before the CTA exits (a pair's
+                // copies complete on the leader's barriers; the final cluster barrier holds
+                // the other CTA until the leader has drained them)
                 for (int s = 0; s < S; ++s) {
                     if (!(issued_mask & (1u << s))) continue;
                     const uint32_t par = (issued_par >> s) & 1u;
@@ -479,7 +623,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else if (warp == TC_MMA_WARP) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             // ---------------- MMA issuer ----------------
             int stage = 0;
             uint32_t phase = 0;
@@ -492,7 +636,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const CUtensorMap *mA_hi, *mA_lo, *mB_hi, *mB_lo;
                 fetch(item, c, q, mA_hi, mA_lo, mB_hi, mB_lo);
                 const int bn = c.nw;
-                const uint32_t idesc = F8 ? idesc_e4m3(bn) : idesc_bf16(bn);
+                constexpr int MM = PAIR ? 2 * TC_BM : TC_BM;
+                const uint32_t idesc = F8 ? idesc_e4m3(bn, MM) : idesc_bf16(bn, MM);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(acc * p.slot_bn);
@@ -510,6 +655,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int k = 0; k < TC_BK / 16; ++k) {
                         const uint32_t off = k * 32;
                         const uint32_t first = (kb == c.kb0 && k == 0) ? 0u : 1u;
+                        if constexpr (PAIR) {
+                            if constexpr (F8) {
+                                mma_e4m3_pair(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
+                                continue;
+                            }
+                            mma_bf16_pair(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
+                            if (NTERMS == 3) {
+                                mma_bf16_pair(dt, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+                                mma_bf16_pair(dt, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+                            }
+                            continue;
+                        }
                         if constexpr (F8) {
                             mma_e4m3(dt, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, first);
                             continue;
@@ -520,7 +677,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             mma_bf16(dt, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
                         }
                     }
-                    if constexpr (CL > 1) mma_commit_mc(empty_bar(stage), (uint16_t)((1u << CL) - 1u));
+                    if constexpr (PAIR) mma_commit_pair_mc(empty_bar(stage), (uint16_t)3u);
+                    else if constexpr (CL > 1) mma_commit_mc(empty_bar(stage), (uint16_t)((1u << CL) - 1u));
                     else mma_commit(empty_bar(stage));
                     if (++stage == S) {
                         stage = 0;
@@ -528,12 +686,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                mma_commit(tfull_bar(acc));
+                if constexpr (PAIR) mma_commit_pair_mc(tfull_bar(acc), (uint16_t)3u);
+                else mma_commit(tfull_bar(acc));
                 acc ^= 1;
                 if (acc == 0) acc_phase ^= 1u;
             }
-            // all MMAs of this CTA complete before TMEM is released
-            mma_commit(done_bar);
+            // all MMAs of this CTA (of the pair) complete before TMEM is released
+            if constexpr (PAIR) mma_commit_pair(done_bar);
+            else mma_commit(done_bar);
             const unsigned long long t0 = gtimer();
             while (!mbar_try(done_bar, 0) && gtimer() - t0 < TC_WAIT_NS) {
             }
@@ -543,6 +703,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // warp w reads TMEM lanes 32 * (w % 4) .. + 31 (one output row per thread) and the
         // columns [cbeg, cend) of its half of the tile
         const int quarter = warp & 3, half = warp >> 2;
+        bool bulk_pending = false;  // this warp's staging tile is being read by a bulk store
         int acc = 0;
         uint32_t acc_phase = 0;
         const int row = quarter * 32 + lane;
@@ -590,6 +751,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int cb = c0 + 32 * hc;
                             float v[32];
                             if (cb < cend) tmem_ld32(tbase + cb, cb + 16 < cend, v);
+                            if (hc == 0 && bulk_pending) {
+                                // the previous bulk store has read the staging tile
+                                if (lane == 0) bulk_wait_read();
+                                __syncwarp();
+                                bulk_pending = false;
+                            }
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
                                 const int g = 4 * hc + h;
@@ -621,19 +788,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                             }
                         }
-                        // row pass: lane writes group gl of rows 4 i + lane / 8
-                        const int ng = c.n0 + c0 + 8 * gl;
+                        // the chunk's first column: vector jc, column ccc inside it
+                        const int nc = c.n0 + c0;
+                        const int jc = nc / n_per_j, ccc = nc - jc * n_per_j;
+                        // whole chunk inside one vector and inside the tile: one bulk tensor
+                        // store of the staged box (its layout is the 128-byte swizzle)
+                        const bool bulk = p.t_store && c0 + 64 <= cend && ccc + 64 <= n_per_j &&
+                                          nc + 64 <= n_total;
+                        // row pass otherwise: lane writes group gl of rows 4 i + lane / 8
+                        const int ng = nc + 8 * gl;
                         const bool gok = c0 + 8 * gl < cend && ng < n_total;
                         const int jg = ng / n_per_j;
                         const int64_t cg = (int64_t)jg * n_pad + (ng - jg * n_per_j);
 #pragma unroll
                         for (int t = 0; t < (NTERMS == 3 ? 2 : 1); ++t) {
                             if (t == 1) {
+                                if (bulk) {
+                                    if (lane == 0) bulk_wait_read();
+                                    __syncwarp();
+                                }
 #pragma unroll
                                 for (int g = 0; g < 8; ++g)
                                     if constexpr (NTERMS == 3)
                                         *(uint4*)(stg + lane * 128 + ((g ^ (lane & 7)) << 4)) =
                                             make_uint4(lo_w[g][0], lo_w[g][1], lo_w[g][2], lo_w[g][3]);
+                            }
+                            if (bulk) {
+                                fence_proxy_async_smem();
+                                __syncwarp();
+                                if (lane == 0 && R0 < q->M_rows) {
+                                    tma_store_3d(t == 0 ? &tmT_hi : &tmT_lo, smem_u32(stg), ccc, jc, (int)R0);
+                                    bulk_commit();
+                                }
+                                continue;
                             }
                             __syncwarp();
                             __nv_bfloat16* dst = t == 0 ? t_hi0 : t_lo0;
@@ -646,6 +833,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                             __syncwarp();
                         }
+                        if (bulk) bulk_pending = true;
                     }
                 } else
                 for (int c0 = cbeg; c0 < cend; c0 += 32) {
@@ -718,10 +906,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             tc_fence_before();
-            mbar_arrive(tempty_bar(acc));
+            if constexpr (PAIR) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa_rank(tempty_bar(acc), 0));
+            } else {
+                mbar_arrive(tempty_bar(acc));
+            }
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
+        // the bulk stores of T are complete before the CTA exits
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
 
     tc_fence_before();
@@ -731,9 +927,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if constexpr (CL > 1) cluster_sync_all();
     if (warp == TC_MMA_WARP) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"((uint32_t)p.tmem_cols)
-                     : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"((uint32_t)p.tmem_cols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"((uint32_t)p.tmem_cols)
+                         : "memory");
     }
 }
 
@@ -808,10 +1009,23 @@ static size_t plan_smem(TcParams& p, int bn, int nterms, bool want_epi) {
     return (size_t)slot_bytes_for(bn, nterms) * p.stages + 1024 + (p.epi_stage ? TC_EPI_BYTES : 0);
 }
 
+// Zero-filled stand-in for tensor-map parameters a launch does not use.
+static const CUtensorMap& no_map() {
+    static CUtensorMap m = [] {
+        CUtensorMap z;
+        std::memset(&z, 0, sizeof(z));
+        return z;
+    }();
+    return m;
+}
+
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st,
-                   bool f8) {
+                   bool f8, const CUtensorMap* t_hi, const CUtensorMap* t_lo) {
     if (p.total_items <= 0) return PPRPA_OK;
+    p.t_store = (p.mode == 0 && t_hi) ? 1 : 0;
+    const CUtensorMap& th = t_hi ? *t_hi : no_map();
+    const CUtensorMap& tl = t_lo ? *t_lo : th;
     if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0)
         return set_error(PPRPA_ERR_ARG, "tc_gemm: BN must be a multiple of 16 in [16, 256]");
     p.slot_bn = p.BN;
@@ -824,13 +1038,13 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
     if (f8) {
         if (p.mode != 0 || nterms != 1) return set_error(PPRPA_ERR_ARG, "tc_gemm: FP8 is stage 1, one term");
         cudaFuncSetAttribute(tc_gemm_kernel<1, false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1, false, 1, true><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+        tc_gemm_kernel<1, false, 1, true><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, th, tl, p, nullptr, nullptr);
     } else if (nterms == 3) {
         cudaFuncSetAttribute(tc_gemm_kernel<3, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<3, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+        tc_gemm_kernel<3, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, th, tl, p, nullptr, nullptr);
     } else {
         cudaFuncSetAttribute(tc_gemm_kernel<1, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, p, nullptr, nullptr);
+        tc_gemm_kernel<1, false, 1><<<grid, TC_THREADS, smem, st>>>(a_hi, a_lo, b_hi, b_lo, th, tl, p, nullptr, nullptr);
     }
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
@@ -839,11 +1053,12 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
 // Stage 1 on clusters of CL CTAs sharing the B tile (TMA multicast).  Items are groups of
 // CL M tiles; p.total_items is set here to the group count.  The B tensor maps must have
 // boxes of BN / CL rows.
-template <int NT, int CL, bool F8 = false>
+template <int NT, int CL, bool F8 = false, bool PAIR = false>
 static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
-                                  const CUtensorMap& b_hi, const CUtensorMap& b_lo, const TcParams& p,
+                                  const CUtensorMap& b_hi, const CUtensorMap& b_lo,
+                                  const CUtensorMap& t_hi, const CUtensorMap& t_lo, const TcParams& p,
                                   size_t smem, int groups, int num_sms, cudaStream_t st) {
-    cudaFuncSetAttribute(tc_gemm_kernel<NT, false, CL, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(tc_gemm_kernel<NT, false, CL, F8, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -858,18 +1073,25 @@ static cudaError_t launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_
     int clusters = std::min(groups, num_sms / CL);
     cfg.gridDim = dim3(CL * clusters);
     int maxc = 0;
-    if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<NT, false, CL, F8>, &cfg) == cudaSuccess && maxc > 0)
+    if (cudaOccupancyMaxActiveClusters(&maxc, tc_gemm_kernel<NT, false, CL, F8, PAIR>, &cfg) == cudaSuccess && maxc > 0)
         clusters = std::min(clusters, maxc);
     cfg.gridDim = dim3(CL * clusters);
     const TcJob* nj = nullptr;
     const TcItem* ni = nullptr;
-    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<NT, false, CL, F8>, a_hi, a_lo, b_hi, b_lo, p, nj, ni);
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<NT, false, CL, F8, PAIR>, a_hi, a_lo, b_hi, b_lo, t_hi,
+                              t_lo, p, nj, ni);
 }
 
 int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
-                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8) {
+                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8, bool pair,
+                           const CUtensorMap* t_hi, const CUtensorMap* t_lo) {
+    p.t_store = (p.mode == 0 && t_hi) ? 1 : 0;
+    const CUtensorMap& th = t_hi ? *t_hi : no_map();
+    const CUtensorMap& tl = t_lo ? *t_lo : th;
     if (cl != 2 && cl != 4) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: cluster size 2 or 4");
+    if (pair && (cl != 2 || (p.BN % 32) != 0))
+        return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: a CTA pair is a cluster of 2 with BN a multiple of 32");
     // each CTA loads BN / cl rows of the B tile: a whole number of 8-row swizzle atoms
     if (p.BN < 16 || p.BN > 256 || (p.BN % 16) != 0 || (p.BN % (8 * cl)) != 0)
         return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: BN must be a multiple of 16 and of 8 * cluster size");
@@ -880,28 +1102,35 @@ int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
     } else {
         if (!p.tile_list || p.ntiles <= 0 || p.nbatch <= 0 || p.nsplit <= 0)
             return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: stage-2 parameters missing");
-        groups = (int64_t)p.ntiles * ceil_div(p.nbatch, cl) * p.nsplit;
+        // pair: one group per (256-row tile, vector, K slice); else CL vectors per group
+        groups = (int64_t)p.ntiles * (pair ? p.nbatch : ceil_div(p.nbatch, cl)) * p.nsplit;
     }
     if (groups <= 0) return PPRPA_OK;
     if (groups > INT32_MAX) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: too many tiles");
     p.total_items = (int)groups;
     p.slot_bn = p.BN;
-    const size_t smem = plan_smem(p, p.BN, nterms, p.mode == 0);
+    // a pair's CTA holds half of the B tile
+    const size_t smem = plan_smem(p, pair ? p.BN / 2 : p.BN, nterms, p.mode == 0);
     if (p.stages < 2) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: tile too large for shared memory");
     int cols = 32;
     while (cols < 2 * p.BN) cols <<= 1;
     p.tmem_cols = cols;
     cudaError_t e;
-    if (f8) {
+    if (pair) {
+        if (f8 && nterms != 1) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: FP8 is one term");
+        e = f8 ? launch_cluster<1, 2, true, true>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st)
+           : nterms == 3 ? launch_cluster<3, 2, false, true>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st)
+                         : launch_cluster<1, 2, false, true>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st);
+    } else if (f8) {
         if (nterms != 1) return set_error(PPRPA_ERR_ARG, "tc_gemm_cluster: FP8 is one term");
-        e = cl == 2 ? launch_cluster<1, 2, true>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
-                    : launch_cluster<1, 4, true>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
+        e = cl == 2 ? launch_cluster<1, 2, true>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<1, 4, true>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st);
     } else if (nterms == 3) {
-        e = cl == 2 ? launch_cluster<3, 2>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
-                    : launch_cluster<3, 4>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
+        e = cl == 2 ? launch_cluster<3, 2>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<3, 4>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st);
     } else {
-        e = cl == 2 ? launch_cluster<1, 2>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st)
-                    : launch_cluster<1, 4>(a_hi, a_lo, b_hi_part, b_lo_part, p, smem, (int)groups, num_sms, st);
+        e = cl == 2 ? launch_cluster<1, 2>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st)
+                    : launch_cluster<1, 4>(a_hi, a_lo, b_hi_part, b_lo_part, th, tl, p, smem, (int)groups, num_sms, st);
     }
     if (e != cudaSuccess) return set_error(PPRPA_ERR_CUDA, std::string("cluster launch: ") + cudaGetErrorString(e));
     PP_CHECK_LAUNCH();
@@ -928,10 +1157,12 @@ int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_ite
     std::memset(&dummy, 0, sizeof(dummy));
     if (nterms == 3) {
         cudaFuncSetAttribute(tc_gemm_kernel<3, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<3, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
+        tc_gemm_kernel<3, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, dummy, dummy, p,
+                                                                    jobs, items);
     } else {
         cudaFuncSetAttribute(tc_gemm_kernel<1, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc_gemm_kernel<1, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, p, jobs, items);
+        tc_gemm_kernel<1, true, 1><<<grid, TC_THREADS, smem, st>>>(dummy, dummy, dummy, dummy, dummy, dummy, p,
+                                                                    jobs, items);
     }
     PP_CHECK_LAUNCH();
     return PPRPA_OK;

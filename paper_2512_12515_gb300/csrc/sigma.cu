@@ -134,18 +134,18 @@ int ensure_fp8(pprpa_ctx* c) {
 }
 
 // Output tiles of the second stage over the upper triangle (row <= column) of a block of
-// `valid` rows: each 128-row M tile starting at row r0 covers the columns [r0, valid) in
-// near-equal widths, multiples of 16 and at most BN, so that only the diagonal 128 x 128
-// corner and the 16-column rounding are computed beyond the triangle.
-static std::vector<int4> triangle_tiles(int valid, int BN) {
+// `valid` rows: each M tile of `mrows` rows starting at row r0 covers the columns [r0, valid)
+// in near-equal widths, multiples of `wmul` and at most BN, so that only the diagonal corner
+// and the rounding are computed beyond the triangle.  Entry: (M tile, first column, width).
+static std::vector<int4> triangle_tiles(int valid, int BN, int mrows = 128, int wmul = 16) {
     std::vector<int4> t;
-    const int mt = (int)ceil_div(valid, 128);
+    const int mt = (int)ceil_div(valid, mrows);
     for (int mb = 0; mb < mt; ++mb) {
-        const int r0 = mb * 128, len = valid - r0;
+        const int r0 = mb * mrows, len = valid - r0;
         const int nch = (int)ceil_div(len, BN);
-        const int w = std::min(BN, (int)round_up(ceil_div(len, nch), 16));
+        const int w = std::min(BN, (int)round_up(ceil_div(len, nch), wmul));
         for (int n0 = r0; n0 < valid; n0 += w)
-            t.push_back(make_int4(mb, n0, std::min(w, (int)round_up(valid - n0, 16)), 0));
+            t.push_back(make_int4(mb, n0, std::min(w, (int)round_up(valid - n0, wmul)), 0));
     }
     return t;
 }
@@ -168,7 +168,9 @@ int stage2_bn(int valid) {
 // Launch with optional event timing (pprpa_profile).
 static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap& a_hi,
                         const CUtensorMap& a_lo, const CUtensorMap& b_hi, const CUtensorMap& b_lo,
-                        const TcParams& p, int nterms, int cluster = 1, bool f8 = false) {
+                        const TcParams& p, int nterms, int cluster = 1, bool f8 = false,
+                        bool pair = false, const CUtensorMap* t_hi = nullptr,
+                        const CUtensorMap* t_lo = nullptr) {
     ProfRec r;
     const bool rec = c->profile && c->prof.size() < 200000;
     if (rec) {
@@ -179,8 +181,9 @@ static int timed_launch(pprpa_ctx* c, int kind, double flops, const CUtensorMap&
         PP_CUDA(cudaEventRecord(r.a, c->stream));
     }
     if (cluster > 1)
-        PP_TRY(tc_gemm_launch_cluster(a_hi, a_lo, b_hi, b_lo, p, nterms, cluster, c->num_sms, c->stream, f8));
-    else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream, f8));
+        PP_TRY(tc_gemm_launch_cluster(a_hi, a_lo, b_hi, b_lo, p, nterms, cluster, c->num_sms, c->stream, f8,
+                                      pair, t_hi, t_lo));
+    else PP_TRY(tc_gemm_launch(a_hi, a_lo, b_hi, b_lo, p, nterms, c->num_sms, c->stream, f8, t_hi, t_lo));
     if (rec) {
         PP_CUDA(cudaEventRecord(r.b, c->stream));
         c->prof.push_back(r);
@@ -223,6 +226,9 @@ struct TcJobHost {
     double flops = 0.0;  // algorithmic
     int cluster = 1;                     // clusters of this many CTAs sharing the B tile
     bool f8 = false;                     // E4M3 operands (stage 1 of the FP8 form)
+    bool pair = false;                   // cluster of 2 as one tcgen05 CTA pair (M = 256)
+    bool t_store = false;                // stage 1: T written by bulk tensor stores
+    CUtensorMap t_hi_map, t_lo_map;      // T of this block: (column, vector, row), box 64 x 1 x 32
     CUtensorMap b_hi_half, b_lo_half;    // B boxes of BN / cluster rows for the cluster form
 };
 
@@ -329,7 +335,8 @@ static int tile_bn(pprpa_ctx* c, int stage, int sz, int k, int szp) {
 
 // Jobs of one P chunk [P0, P0 + npc).
 static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vector<TcJobHost>& s1,
-                   std::vector<TcJobHost>& s2, std::vector<std::vector<int4>>& tiles) {
+                   std::vector<TcJobHost>& s2, std::vector<std::vector<int4>>& tiles,
+                   bool single_launch = true) {
     const PadMap pm = pr.pm;
     const int no = c->no, nv = c->nv, k = pr.k;
     const int64_t np = pm.n_pad;
@@ -392,11 +399,28 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         p.total_items = (int)items;
         h.kind = split ? 2 : 0;
         h.f8 = pr.f8;
+        // T of this block as a 3-D tensor (column inside the block, vector, row R) for bulk
+        // stores of 32 x 64 boxes; blocks narrower than one box keep per-thread stores.
+        // Measured at the 50 + 600 active, naux 2700 case: faster for the FP8 form (stage 1
+        // 1200 -> 1233 TF/s), not for BF16 (877 -> 859), so by default only for FP8.
+        if (env_int("PPRPA_TSTORE", pr.f8 ? 1 : 0) && szp >= 64) {
+            const uint64_t tdims[3] = {(uint64_t)szp, (uint64_t)k, (uint64_t)p.M_rows};
+            const uint64_t tstr[2] = {(uint64_t)np * 2, (uint64_t)k * np * 2};
+            const uint32_t tbox[3] = {64, 1, 32};
+            PP_TRY(make_tmap_bf16(&h.t_hi_map, pr.t_hi + p.t_col_off, 3, tdims, tstr, tbox));
+            PP_TRY(make_tmap_bf16(&h.t_lo_map, (split ? pr.t_lo : pr.t_hi) + p.t_col_off, 3, tdims, tstr, tbox));
+            h.t_store = true;
+        }
         h.flops = 2.0 * npc * (double)(no + nv) * (double)sz * sz * k;
-        // clusters of CTAs share the B tile when there are enough M tiles to group
+        // clusters of CTAs share the B tile when there are enough M tiles to group: either a
+        // tcgen05 CTA pair (each CTA holds half of B) or a multicast cluster (each holds all)
         int cl = env_int("PPRPA_CLUSTER", 4);
         while (cl > 1 && (BN % (16 * cl) != 0 || ceil_div(p.M_rows, 128) < cl)) cl /= 2;
         h.cluster = cl == 2 || cl == 4 ? cl : 1;
+        if (single_launch && env_int("PPRPA_PAIR1", 0) && BN % 32 == 0 && ceil_div(p.M_rows, 128) >= 2) {
+            h.cluster = 2;
+            h.pair = true;
+        }
         if (h.cluster > 1) {
             const uint32_t hbox[2] = {bke, (uint32_t)(BN / h.cluster)};
             if (pr.f8) {
@@ -413,8 +437,11 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         const int sz = blk == 0 ? nv : no;
         if (sz == 0) continue;
         const int off = blk == 0 ? pm.no_p : 0;
-        const int BN = tile_bn(c, 2, sz, k, 0);
-        tiles.push_back(triangle_tiles(sz, BN));
+        // stage 2 as tcgen05 CTA pairs: 256-row tiles, each CTA holding half of the L^P tile
+        const bool pair2 = single_launch && env_int("PPRPA_PAIR2", 0) != 0;
+        int BN = tile_bn(c, 2, sz, k, 0);
+        if (pair2) BN = (int)std::min<int64_t>(256, round_up(BN, 32));
+        tiles.push_back(pair2 ? triangle_tiles(sz, BN, 256, 32) : triangle_tiles(sz, BN));
         const std::vector<int4>& tl = tiles.back();
         TcJobHost h;
         TcJob& j = h.job;
@@ -441,7 +468,7 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         // accumulation loses accuracy over very long reductions (partial sums of the
         // slices are added in FP32 in L2)
         const int64_t base_items = (int64_t)p.ntiles * k;
-        int64_t ns = ceil_div(4LL * c->num_sms, base_items);
+        int64_t ns = ceil_div(4LL * (pair2 ? c->num_sms / 2 : c->num_sms), base_items);
         ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max(1, p.kb_total / 8)));
         const int pcap = env_int(split ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", split ? 2 : 128);
         if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
@@ -459,7 +486,11 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         // divides k and BN / 4 is whole swizzle atoms, else 2
         int cl2 = env_int("PPRPA_CLUSTER2", -1);
         if (cl2 < 0) cl2 = (k % 4 == 0 && BN % 32 == 0) ? 4 : (k >= 2 ? 2 : 1);
-        if ((cl2 == 2 || cl2 == 4) && BN % 16 == 0 && BN % (8 * cl2) == 0 && k >= 2) {
+        if (pair2) {
+            cl2 = 2;
+            h.pair = true;
+        }
+        if ((cl2 == 2 || cl2 == 4) && BN % 16 == 0 && BN % (8 * cl2) == 0 && (k >= 2 || pair2)) {
             h.cluster = cl2;
             const uint32_t hbox[3] = {64, (uint32_t)(BN / cl2), 1};
             PP_TRY(make_tmap_bf16(&h.b_hi_half, Lh, 3, bdims, bstr, hbox));
@@ -483,12 +514,14 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
         std::vector<std::vector<int4>> tiles;
         PP_TRY(tc_jobs(c, pr, P0, npc, s1, s2, tiles));
         for (auto& h : s1) {
+            const CUtensorMap* th = h.t_store ? &h.t_hi_map : nullptr;
+            const CUtensorMap* tl = h.t_store ? &h.t_lo_map : nullptr;
             if (h.cluster > 1)
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
-                                    h.b_lo_half, h.job.p, nterms, h.cluster, h.f8));
+                                    h.b_lo_half, h.job.p, nterms, h.cluster, h.f8, h.pair, th, tl));
             else
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
-                                    h.job.b_lo, h.job.p, nterms, 1, h.f8));
+                                    h.job.b_lo, h.job.p, nterms, 1, h.f8, false, th, tl));
         }
         for (size_t b = 0; b < s2.size(); ++b) {
             TcJobHost& h = s2[b];
@@ -499,7 +532,7 @@ int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, 
             h.job.p.tile_list = d_tiles;
             if (h.cluster > 1)
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.b_hi_half,
-                                    h.b_lo_half, h.job.p, nterms, h.cluster));
+                                    h.b_lo_half, h.job.p, nterms, h.cluster, false, h.pair));
             else
                 PP_TRY(timed_launch(c, h.kind, h.flops, h.job.a_hi, h.job.a_lo, h.job.b_hi,
                                     h.job.b_lo, h.job.p, nterms));
@@ -616,7 +649,7 @@ int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int
         if (bp->prs[m].pc < c->naux)
             return set_error(PPRPA_ERR_ARG, "sigma_batch: a molecule's intermediate exceeds the T budget");
         const size_t before = tiles.size(), s2_before = s2.size();
-        PP_TRY(tc_jobs(c, bp->prs[m], 0, c->naux, s1, s2, tiles));
+        PP_TRY(tc_jobs(c, bp->prs[m], 0, c->naux, s1, s2, tiles, false));
         for (size_t t = s2_before; t < s2.size(); ++t) s2_tile_index.push_back((int)(before + (t - s2_before)));
     }
     std::vector<TcJob> j1, j2;

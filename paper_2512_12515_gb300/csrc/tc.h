@@ -41,6 +41,7 @@ struct TcParams {
     // set by the launcher: shared memory past the pipeline slots holds one 32 x 128-byte
     // staging tile per epilogue warp, used to write stage-1 output rows coalesced
     int epi_stage = 0;
+    int t_store = 0;  // set by the launcher: stage-1 T written by bulk tensor stores
 };
 
 // Batched form: one job per (molecule, stage block); tensor maps and parameters in global
@@ -58,12 +59,17 @@ int make_tmap_bf16(CUtensorMap* map, const void* ptr, int rank, const uint64_t* 
 int make_tmap(CUtensorMap* map, const void* ptr, int rank, const uint64_t* dims,
               const uint64_t* strides_bytes, const uint32_t* box, int elt_bytes);
 int tc_stages_for(int BN, int nterms, bool epi_stage = false);
+// t_hi / t_lo (stage 1, optional): 3-D maps of T (column in the block, vector, row) with a
+// 64 x 1 x 32 box and 128-byte swizzle, for bulk tensor stores of the output.
 int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUtensorMap& b_hi,
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms,
-                   cudaStream_t st, bool f8 = false);
+                   cudaStream_t st, bool f8 = false, const CUtensorMap* t_hi = nullptr,
+                   const CUtensorMap* t_lo = nullptr);
 int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
-                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8 = false);
+                           int nterms, int cl, int num_sms, cudaStream_t st, bool f8 = false,
+                           bool pair = false, const CUtensorMap* t_hi = nullptr,
+                           const CUtensorMap* t_lo = nullptr);
 int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_items, int max_bn,
                            int nterms, int num_sms, int* status, cudaStream_t st);
 

@@ -284,3 +284,27 @@ def test_correlation_energy_gradient(pp, mult):
         D /= np.linalg.norm(D)
         fd = (ec(eps, L + h * D) - ec(eps, L - h * D)) / (2 * h)
         assert abs(fd - float(np.sum(dL * D))) < 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("env", [{"PPRPA_PAIR1": "1", "PPRPA_PAIR2": "1"}, {"PPRPA_TSTORE": "1"},
+                                 {"PPRPA_TSTORE": "0", "PPRPA_CLUSTER": "1", "PPRPA_CLUSTER2": "1"}])
+@pytest.mark.parametrize("mult", [1, 3])
+def test_sigma_alternative_tensor_core_forms(pp, monkeypatch, env, mult):
+    """The non-default launch forms of the sandwich give the same sigma: tcgen05 CTA pairs
+    (M = 256 tiles, each CTA holding half of B), bulk tensor stores of T, and single-CTA
+    launches without clusters."""
+    for k_, v in env.items():
+        monkeypatch.setenv(k_, v)
+    spec, s, L, eps = make(13, 70, 97, 4)
+    M, nvv, noo = oracle.build_matrix(eps, 13, L, mult)
+    Z = synth.random_trial_vectors(nvv + noo, 5, 9)
+    ref = Z @ M.T
+    two_e = Z @ (M - np.diag(np.diag(M))).T
+    scale = np.abs(two_e).max()
+    with gpu_ctx(pp, spec, s) as c:
+        s16 = c.sigma(mult, Z, pp.PREC_BF16)
+        s48 = c.sigma(mult, Z, pp.PREC_BF16_SPLIT)
+        s8 = c.sigma(mult, Z, pp.PREC_FP8)
+    assert np.abs(s16 - ref).max() <= 2e-2 * scale
+    assert np.abs(s48 - ref).max() <= 2e-5 * scale
+    assert np.linalg.norm(s8 - ref) <= 0.06 * np.linalg.norm(two_e)
