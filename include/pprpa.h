@@ -228,6 +228,22 @@ int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double
  * be NULL.  Host or device per `where`. */
 int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
 
+/* pprpa_analyze: analysis outputs of root `root` of the last pprpa_solve (either channel).
+ * With the root's X (nv x nv) and Y (no x no) viewed as upper-triangular matrices over the
+ * pair list (Sec. "Natural Transition Orbital"):
+ *   D2e[n][n]: the two-electron addition/removal density matrix of Sec. "Density Matrix",
+ *     active-orbital order (occupied first): virtual block X X^T + X^T X, occupied block
+ *     -(Y Y^T + Y^T Y), zero elsewhere; its trace is +2 (addition) or -2 (removal), and its
+ *     diagonal times z^T W z is d omega / d eps.
+ *   lam_p[nv], Cp1[nv][nv], Cp2[nv][nv]: NTO weights (descending) and coefficient matrices of
+ *     X = Cp1 diag(sqrt(lam_p)) Cp2^T (Eq. nto_pp); lam_h[no], Ch1, Ch2 likewise for Y
+ *     (Eq. nto_hh).  sum(lam_p) - sum(lam_h) = +-1.  Each Cp1 / Ch1 column has its
+ *     largest-magnitude entry positive; columns of Cp2 / Ch2 with zero weight are zero.
+ * Any output may be NULL; NTOs need nv (no) <= 1024.  FP64 on the device (the NTOs through a
+ * one-CTA Jacobi eigensolver of X X^T); outputs host or device per `where`. */
+int pprpa_analyze(pprpa_ctx* ctx, int root, double* D2e, double* lam_p, double* lam_h,
+                  double* Cp1, double* Cp2, double* Ch1, double* Ch2, int where);
+
 /* pprpa_grad_ao: adjoint of the AO->MO transform of pprpa_set_ao, the step from the
  * MO-space gradient of pprpa_grad / pprpa_grad_ec / pprpa_grad_vector back to the AO inputs
  * (the chain toward the nuclear gradients of Sec. "Analytic Gradient").  With

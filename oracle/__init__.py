@@ -23,6 +23,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   chain (AO integrals or MO coefficients -> L -> M -> omega).
 * ri_sigma / davidson: pinned by the explicit matrix (sigma) and by full
   diagonalisation (Davidson roots).
+* two_e_density, nto: pinned by the trace rule, by the epsilon gradient (the
+  diagonal), by reconstructing X and Y from their NTOs and by the identity
+  X X^T + X^T X = C^p1 L C^p1^T + C^p2 L C^p2^T between the two definitions.
 * eigenvector phase: fixed by convention (largest-magnitude component
   positive); parity unpinned beyond that convention.
 """
@@ -40,6 +43,8 @@ from .pprpa_ref import (  # noqa: F401
     correlation_energy,
     grad_omega,
     two_e_density_diag,
+    two_e_density,
+    nto,
     nto_weights,
     diag_of_matrix,
 )

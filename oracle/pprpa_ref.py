@@ -328,6 +328,41 @@ def two_e_density_diag(z, nocc_act, nvir_act, mult):
     return np.concatenate([do, dv])
 
 
+def two_e_density(z, nocc_act, nvir_act, mult):
+    """The two-electron addition/removal density matrix D^2e (Sec. Density Matrix), n x n in
+    active-orbital order (occupied first): virtual block X X^T + X^T X, occupied block
+    -(Y Y^T + Y^T Y), zero occupied-virtual blocks; X, Y the triangular matrices of z."""
+    nvv = len(pair_list(nvir_act, mult))
+    X = _triangular(z[:nvv], nvir_act, mult)
+    Y = _triangular(z[nvv:], nocc_act, mult)
+    n = nocc_act + nvir_act
+    D = np.zeros((n, n))
+    D[:nocc_act, :nocc_act] = -(Y @ Y.T + Y.T @ Y)
+    D[nocc_act:, nocc_act:] = X @ X.T + X.T @ X
+    return D
+
+
+def nto(z, nocc_act, nvir_act, mult):
+    """Natural transition orbitals (Eqs. nto_pp, nto_hh): X = C^p1 sqrt(lambda^p) C^p2^T and
+    Y = C^h1 sqrt(lambda^h) C^h2^T, the singular value decompositions of the triangular X and
+    Y, weights descending.  Phase convention: the largest-magnitude entry of each C^p1 / C^h1
+    column is positive (C^p2 / C^h2 follow).  Returns (lam_p, Cp1, Cp2, lam_h, Ch1, Ch2)."""
+    nvv = len(pair_list(nvir_act, mult))
+    out = []
+    for T in (_triangular(z[:nvv], nvir_act, mult), _triangular(z[nvv:], nocc_act, mult)):
+        if T.shape[0] == 0:
+            out += [np.zeros(0), np.zeros((0, 0)), np.zeros((0, 0))]
+            continue
+        U, sv, Vt = np.linalg.svd(T)
+        V = Vt.T
+        for k in range(U.shape[1]):
+            if U[np.argmax(np.abs(U[:, k])), k] < 0:
+                U[:, k] *= -1
+                V[:, k] *= -1
+        out += [sv ** 2, U, V]
+    return tuple(out)
+
+
 def nto_weights(z, nocc_act, nvir_act, mult):
     """NTO weights lambda^p, lambda^h: squared singular values of the
     triangular X and Y (Eqs. nto_pp, nto_hh)."""

@@ -88,6 +88,7 @@ SIGNATURES = {
     "pprpa_grad_vector": (_I, [_P, _I, _P, _P, _P, _I]),
     "pprpa_grad_ec": (_I, [_P, _P, _P, _I]),
     "pprpa_grad_ao": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I]),
+    "pprpa_analyze": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
@@ -311,6 +312,21 @@ class Context:
         p2, w2 = _ptr(deps, True)
         _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
         return dL, deps
+
+    def analyze(self, root):
+        """Two-electron density matrix and NTOs of root `root` of the last solve (host arrays):
+        dict with D2e (n x n), lam_p, Cp1, Cp2 (virtual block) and lam_h, Ch1, Ch2 (occupied)."""
+        n, _, nvv1, _ = self.dims(1)
+        nv = int(round((np.sqrt(8.0 * nvv1 + 1.0) - 1.0) / 2.0))  # singlet nvv = nv (nv + 1) / 2
+        no = n - nv
+        out = {"D2e": np.empty((n, n)), "lam_p": np.empty(nv), "lam_h": np.empty(no),
+               "Cp1": np.empty((nv, nv)), "Cp2": np.empty((nv, nv)),
+               "Ch1": np.empty((no, no)), "Ch2": np.empty((no, no))}
+        ptr = lambda a: a.ctypes.data if a.size else None
+        _check(self.lib.pprpa_analyze(self._h, int(root), ptr(out["D2e"]), ptr(out["lam_p"]),
+                                      ptr(out["lam_h"]), ptr(out["Cp1"]), ptr(out["Cp2"]),
+                                      ptr(out["Ch1"]), ptr(out["Ch2"]), HOST))
+        return out
 
     def grad_ao(self, C, dL, ao3c=None, want_dao=True, want_dc=True):
         """Adjoint of the AO->MO transform: (d/d(P|mu nu), d/dC) from d/dL^P_pq.

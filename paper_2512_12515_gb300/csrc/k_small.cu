@@ -335,4 +335,24 @@ int launch_cholqr_small(const double* Gm, int k, double tol, double* T, int* kee
     return PPRPA_OK;
 }
 
+// Symmetric eigendecomposition of `batch` matrices H (m x m each, row-major, `stride` doubles
+// apart) by the one-CTA parallel Jacobi above, one CTA per matrix: H is overwritten (the
+// eigenvalues end on its diagonal) and U receives the eigenvectors as columns.
+// work: batch x 1152 doubles, iwork: batch x 1024 ints (m <= 1024).
+__global__ void __launch_bounds__(1024, 1) sym_eig_kernel(double* H, double* U, int m, int64_t stride,
+                                                          double* work, int* iwork) {
+    const int b = blockIdx.x;
+    double* rot = work + (int64_t)b * 1152;
+    block_jacobi(H + b * stride, U + b * stride, m, m, rot, iwork + (int64_t)b * 1024, rot + 1024);
+}
+
+int launch_sym_eig(double* H, double* U, int m, int batch, int64_t stride, double* work, int* iwork,
+                   cudaStream_t st) {
+    if (m <= 0 || batch <= 0) return PPRPA_OK;
+    if (m > 1024) return set_error(PPRPA_ERR_ARG, "sym_eig: order above 1024");
+    sym_eig_kernel<<<batch, 1024, 0, st>>>(H, U, m, stride, work, iwork);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
 }  // namespace pprpa

@@ -127,6 +127,10 @@ int launch_rr_general(const RRGenArgs& a, cudaStream_t st);
 // Block orthonormalisation of k rows: given Gram Gm (k x k), returns T (k x k) with
 // T * X orthonormal rows; rows whose residual pivot is below tol are zeroed and flagged
 // keep[j] = 0.
+// Symmetric eigendecomposition (one CTA per m x m matrix, m <= 1024): eigenvalues on the
+// diagonal of H, eigenvectors as the columns of U.  work: batch*1152 doubles, iwork: batch*1024.
+int launch_sym_eig(double* H, double* U, int m, int batch, int64_t stride, double* work, int* iwork,
+                   cudaStream_t st);
 int launch_cholqr_small(const double* Gm, int k, double tol, double* T, int* keep,
                         double* work, cudaStream_t st);
 

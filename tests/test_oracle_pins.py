@@ -303,6 +303,42 @@ def test_nto_weight_sum_rule(mult):
 
 
 @pytest.mark.parametrize("mult", [1, 3])
+def test_density_matrix_and_ntos(mult):
+    """Sec. Density Matrix and Eqs. nto_pp / nto_hh: the full D^2e has the epsilon gradient on
+    its diagonal (d omega / d eps_p = s D^2e_pp), trace +-2, zero occupied-virtual blocks and a
+    positive semidefinite virtual block; the NTOs rebuild X and Y, have orthonormal columns,
+    obey the weight sum rule, and give back the density blocks."""
+    no, nv = 3, 6
+    eps, L = small(no, nv, 7, 6)
+    M, nvv, noo = oracle.build_matrix(eps, no, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    for key, s in (("pp", 1.0), ("hh", -1.0)):
+        z = sol["z_" + key][:, 1]
+        D = oracle.two_e_density(z, no, nv, mult)
+        de, _ = oracle.grad_omega(eps, no, L, mult, z)
+        assert np.allclose(np.diag(D) * s, de, atol=1e-12)
+        assert abs(np.trace(D) - 2 * s) < 1e-12
+        assert np.all(D[:no, no:] == 0) and np.allclose(D, D.T, atol=1e-14)
+        assert np.linalg.eigvalsh(D[no:, no:]).min() > -1e-12
+        assert np.linalg.eigvalsh(-D[:no, :no]).min() > -1e-12
+        lp, cp1, cp2, lh, ch1, ch2 = oracle.nto(z, no, nv, mult)
+        X = np.zeros((nv, nv))
+        Y = np.zeros((no, no))
+        for I, (p, q) in enumerate(oracle.pair_list(nv, mult)):
+            X[p, q] = z[I]
+        for I, (p, q) in enumerate(oracle.pair_list(no, mult)):
+            Y[p, q] = z[nvv + I]
+        assert np.allclose(cp1 @ np.diag(np.sqrt(lp)) @ cp2.T, X, atol=1e-12)
+        assert np.allclose(ch1 @ np.diag(np.sqrt(lh)) @ ch2.T, Y, atol=1e-12)
+        for C in (cp1, cp2, ch1, ch2):
+            assert np.allclose(C.T @ C, np.eye(C.shape[1]), atol=1e-12)
+        assert np.all(np.diff(lp) <= 1e-15) and np.all(np.diff(lh) <= 1e-15)
+        assert abs(lp.sum() - lh.sum() - s) < 1e-12
+        assert np.allclose(cp1 @ np.diag(lp) @ cp1.T + cp2 @ np.diag(lp) @ cp2.T, D[no:, no:], atol=1e-12)
+        assert np.allclose(-(ch1 @ np.diag(lh) @ ch1.T + ch2 @ np.diag(lh) @ ch2.T), D[:no, :no], atol=1e-12)
+
+
+@pytest.mark.parametrize("mult", [1, 3])
 @pytest.mark.parametrize("no,nv", [(1, 2), (3, 7), (5, 9)])
 def test_ri_sigma_equals_explicit_matrix(mult, no, nv):
     eps, L = small(no, nv, 11, 3 * no + nv)
