@@ -106,16 +106,23 @@ int pprpa_create(pprpa_ctx** out, int device, void* cuda_stream);
 void pprpa_destroy(pprpa_ctx* ctx);
 
 /* ---- inputs ---------------------------------------------------------------
- * pprpa_set_orbitals: occupation numbers occ[nmo] (each 0 or 1; closed
- * shell) and orbital energies eps[nmo] in Hartree, sorted ascending.
- * Inputs of Sec. "Implementation Details" (a) and (b).  Host pointers.
+ * pprpa_set_orbitals: occupation numbers occ[nmo] per spatial orbital (the same for both
+ * spins) and orbital energies eps[nmo] in Hartree, sorted ascending.  Inputs of Sec.
+ * "Implementation Details" (a) and (b).  Occupations lie in [0, 1] and do not increase with
+ * the orbital index: 1 (closed shell), fractional (Sec. "ppRPA for Fractional Charge
+ * Systems") or 0.  Hole slots are orbitals with occ > 0 and particle slots orbitals with
+ * occ < 1, so a fractionally occupied orbital is both; the fractional matrix elements
+ * factor into one weight per slot, sqrt(occ) on holes and sqrt(1 - occ) on particles, which
+ * multiply the integrals: L~^P_st = w_s w_t L^P_st (B's weight read as sqrt((1-n_a)(1-n_b)
+ * n_k n_l)).  With 0/1 occupations every weight is 1.  Host pointers.
  */
 int pprpa_set_orbitals(pprpa_ctx* ctx, int nmo, const double* occ, const double* eps);
 
-/* pprpa_set_active: active space = the highest nocc_act occupied and the
- * lowest nvir_act virtual orbitals (the active-space formalism of
- * Sec. "ppRPA Equation").  Must follow set_orbitals and precede
- * set_ao / set_mo.  Default: every orbital active.
+/* pprpa_set_active: active space = the highest nocc_act hole slots (orbitals with occ > 0)
+ * and the lowest nvir_act particle slots (occ < 1) (the active-space formalism of
+ * Sec. "ppRPA Equation").  n = nocc_act + nvir_act slots, holes first; everything below
+ * (pair lists, L, gradients, analysis) is indexed by slot.  Must follow set_orbitals and
+ * precede set_ao / set_mo.  Default: every slot active.
  */
 int pprpa_set_active(pprpa_ctx* ctx, int nocc_act, int nvir_act);
 
@@ -135,7 +142,9 @@ int pprpa_set_ao(pprpa_ctx* ctx, int nbasis, int naux, const double* C,
 int pprpa_set_mo(pprpa_ctx* ctx, int naux, const double* L, int where);
 
 /* pprpa_get_L: copy the active-space L^P_pq (naux x n x n, n = nocc_act +
- * nvir_act, occupied first) into `out` (host or device per `where`). */
+ * nvir_act, hole slots first; with fractional occupations the weighted L~ that the
+ * matrix elements use, which pprpa_grad also differentiates) into `out` (host or device
+ * per `where`). */
 int pprpa_get_L(pprpa_ctx* ctx, double* out, int where);
 
 /* pprpa_dims: sizes of the current problem: n active orbitals, naux, and

@@ -23,6 +23,10 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   chain (AO integrals or MO coefficients -> L -> M -> omega).
 * ri_sigma / davidson: pinned by the explicit matrix (sigma) and by full
   diagonalisation (Davidson roots).
+* fractional_slots, fractional_integrals: pinned by the spin-orbital brute force
+  written element by element from the fractional matrix elements (its spectrum is the
+  union of the folded singlet roots and three copies of the triplet roots), and by
+  integer occupations reducing to the ordinary path.
 * two_e_density, nto: pinned by the trace rule, by the epsilon gradient (the
   diagonal), by reconstructing X and Y from their NTOs and by the identity
   X X^T + X^T X = C^p1 L C^p1^T + C^p2 L C^p2^T between the two definitions.
@@ -31,6 +35,8 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
 """
 from .pprpa_ref import (  # noqa: F401
     active_orbitals,
+    fractional_slots,
+    fractional_integrals,
     ao_to_mo,
     ao_to_mo_rows,
     grad_ao,
@@ -48,5 +54,5 @@ from .pprpa_ref import (  # noqa: F401
     nto_weights,
     diag_of_matrix,
 )
-from .brute import spinorb_matrix, two_electron_ci, mp2_pair_energy  # noqa: F401
+from .brute import spinorb_matrix, spinorb_matrix_fractional, two_electron_ci, mp2_pair_energy  # noqa: F401
 from .davidson_ref import ri_sigma, ri_sigma_rows, davidson  # noqa: F401

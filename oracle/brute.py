@@ -6,6 +6,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   antisymmetrised interaction (Sec. ppRPA Equation, general A, B, C with
   a < b, i < j).  Its spectrum is the union of the singlet roots and three
   copies of the triplet roots.
+* ``spinorb_matrix_fractional``: the same with the fractional-occupation weights of
+  Sec. ppRPA for Fractional Charge Systems, over distinct orbitals (a fractionally
+  occupied orbital gives both hole and particle spin orbitals).
 * ``two_electron_ci``: the Hamiltonian of two electrons in the virtual
   orbitals, in the basis of opposite-spin determinants, from the
   Slater-Condon rules.  With no occupied orbitals ppRPA is exact for two
@@ -59,6 +62,36 @@ def spinorb_matrix(eps_act, nocc_act, L_act):
             M[I, I] += e_so[p] + e_so[q]
         else:
             M[I, I] -= e_so[p] + e_so[q]
+    return M, nvv, noo
+
+
+def spinorb_matrix_fractional(eps, occ, L, holes, parts):
+    """Spin-orbital ppRPA matrix of a fractionally occupied system, element by element from
+    the matrix elements of Sec. ppRPA for Fractional Charge Systems:
+      A_{ab,cd} = d_ac d_bd (eps_a + eps_b) + sqrt((1-n_a)(1-n_b)(1-n_c)(1-n_d)) <ab||cd>,
+      B_{ab,kl} = sqrt((1-n_a)(1-n_b) n_k n_l) <ab||kl>,
+      C_{ij,kl} = -d_ik d_jl (eps_i + eps_j) + sqrt(n_i n_j n_k n_l) <ij||kl>,
+    a < b over the spin orbitals of the particle orbitals ``parts``, i < j over those of the
+    hole orbitals ``holes`` (indices into the distinct orbitals of ``eps``, ``occ`` and
+    ``L``; an orbital may be in both lists).  Returns ``(M, nvv, noo)``."""
+    eps = np.asarray(eps, dtype=np.float64)
+    occ = np.asarray(occ, dtype=np.float64)
+    anti = _spin_eri(L)
+    so_h = [2 * p + sg for p in holes for sg in (0, 1)]
+    so_p = [2 * p + sg for p in parts for sg in (0, 1)]
+    vv = [(so_p[x], so_p[y]) for x in range(len(so_p)) for y in range(x + 1, len(so_p))]
+    oo = [(so_h[x], so_h[y]) for x in range(len(so_h)) for y in range(x + 1, len(so_h))]
+    wp = lambda P: np.sqrt(1.0 - occ[P // 2])
+    wh = lambda P: np.sqrt(occ[P // 2])
+    nvv, noo = len(vv), len(oo)
+    M = np.zeros((nvv + noo, nvv + noo))
+    for I, (a, b) in enumerate(vv + oo):
+        fa = wp(a) * wp(b) if I < nvv else wh(a) * wh(b)
+        for J, (c, d) in enumerate(vv + oo):
+            fc = wp(c) * wp(d) if J < nvv else wh(c) * wh(d)
+            M[I, J] = fa * fc * anti[a, b, c, d]
+        e = eps[a // 2] + eps[b // 2]
+        M[I, I] += e if I < nvv else -e
     return M, nvv, noo
 
 

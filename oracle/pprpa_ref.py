@@ -29,6 +29,40 @@ def active_orbitals(occ, nocc_act, nvir_act):
     return np.concatenate([np.arange(nocc - nocc_act, nocc), np.arange(nocc, nocc + nvir_act)])
 
 
+def fractional_slots(occ, nocc_act, nvir_act):
+    """Active slots for fractional occupations (Sec. ppRPA for Fractional Charge Systems).
+
+    With occupation numbers n_p in [0, 1] per spatial orbital (equal for both spins),
+    non-increasing in orbital order, the hole slots are the highest ``nocc_act`` orbitals
+    with n > 0 and the particle slots the lowest ``nvir_act`` orbitals with n < 1, so that
+    a fractionally occupied orbital is both.  The paper's matrix elements carry
+    sqrt((1-n_a)(1-n_b)(1-n_c)(1-n_d)), sqrt((1-n_a)(1-n_b) n_k n_l) and sqrt(n_i n_j n_k n_l)
+    (reading its "n_k n_k" in B as n_k n_l), which factor into one weight per slot:
+    sqrt(n) on hole slots and sqrt(1 - n) on particle slots.  Returns (orb, w): the MO index
+    and the weight of every slot, holes first.  Integer occupations give
+    ``active_orbitals`` with unit weights.
+    """
+    occ = np.asarray(occ, dtype=np.float64)
+    if np.any(occ < 0) or np.any(occ > 1) or np.any(np.diff(occ) > 0):
+        raise ValueError("occupations must lie in [0, 1] and be non-increasing")
+    holes = np.flatnonzero(occ > 0)
+    parts = np.flatnonzero(occ < 1)
+    if not (0 <= nocc_act <= len(holes) and 0 <= nvir_act <= len(parts)):
+        raise ValueError("active space larger than the orbital space")
+    h = holes[len(holes) - nocc_act:]
+    p = parts[:nvir_act]
+    return np.concatenate([h, p]), np.concatenate([np.sqrt(occ[h]), np.sqrt(1.0 - occ[p])])
+
+
+def fractional_integrals(ao3c, C, occ, eps, nocc_act, nvir_act):
+    """Weighted integrals L~^P_st = w_s w_t L^P_{orb(s) orb(t)} and slot energies for the
+    fractional-occupation matrix elements (see :func:`fractional_slots`); with them
+    ``build_matrix`` gives the paper's fractional A, B and C."""
+    orb, w = fractional_slots(occ, nocc_act, nvir_act)
+    L = ao_to_mo(ao3c, C, orb) * w[None, :, None] * w[None, None, :]
+    return L, np.asarray(eps, dtype=np.float64)[orb]
+
+
 def ao_to_mo(ao3c, C, orb):
     """L^P_pq = sum_{mu,nu} C_{mu p} (P|mu nu) C_{nu q} for p, q in ``orb``.
 

@@ -85,16 +85,51 @@ static void reset_integrals(pprpa_ctx* c) {
     for (auto& t : c->pairs) t.ready = false;
 }
 
+// Slot energies, weights and MO indices on the device.
 static int upload_eps(pprpa_ctx* c) {
     const int n = c->n();
     if (c->d_eps) cudaFree(c->d_eps);
-    c->d_eps = nullptr;
+    if (c->d_slot_w) cudaFree(c->d_slot_w);
+    if (c->d_slot_orb) cudaFree(c->d_slot_orb);
+    c->d_eps = c->d_slot_w = nullptr;
+    c->d_slot_orb = nullptr;
     if (n == 0) return PPRPA_OK;
-    std::vector<double> e(n);
-    const int first = c->nocc - c->no;
-    for (int p = 0; p < n; ++p) e[p] = c->eps[first + p];
+    std::vector<double> e(n), w(n);
+    std::vector<int> o(n);
+    for (int s = 0; s < n; ++s) {
+        o[s] = c->orb(s);
+        e[s] = c->eps[o[s]];
+        w[s] = c->slot_w(s);
+    }
     PP_CUDA(cudaMalloc(&c->d_eps, sizeof(double) * n));
     PP_CUDA(cudaMemcpy(c->d_eps, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PP_CUDA(cudaMalloc(&c->d_slot_w, sizeof(double) * n));
+    PP_CUDA(cudaMemcpy(c->d_slot_w, w.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PP_CUDA(cudaMalloc(&c->d_slot_orb, sizeof(int) * n));
+    PP_CUDA(cudaMemcpy(c->d_slot_orb, o.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    return PPRPA_OK;
+}
+
+// Active columns of C (nbasis x nmo, row-major) in slot order -> d_Cact (nbasis x n).
+static int gather_slot_columns(pprpa_ctx* c, const double* C, int nbasis, int where, double* d_Cact) {
+    const int n = c->n(), nmo = c->nmo;
+    cudaStream_t st = c->stream;
+    if (where == PPRPA_HOST) {
+        std::vector<double> ca((size_t)nbasis * n);
+        for (int m = 0; m < nbasis; ++m)
+            for (int s = 0; s < n; ++s) ca[(size_t)m * n + s] = C[(size_t)m * nmo + c->orb(s)];
+        PP_CUDA(cudaMemcpyAsync(d_Cact, ca.data(), sizeof(double) * ca.size(), cudaMemcpyHostToDevice, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+    } else {
+        // hole slots and particle slots are each a contiguous range of MO columns
+        if (c->no)
+            PP_CUDA(cudaMemcpy2DAsync(d_Cact, sizeof(double) * n, C + c->orb(0), sizeof(double) * nmo,
+                                      sizeof(double) * c->no, nbasis, cudaMemcpyDeviceToDevice, st));
+        if (c->nv)
+            PP_CUDA(cudaMemcpy2DAsync(d_Cact + c->no, sizeof(double) * n, C + c->orb(c->no),
+                                      sizeof(double) * nmo, sizeof(double) * c->nv, nbasis,
+                                      cudaMemcpyDeviceToDevice, st));
+    }
     return PPRPA_OK;
 }
 
@@ -160,6 +195,8 @@ void pprpa_destroy(pprpa_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     reset_integrals(c);
     if (c->d_eps) cudaFree(c->d_eps);
+    if (c->d_slot_w) cudaFree(c->d_slot_w);
+    if (c->d_slot_orb) cudaFree(c->d_slot_orb);
     for (auto& t : c->pairs) {
         if (t.d_pp) cudaFree(t.d_pp);
         if (t.d_pq) cudaFree(t.d_pq);
@@ -179,31 +216,32 @@ void pprpa_destroy(pprpa_ctx* c) {
 int pprpa_set_orbitals(pprpa_ctx* c, int nmo, const double* occ, const double* eps) {
     PP_TRY(check_ctx(c));
     if (nmo <= 0 || !occ || !eps) return set_error(PPRPA_ERR_ARG, "set_orbitals: bad arguments");
-    int nocc = 0;
+    int nocc = 0, nfull = 0;
     for (int i = 0; i < nmo; ++i) {
-        if (occ[i] != 0.0 && occ[i] != 1.0)
-            return set_error(PPRPA_ERR_ARG, "set_orbitals: occupations must be 0 or 1 (closed shell)");
-        if (occ[i] == 1.0) {
-            if (i != nocc) return set_error(PPRPA_ERR_ARG, "set_orbitals: occupied orbitals must come first");
-            ++nocc;
-        }
+        if (!(occ[i] >= 0.0 && occ[i] <= 1.0))
+            return set_error(PPRPA_ERR_ARG, "set_orbitals: occupations must lie in [0, 1]");
+        if (i > 0 && occ[i] > occ[i - 1])
+            return set_error(PPRPA_ERR_ARG, "set_orbitals: occupations must be non-increasing");
+        if (occ[i] > 0.0) ++nocc;
+        if (occ[i] == 1.0) ++nfull;
         if (!std::isfinite(eps[i])) return set_error(PPRPA_ERR_ARG, "set_orbitals: non-finite energy");
         if (i > 0 && eps[i] < eps[i - 1]) return set_error(PPRPA_ERR_ARG, "set_orbitals: energies must be ascending");
     }
     reset_integrals(c);
     c->nmo = nmo;
     c->nocc = nocc;
+    c->nfull = nfull;
     c->occ.assign(occ, occ + nmo);
     c->eps.assign(eps, eps + nmo);
     c->no = nocc;
-    c->nv = nmo - nocc;
+    c->nv = nmo - nfull;
     return upload_eps(c);
 }
 
 int pprpa_set_active(pprpa_ctx* c, int nocc_act, int nvir_act) {
     PP_TRY(check_ctx(c));
     if (c->nmo == 0) return set_error(PPRPA_ERR_STATE, "set_active: call set_orbitals first");
-    if (nocc_act < 0 || nvir_act < 0 || nocc_act > c->nocc || nvir_act > c->nmo - c->nocc)
+    if (nocc_act < 0 || nvir_act < 0 || nocc_act > c->nocc || nvir_act > c->nmo - c->nfull)
         return set_error(PPRPA_ERR_ARG, "set_active: active space larger than the orbital space");
     if (nocc_act + nvir_act == 0) return set_error(PPRPA_ERR_ARG, "set_active: empty active space");
     if (c->have_L) return set_error(PPRPA_ERR_STATE, "set_active must precede set_ao / set_mo");
@@ -219,22 +257,12 @@ int pprpa_set_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const doub
     if (nbasis <= 0 || naux <= 0 || !C || !ao3c || (where != PPRPA_HOST && where != PPRPA_DEVICE))
         return set_error(PPRPA_ERR_ARG, "set_ao: bad arguments");
     if (c->have_L) reset_integrals(c);
-    const int n = c->n(), nmo = c->nmo;
+    const int n = c->n();
     cudaStream_t st = c->stream;
-    const int first = c->nocc - c->no;
-    // active columns of C (nbasis x n) on the device
+    // active columns of C (nbasis x n, slot order) on the device
     double* d_Cact;
     PP_TRY(ws_get(c, "ao_Cact", sizeof(double) * nbasis * n, (void**)&d_Cact));
-    if (where == PPRPA_HOST) {
-        std::vector<double> ca((size_t)nbasis * n);
-        for (int m = 0; m < nbasis; ++m)
-            for (int p = 0; p < n; ++p) ca[(size_t)m * n + p] = C[(size_t)m * nmo + first + p];
-        PP_CUDA(cudaMemcpyAsync(d_Cact, ca.data(), sizeof(double) * ca.size(), cudaMemcpyHostToDevice, st));
-        PP_CUDA(cudaStreamSynchronize(st));
-    } else {
-        PP_CUDA(cudaMemcpy2DAsync(d_Cact, sizeof(double) * n, C + first, sizeof(double) * nmo,
-                                  sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
-    }
+    PP_TRY(gather_slot_columns(c, C, nbasis, where, d_Cact));
     const int64_t nb2 = (int64_t)nbasis * nbasis;
     PP_CUDA(cudaMalloc(&c->d_L, sizeof(double) * (size_t)naux * n * n));
     c->naux = naux;
@@ -272,6 +300,8 @@ int pprpa_set_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const doub
         PP_TRY(dgemm(g2, st));
         if (where == PPRPA_HOST) PP_CUDA(cudaStreamSynchronize(st));
     }
+    // fractional occupations: L~^P_st = w_s w_t L^P_st
+    if (c->weighted()) PP_TRY(launch_scale_slots(c->d_L, naux, n, c->d_slot_w, st));
     PP_CUDA(cudaStreamSynchronize(st));
     c->have_L = true;
     return PPRPA_OK;
@@ -286,39 +316,33 @@ int pprpa_grad_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const dou
     if (dC && !ao3c) return set_error(PPRPA_ERR_ARG, "grad_ao: dC needs the AO integrals");
     if (!dAO && !dC) return PPRPA_OK;
     const int n = c->n(), nmo = c->nmo;
-    const int first = c->nocc - c->no;
     cudaStream_t st = c->stream;
     const bool host = where == PPRPA_HOST;
+    const bool weighted = c->weighted();
     const int64_t nb2 = (int64_t)nbasis * nbasis, nbn = (int64_t)nbasis * n, n2 = (int64_t)n * n;
-    // active columns of C (nbasis x n)
+    // active columns of C (nbasis x n, slot order)
     double* d_Cact;
     PP_TRY(ws_get(c, "gao_Cact", sizeof(double) * nbn, (void**)&d_Cact));
-    if (host) {
-        std::vector<double> ca((size_t)nbn);
-        for (int m = 0; m < nbasis; ++m)
-            for (int p = 0; p < n; ++p) ca[(size_t)m * n + p] = C[(size_t)m * nmo + first + p];
-        PP_CUDA(cudaMemcpyAsync(d_Cact, ca.data(), sizeof(double) * ca.size(), cudaMemcpyHostToDevice, st));
-        PP_CUDA(cudaStreamSynchronize(st));
-    } else {
-        PP_CUDA(cudaMemcpy2DAsync(d_Cact, sizeof(double) * n, C + first, sizeof(double) * nmo,
-                                  sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
-    }
+    PP_TRY(gather_slot_columns(c, C, nbasis, where, d_Cact));
     // chunk of P: dL slices, AO slices and the outputs staged on the device for host arguments,
     // the half-transformed products always
-    const int64_t per_p = sizeof(double) * (nbn + (host ? n2 + (dAO ? nb2 : 0) + (dC ? nb2 : 0) : 0));
+    const int64_t per_p = sizeof(double) * (nbn + (host || weighted ? n2 : 0) +
+                                            (host ? (dAO ? nb2 : 0) + (dC ? nb2 : 0) : 0));
     const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (2LL << 30) / per_p));
     double *d_T, *d_dL = nullptr, *d_ao = nullptr, *d_out = nullptr, *d_dCact = nullptr;
     PP_TRY(ws_get(c, "gao_T", sizeof(double) * nbn * pc, (void**)&d_T));
-    if (host) PP_TRY(ws_get(c, "gao_dL", sizeof(double) * n2 * pc, (void**)&d_dL));
+    if (host || weighted) PP_TRY(ws_get(c, "gao_dL", sizeof(double) * n2 * pc, (void**)&d_dL));
     if (host && dC) PP_TRY(ws_get(c, "gao_ao", sizeof(double) * nb2 * pc, (void**)&d_ao));
     if (host && dAO) PP_TRY(ws_get(c, "gao_out", sizeof(double) * nb2 * pc, (void**)&d_out));
     if (dC) PP_TRY(ws_get(c, "gao_dCact", sizeof(double) * nbn, (void**)&d_dCact));
     for (int P0 = 0; P0 < naux; P0 += pc) {
         const int np = std::min(pc, naux - P0);
         const double* g;
-        if (host) {
+        if (host || weighted) {
             PP_CUDA(cudaMemcpyAsync(d_dL, dL + (size_t)P0 * n2, sizeof(double) * n2 * np,
-                                    cudaMemcpyHostToDevice, st));
+                                    host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+            // the slots carry weights: L~_st = w_s w_t C_s^T (P|..) C_t
+            if (weighted) PP_TRY(launch_scale_slots(d_dL, np, n, c->d_slot_w, st));
             g = d_dL;
         } else {
             g = dL + (size_t)P0 * n2;
@@ -374,17 +398,18 @@ int pprpa_grad_ao(pprpa_ctx* c, int nbasis, int naux, const double* C, const dou
         if (host) PP_CUDA(cudaStreamSynchronize(st));
     }
     if (dC) {
+        // slot columns back to MO columns, summed where an orbital is both a hole and a
+        // particle slot
         if (host) {
             std::vector<double> da((size_t)nbn);
             PP_CUDA(cudaMemcpyAsync(da.data(), d_dCact, sizeof(double) * nbn, cudaMemcpyDeviceToHost, st));
             PP_CUDA(cudaStreamSynchronize(st));
             std::fill(dC, dC + (size_t)nbasis * nmo, 0.0);
             for (int m = 0; m < nbasis; ++m)
-                for (int p = 0; p < n; ++p) dC[(size_t)m * nmo + first + p] = da[(size_t)m * n + p];
+                for (int s = 0; s < n; ++s) dC[(size_t)m * nmo + c->orb(s)] += da[(size_t)m * n + s];
         } else {
             PP_CUDA(cudaMemsetAsync(dC, 0, sizeof(double) * (size_t)nbasis * nmo, st));
-            PP_CUDA(cudaMemcpy2DAsync(dC + first, sizeof(double) * nmo, d_dCact, sizeof(double) * n,
-                                      sizeof(double) * n, nbasis, cudaMemcpyDeviceToDevice, st));
+            PP_TRY(launch_scatter_add_cols(dC, nmo, d_dCact, nbasis, n, c->d_slot_orb, st));
         }
     }
     PP_CUDA(cudaStreamSynchronize(st));
@@ -399,12 +424,7 @@ int pprpa_set_mo(pprpa_ctx* c, int naux, const double* L, int where) {
     if (c->have_L) reset_integrals(c);
     const int n = c->n(), nmo = c->nmo;
     cudaStream_t st = c->stream;
-    std::vector<int> orb(n);
-    const int first = c->nocc - c->no;
-    for (int p = 0; p < n; ++p) orb[p] = first + p;
-    int* d_orb;
-    PP_TRY(ws_get(c, "mo_orb", sizeof(int) * n, (void**)&d_orb));
-    PP_CUDA(cudaMemcpyAsync(d_orb, orb.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    const int* d_orb = c->d_slot_orb;  // MO index of every slot
     PP_CUDA(cudaMalloc(&c->d_L, sizeof(double) * (size_t)naux * n * n));
     c->naux = naux;
     const int64_t nm2 = (int64_t)nmo * nmo;
@@ -422,6 +442,8 @@ int pprpa_set_mo(pprpa_ctx* c, int naux, const double* L, int where) {
             PP_CUDA(cudaStreamSynchronize(st));
         }
     }
+    // fractional occupations: L~^P_st = w_s w_t L^P_st
+    if (c->weighted()) PP_TRY(launch_scale_slots(c->d_L, naux, n, c->d_slot_w, st));
     PP_CUDA(cudaStreamSynchronize(st));
     c->have_L = true;
     return PPRPA_OK;

@@ -1,5 +1,6 @@
 // Internal state of a ppRPA context (host runtime of the C ABI).
 #pragma once
+#include <cmath>
 #include <cuda.h>
 
 #include <map>
@@ -38,12 +39,27 @@ struct pprpa_ctx {
     bool own_stream = false;
     int num_sms = 152;
 
-    int nmo = 0, nocc = 0;
+    int nmo = 0, nocc = 0;  // orbitals, orbitals with occupation n > 0 (hole candidates)
+    int nfull = 0;          // orbitals with n = 1; those with n < 1 are particle candidates
     std::vector<double> occ, eps;
-    int no = -1, nv = -1;  // active space
+    int no = -1, nv = -1;  // active space: hole slots, particle slots
     bool have_L = false;
     int naux = 0;
-    double* d_eps = nullptr;  // active orbital energies (n)
+    double* d_eps = nullptr;  // slot energies (n)
+    double* d_slot_w = nullptr;  // slot weights (n): sqrt(n_p) on holes, sqrt(1 - n_p) on particles
+    int* d_slot_orb = nullptr;   // MO index of every slot (n)
+    // MO index of slot s: the highest `no` orbitals with n > 0, then the lowest `nv` with n < 1
+    // (a fractionally occupied orbital can be both)
+    int orb(int s) const { return s < no ? nocc - no + s : nfull + (s - no); }
+    double slot_w(int s) const {
+        const double f = occ[orb(s)];
+        return s < no ? std::sqrt(f) : std::sqrt(1.0 - f);
+    }
+    bool weighted() const {  // some active slot has a weight other than 1
+        for (int s = 0; s < no + nv; ++s)
+            if (slot_w(s) != 1.0) return true;
+        return false;
+    }
     double* d_L = nullptr;    // [naux][n][n]
 
     pprpa::PairTable pairs[2];  // [0] singlet, [1] triplet

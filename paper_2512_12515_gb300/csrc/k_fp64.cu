@@ -733,4 +733,44 @@ int launch_unpack_fp8(const double* z, int k, int N, int nvv, const int* pp, con
     return PPRPA_OK;
 }
 
+// Fractional occupations: X[P][s][t] *= w[s] w[t] (slot weights sqrt(n) / sqrt(1 - n)).
+__global__ void scale_slots_kernel(double* __restrict__ X, int naux, int n, const double* __restrict__ w) {
+    const int64_t total = (int64_t)naux * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int q = t % n, p = (t / n) % n;
+        X[t] *= w[p] * w[q];
+    }
+}
+
+int launch_scale_slots(double* X, int naux, int n, const double* w, cudaStream_t st) {
+    const int64_t total = (int64_t)naux * n * n;
+    if (!total) return PPRPA_OK;
+    scale_slots_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 32), 256, 0, st>>>(X, naux, n, w);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// dst[m][orb[s]] += src[m][s] (an orbital may own several slots).
+__global__ void scatter_add_cols_kernel(double* __restrict__ dst, int nmo, const double* __restrict__ src,
+                                        int nbasis, int n, const int* __restrict__ orb) {
+    const int64_t total = (int64_t)nbasis * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int s = t % n;
+        const int64_t m = t / n;
+        atomicAdd(dst + m * nmo + orb[s], src[t]);
+    }
+}
+
+int launch_scatter_add_cols(double* dst, int nmo, const double* src, int nbasis, int n, const int* orb,
+                            cudaStream_t st) {
+    const int64_t total = (int64_t)nbasis * n;
+    if (!total) return PPRPA_OK;
+    scatter_add_cols_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 8), 256, 0, st>>>(
+        dst, nmo, src, nbasis, n, orb);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
 }  // namespace pprpa

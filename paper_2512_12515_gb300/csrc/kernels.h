@@ -32,6 +32,11 @@ int auto_splitk(int M, int N, int K, int batches);
 
 // ---------------------------------------------------------------------------
 // Elementwise / reduction kernels (FP64 unless noted).
+// X[P][s][t] *= w[s] w[t] over naux slices of n x n.
+int launch_scale_slots(double* X, int naux, int n, const double* w, cudaStream_t st);
+// dst[m][orb[s]] += src[m][s]: dst nbasis x nmo, src nbasis x n.
+int launch_scatter_add_cols(double* dst, int nmo, const double* src, int nbasis, int n, const int* orb,
+                            cudaStream_t st);
 int launch_extract_active(const double* Lfull, int naux, int nmo, const int* orb, int n,
                           double* Lact, cudaStream_t st);
 int launch_diag(const double* L, int naux, int n, const double* eps, const int* pp,

@@ -66,6 +66,94 @@ def test_spin_adapted_spectrum_equals_spin_orbital(no, nv):
     assert abs(ec_so - (parts[1]["Ec"] + 3 * parts[3]["Ec"])) < 1e-11
 
 
+@pytest.mark.parametrize("frac", [0.6, 0.15, 0.97])
+def test_fractional_occupation_folding_equals_spin_orbital_elements(frac):
+    """Sec. ppRPA for Fractional Charge Systems: the weighted integrals over hole and particle
+    slots (a fractional HOMO in both lists) give, through the spin adaptation, the spectrum
+    of the spin-orbital matrix written element by element from the paper's fractional A, B
+    and C: singlet roots + 3 x triplet roots, both root sets, and E_c."""
+    spec = synth.SystemSpec("t", 10, 3, 8, 2, 4, 53)
+    s = synth.make_system(spec)
+    occ = np.zeros(spec.nmo)
+    occ[:3] = [1.0, 1.0, frac]
+    orb, w = oracle.fractional_slots(occ, 2, 4)
+    assert list(orb) == [1, 2, 2, 3, 4, 5]
+    assert np.allclose(w, [1.0, np.sqrt(frac), np.sqrt(1 - frac), 1.0, 1.0, 1.0])
+    L, eps_s = oracle.fractional_integrals(s["ao3c"], s["C"], occ, s["eps"], 2, 4)
+    uniq = np.array([1, 2, 3, 4, 5])
+    Lu = oracle.ao_to_mo(s["ao3c"], s["C"], uniq)
+    Mso, nvv_so, noo_so = oracle.spinorb_matrix_fractional(s["eps"][uniq], occ[uniq], Lu, [0, 1], [1, 2, 3, 4])
+    so = oracle.solve_full(Mso, nvv_so, noo_so)
+    parts, ec = {}, 0.0
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps_s, 2, L, mult)
+        parts[mult] = oracle.solve_full(M, nvv, noo)
+        ec += (1 if mult == 1 else 3) * oracle.correlation_energy(M, nvv, noo, parts[mult])[0]
+    for key in ("pp", "hh"):
+        ref = np.sort(np.concatenate([parts[1]["omega_" + key]] + [parts[3]["omega_" + key]] * 3))
+        assert np.allclose(np.sort(so["omega_" + key]), ref, atol=1e-11)
+    assert abs(oracle.correlation_energy(Mso, nvv_so, noo_so, so)[0] - ec) < 1e-11
+
+
+def test_fractional_ao_adjoint_matches_finite_differences():
+    """The AO adjoint of the fractional chain: slots with weights (a duplicated orbital) and
+    d omega / d L~ scaled by w_s w_t, against central differences of a root in the AO
+    integrals and in C."""
+    spec = synth.SystemSpec("t", 10, 3, 7, 2, 4, 56)
+    s = synth.make_system(spec)
+    occ = np.zeros(spec.nmo)
+    occ[:3] = [1.0, 1.0, 0.4]
+    orb, w = oracle.fractional_slots(occ, 2, 4)
+
+    def root(ao, C):
+        L, e = oracle.fractional_integrals(ao, C, occ, s["eps"], 2, 4)
+        M, nvv, noo = oracle.build_matrix(e, 2, L, 1)
+        sol = oracle.solve_full(M, nvv, noo)
+        return sol["omega_pp"][0], sol["z_pp"][:, 0], L, e
+
+    _, z, L, e = root(s["ao3c"], s["C"])
+    _, dL = oracle.grad_omega(e, 2, L, 1, z)
+    d_ao, d_c = oracle.grad_ao(s["ao3c"], s["C"], orb, dL * w[None, :, None] * w[None, None, :])
+    rng = np.random.default_rng(8)
+    h = 1e-5
+    E = rng.standard_normal(s["ao3c"].shape)
+    E = (E + E.transpose(0, 2, 1)) / np.linalg.norm(E)
+    fd = (root(s["ao3c"] + h * E, s["C"])[0] - root(s["ao3c"] - h * E, s["C"])[0]) / (2 * h)
+    assert abs(fd - float(np.sum(d_ao * E))) < 1e-6 * max(1.0, abs(fd))
+    D = rng.standard_normal(s["C"].shape)
+    D /= np.linalg.norm(D)
+    fd = (root(s["ao3c"], s["C"] + h * D)[0] - root(s["ao3c"], s["C"] - h * D)[0]) / (2 * h)
+    assert abs(fd - float(np.sum(d_c * D))) < 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("frac", [0.2, 0.5, 0.9])
+def test_fractional_single_orbital_closed_form(frac):
+    """One orbital that is both the hole and the particle slot (occupation n): the singlet
+    2 x 2 problem has A = 2 eps + (1-n)^2 g, B = n (1-n) g, C = -2 eps + n^2 g with
+    g = (HH|HH), so its roots are 2 eps and 2 eps + ((1-n)^2 - n^2) g; at n = 1/2 they
+    coincide (the pencil is defective there)."""
+    spec = synth.SystemSpec("t", 6, 1, 5, 1, 1, 71)
+    s = synth.make_system(spec)
+    occ = np.zeros(spec.nmo)
+    occ[0] = frac
+    L, e = oracle.fractional_integrals(s["ao3c"], s["C"], occ, s["eps"], 1, 1)
+    M, nvv, noo = oracle.build_matrix(e, 1, L, 1)
+    g = float(np.sum(oracle.ao_to_mo(s["ao3c"], s["C"], [0])[:, 0, 0] ** 2))
+    eps0 = s["eps"][0]
+    want = np.sort([2 * eps0, 2 * eps0 + ((1 - frac) ** 2 - frac ** 2) * g])
+    got = np.sort(np.linalg.eigvals(np.diag([1.0, -1.0]) @ M).real)
+    assert np.allclose(got, want, atol=1e-7 if frac == 0.5 else 1e-12)
+
+
+def test_fractional_path_reduces_to_integer_occupations():
+    spec = synth.SystemSpec("t", 12, 4, 9, 3, 5, 54)
+    s = synth.make_system(spec)
+    L, e = oracle.fractional_integrals(s["ao3c"], s["C"], s["occ"], s["eps"], 3, 5)
+    orb = oracle.active_orbitals(s["occ"], 3, 5)
+    assert np.array_equal(L, oracle.ao_to_mo(s["ao3c"], s["C"], orb))
+    assert np.array_equal(e, s["eps"][orb])
+
+
 @pytest.mark.parametrize("nv", [3, 5])
 def test_two_electrons_are_exact(nv):
     """No occupied orbitals: ppRPA roots equal the two-electron determinant CI."""
