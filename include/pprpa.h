@@ -58,6 +58,7 @@ extern "C" {
 
 #define PPRPA_SINGLET 1
 #define PPRPA_TRIPLET 3
+#define PPRPA_AB 2 /* "mult" code of the alpha-beta subspace of spin-unrestricted ppRPA (pprpa_set_beta) */
 
 #define PPRPA_METHOD_FULL 0     /* explicit A/B/C build + dense diagonalisation */
 #define PPRPA_METHOD_DAVIDSON 1 /* density-fitted sigma + Davidson */
@@ -140,6 +141,25 @@ int pprpa_set_ao(pprpa_ctx* ctx, int nbasis, int naux, const double* C,
 /* pprpa_set_mo: MO-space fitting integrals L[naux][nmo][nmo] (input (c) of
  * Sec. "Implementation Details").  Only the active block is kept. */
 int pprpa_set_mo(pprpa_ctx* ctx, int naux, const double* L, int where);
+
+/* pprpa_set_beta: the beta orbitals of a spin-unrestricted reference, for the
+ * (alpha alpha; beta beta) subspace (Sec. "Implementation Details": spin-unrestricted
+ * ppRPA is built and diagonalised in three subspaces).  The context's own active orbitals,
+ * energies and integrals (set_orbitals / set_active / set_ao or set_mo) are the alpha set;
+ * this call gives the beta active space: nocc_b occupied then nvir_b virtual orbitals,
+ * their energies eps_b[nb] and MO-space fitting integrals L_b[naux][nb][nb]
+ * (nb = nocc_b + nvir_b; naux must equal the alpha one).  Host or device per `where`; the
+ * data is copied.  mult = PPRPA_AB then selects the alpha-beta subspace in pprpa_dims,
+ * pprpa_diag, pprpa_sigma (FP64), pprpa_build_matrix and pprpa_solve (FULL, or Davidson in
+ * FP64): pairs (a_alpha, b_beta) over every virtual x virtual and (i_alpha, j_beta) over
+ * every occupied x occupied, row-major, with A_{ab,cd} = d d (eps_a + eps_b) + (ac|bd),
+ * B_{ab,kl} = (ak|bl), C_{ij,kl} = -d d (eps_i + eps_j) + (ik|jl) and
+ * (pr|qs) = sum_P L^{alpha P}_pr L^{beta P}_qs (no exchange between opposite spins).  The
+ * same-spin subspaces are the PPRPA_TRIPLET problem of one spin's orbitals and integrals
+ * (a context per spin).  Gradients and analysis of the alpha-beta subspace are not built
+ * (PPRPA_ERR_UNSUPPORTED). */
+int pprpa_set_beta(pprpa_ctx* ctx, int nocc_b, int nvir_b, int naux, const double* eps_b,
+                   const double* L_b, int where);
 
 /* pprpa_get_L: copy the active-space L^P_pq (naux x n x n, n = nocc_act +
  * nvir_act, hole slots first; with fractional occupations the weighted L~ that the

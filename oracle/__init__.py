@@ -27,6 +27,10 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   written element by element from the fractional matrix elements (its spectrum is the
   union of the folded singlet roots and three copies of the triplet roots), and by
   integer occupations reducing to the ordinary path.
+* build_matrix_ab (spin-unrestricted alpha-beta subspace): pinned by the
+  restricted limit (alpha = beta: singlet roots plus one copy of the triplet
+  roots) and by the spin-orbital brute force of a spin-unrestricted reference
+  (its spectrum is the union of the three subspaces).
 * two_e_density, nto: pinned by the trace rule, by the epsilon gradient (the
   diagonal), by reconstructing X and Y from their NTOs and by the identity
   X X^T + X^T X = C^p1 L C^p1^T + C^p2 L C^p2^T between the two definitions.
@@ -43,6 +47,7 @@ from .pprpa_ref import (  # noqa: F401
     pair_list,
     eri_phys,
     build_matrix,
+    build_matrix_ab,
     matrix_blocks,
     solve_full,
     solve_full_shifted,
@@ -54,5 +59,11 @@ from .pprpa_ref import (  # noqa: F401
     nto_weights,
     diag_of_matrix,
 )
-from .brute import spinorb_matrix, spinorb_matrix_fractional, two_electron_ci, mp2_pair_energy  # noqa: F401
+from .brute import (  # noqa: F401
+    spinorb_matrix,
+    spinorb_matrix_fractional,
+    spinorb_matrix_unrestricted,
+    two_electron_ci,
+    mp2_pair_energy,
+)
 from .davidson_ref import ri_sigma, ri_sigma_rows, davidson  # noqa: F401

@@ -9,6 +9,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * ``spinorb_matrix_fractional``: the same with the fractional-occupation weights of
   Sec. ppRPA for Fractional Charge Systems, over distinct orbitals (a fractionally
   occupied orbital gives both hole and particle spin orbitals).
+* ``spinorb_matrix_unrestricted``: the spin-orbital matrix of a spin-unrestricted
+  reference (different alpha and beta orbitals); its spectrum is the union of the three
+  subspaces of spin-unrestricted ppRPA.
 * ``two_electron_ci``: the Hamiltonian of two electrons in the virtual
   orbitals, in the basis of opposite-spin determinants, from the
   Slater-Condon rules.  With no occupied orbitals ppRPA is exact for two
@@ -93,6 +96,46 @@ def spinorb_matrix_fractional(eps, occ, L, holes, parts):
         e = eps[a // 2] + eps[b // 2]
         M[I, I] += e if I < nvv else -e
     return M, nvv, noo
+
+
+def spinorb_matrix_unrestricted(eps_a, nocc_a, L_a, eps_b, nocc_b, L_b):
+    """ppRPA matrix over spin orbitals with different alpha and beta spatial orbitals (a
+    spin-unrestricted reference): spin orbitals are the alpha orbitals then the beta
+    orbitals, <PQ||RS> = <PQ|RS> - <PQ|SR> with <PQ|RS> = (PR|QS) nonzero only for equal
+    spins of P, R and of Q, S, and (pr|qs) from L^alpha / L^beta by the spins of the two
+    charge distributions; pairs a < b over virtual and i < j over occupied spin orbitals.
+    Returns ``(M, nvv, noo)``; its spectrum is the union of the alpha-alpha, beta-beta
+    and alpha-beta subspaces."""
+    ea = np.asarray(eps_a, dtype=np.float64)
+    eb = np.asarray(eps_b, dtype=np.float64)
+    La = np.asarray(L_a, dtype=np.float64)
+    Lb = np.asarray(L_b, dtype=np.float64)
+    na, nb = ea.shape[0], eb.shape[0]
+    so = [(0, p) for p in range(na)] + [(1, p) for p in range(nb)]  # (spin, spatial index)
+    e_so = np.concatenate([ea, eb])
+    occ_so = [P for P, (sg, p) in enumerate(so) if p < (nocc_a if sg == 0 else nocc_b)]
+    vir_so = [P for P in range(len(so)) if P not in occ_so]
+    Ls = (La, Lb)
+
+    def chem(P, R, Q, S):  # (PR|QS)
+        (s1, p), (s2, r), (s3, q), (s4, t) = so[P], so[R], so[Q], so[S]
+        if s1 != s2 or s3 != s4:
+            return 0.0
+        return float(np.dot(Ls[s1][:, p, r], Ls[s3][:, q, t]))
+
+    def anti(P, Q, R, S):
+        return chem(P, R, Q, S) - chem(P, S, Q, R)
+
+    vv = [(vir_so[x], vir_so[y]) for x in range(len(vir_so)) for y in range(x + 1, len(vir_so))]
+    oo = [(occ_so[x], occ_so[y]) for x in range(len(occ_so)) for y in range(x + 1, len(occ_so))]
+    pairs = vv + oo
+    nvv = len(vv)
+    M = np.zeros((len(pairs), len(pairs)))
+    for I, (P, Q) in enumerate(pairs):
+        for J, (R, S) in enumerate(pairs):
+            M[I, J] = anti(P, Q, R, S)
+        M[I, I] += (e_so[P] + e_so[Q]) if I < nvv else -(e_so[P] + e_so[Q])
+    return M, nvv, len(oo)
 
 
 def two_electron_ci(eps_act, L_act):

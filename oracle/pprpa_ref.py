@@ -199,6 +199,36 @@ def build_matrix(eps_act, nocc_act, L_act, mult):
     return M, A.shape[0], C.shape[0]
 
 
+def build_matrix_ab(eps_a, nocc_a, L_a, eps_b, nocc_b, L_b):
+    """The (alpha alpha; beta beta) subspace of spin-unrestricted ppRPA (Sec. Implementation
+    Details: the matrix is built and diagonalised in three subspaces).
+
+    Pairs of one alpha and one beta orbital: (a, b) over every alpha-virtual x beta-virtual,
+    (i, j) over every alpha-occupied x beta-occupied, row-major.  Opposite spins have no
+    exchange, so with (pr|qs) = sum_P L^{alpha P}_pr L^{beta P}_qs:
+      A_{ab,cd} = d_ac d_bd (eps_a + eps_b) + (ac|bd),  B_{ab,kl} = (ak|bl),
+      C_{ij,kl} = -d_ik d_jl (eps_i + eps_j) + (ik|jl).
+    The same-spin subspaces are ``build_matrix(eps, nocc, L, 3)`` of one spin (a < b,
+    <ab|cd> - <ab|dc>).  Returns ``(M, nvv, noo)``.
+    """
+    ea = np.asarray(eps_a, dtype=np.float64)
+    eb = np.asarray(eps_b, dtype=np.float64)
+    La = np.asarray(L_a, dtype=np.float64)
+    Lb = np.asarray(L_b, dtype=np.float64)
+    na, nb = ea.shape[0], eb.shape[0]
+    vv = [(a, b) for a in range(nocc_a, na) for b in range(nocc_b, nb)]
+    oo = [(i, j) for i in range(nocc_a) for j in range(nocc_b)]
+    V = np.einsum("Ppr,Pqs->pqrs", La, Lb, optimize=True)  # (pr|qs) for p, r alpha; q, s beta
+    pairs = vv + oo
+    nvv = len(vv)
+    M = np.zeros((len(pairs), len(pairs)))
+    for I, (p, q) in enumerate(pairs):
+        for J, (r, t) in enumerate(pairs):
+            M[I, J] = V[p, q, r, t]
+        M[I, I] += (ea[p] + eb[q]) if I < nvv else -(ea[p] + eb[q])
+    return M, nvv, len(oo)
+
+
 def diag_of_matrix(eps_act, nocc_act, L_act, mult):
     """Diagonal of M, from the explicit matrix (for checking the GPU diagonal)."""
     M, _, _ = build_matrix(eps_act, nocc_act, L_act, mult)

@@ -5,6 +5,7 @@ C ABI, see include/pprpa.h); this package only marshals arguments.
 Importing it loads the library and fails loudly when it has not been built.
 """
 from ._lib import (  # noqa: F401
+    AB,
     CHANNEL_HH,
     CHANNEL_PP,
     Context,

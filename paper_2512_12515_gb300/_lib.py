@@ -21,6 +21,7 @@ ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE, ER
     -1, -2, -3, -4, -5, -6, -7, -8)
 HOST, DEVICE = 0, 1
 SINGLET, TRIPLET = 1, 3
+AB = 2  # alpha-beta subspace of spin-unrestricted ppRPA (after Context.set_beta)
 METHOD_FULL, METHOD_DAVIDSON = 0, 1
 PREC_FP64, PREC_BF16, PREC_FP8 = 0, 1, 2
 PREC_BF16_SPLIT = PREC_BF16 + 16  # sigma only: BF16x3 split products
@@ -89,6 +90,7 @@ SIGNATURES = {
     "pprpa_grad_ec": (_I, [_P, _P, _P, _I]),
     "pprpa_grad_ao": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I]),
     "pprpa_analyze": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "pprpa_set_beta": (_I, [_P, _I, _I, _I, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
@@ -225,6 +227,15 @@ class Context:
         if nb != nb2 or C.shape[0] != nb:
             raise ValueError("shape mismatch between C and ao3c")
         _check(self.lib.pprpa_set_ao(self._h, nb, naux, pc, pa, wa))
+
+    def set_beta(self, nocc_b, nvir_b, eps_b, L_b):
+        """Beta active space of a spin-unrestricted reference (the context's own is alpha):
+        energies eps_b[nb] and MO-space integrals L_b[naux][nb][nb], occupied first."""
+        pe, we = _ptr(eps_b)
+        pl, wl = _ptr(L_b)
+        if we != wl:
+            raise ValueError("eps_b and L_b must both be host or both be device arrays")
+        _check(self.lib.pprpa_set_beta(self._h, int(nocc_b), int(nvir_b), int(L_b.shape[0]), pe, pl, wl))
 
     def set_mo(self, L):
         p, w = _ptr(L)

@@ -102,6 +102,8 @@ extern "C" int pprpa_analyze(pprpa_ctx* c, int root, double* D2e, double* lam_p,
     if (where != PPRPA_HOST && where != PPRPA_DEVICE) return set_error(PPRPA_ERR_ARG, "analyze: bad `where`");
     if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "analyze: no solve to analyse");
     if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "analyze: root index out of range");
+    if (c->last_mult == PPRPA_AB)
+        return set_error(PPRPA_ERR_UNSUPPORTED, "analyze: the alpha-beta subspace is not built here");
     PairTable* pt;
     PP_TRY(ensure_pairs(c, c->last_mult, &pt));
     const int no = c->no, nv = c->nv, n = c->n();

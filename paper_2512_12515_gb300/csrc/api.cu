@@ -31,7 +31,8 @@ static int need_L(pprpa_ctx* c) {
 }
 
 int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out) {
-    if (mult != 1 && mult != 3) return set_error(PPRPA_ERR_ARG, "mult must be 1 or 3");
+    if (mult == PPRPA_AB) return ensure_pairs_ab(c, out);
+    if (mult != 1 && mult != 3) return set_error(PPRPA_ERR_ARG, "mult must be 1, 3 or PPRPA_AB");
     PairTable& t = c->pairs[mult == 1 ? 0 : 1];
     if (!t.ready) {
         t.pp.clear();
@@ -197,6 +198,8 @@ void pprpa_destroy(pprpa_ctx* c) {
     if (c->d_eps) cudaFree(c->d_eps);
     if (c->d_slot_w) cudaFree(c->d_slot_w);
     if (c->d_slot_orb) cudaFree(c->d_slot_orb);
+    if (c->d_Lb) cudaFree(c->d_Lb);
+    if (c->d_epsb) cudaFree(c->d_epsb);
     for (auto& t : c->pairs) {
         if (t.d_pp) cudaFree(t.d_pp);
         if (t.d_pq) cudaFree(t.d_pq);
@@ -482,8 +485,9 @@ int pprpa_diag(pprpa_ctx* c, int mult, double* out, int where) {
     double *D, *work;
     PP_TRY(ws_get(c, "diag_D", sizeof(double) * std::max(t->N, 1), (void**)&D));
     PP_TRY(ws_get(c, "diag_work", sizeof(double) * (size_t)c->naux * c->n(), (void**)&work));
-    PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, t->d_pp, t->d_pq, t->nvv, t->N, mult, D,
-                       work, c->stream));
+    if (mult == PPRPA_AB) PP_TRY(diag_ab(c, t, D));
+    else PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, t->d_pp, t->d_pq, t->nvv, t->N, mult, D,
+                            work, c->stream));
     PP_CUDA(cudaMemcpyAsync(out, D, sizeof(double) * t->N,
                             where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             c->stream));
@@ -511,7 +515,11 @@ int pprpa_sigma(pprpa_ctx* c, int mult, int precision, int k, const double* z, d
         ds = bs;
     }
     int rc;
-    if (precision == PPRPA_PREC_FP64) rc = sigma_f64(c, mult, k, dz, ds);
+    if (mult == PPRPA_AB) {
+        if (precision != PPRPA_PREC_FP64)
+            return set_error(PPRPA_ERR_UNSUPPORTED, "sigma: the alpha-beta subspace runs in FP64 only");
+        rc = sigma_ab_f64(c, k, dz, ds);
+    } else if (precision == PPRPA_PREC_FP64) rc = sigma_f64(c, mult, k, dz, ds);
     else if (precision == PPRPA_PREC_BF16) rc = sigma_tc(c, mult, k, dz, ds, 1);
     else if (precision == PPRPA_PREC_BF16 + 16) rc = sigma_tc(c, mult, k, dz, ds, 3);
     else if (precision == PPRPA_PREC_FP8) rc = sigma_tc(c, mult, k, dz, ds, 1, true);
@@ -587,6 +595,8 @@ static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, dou
 extern "C" {
 
 int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
+    if (c && c->last_nroots && c->last_mult == PPRPA_AB)
+        return set_error(PPRPA_ERR_UNSUPPORTED, "gradients of the alpha-beta subspace are not built");
     PP_TRY(check_ctx(c));
     PP_TRY(need_L(c));
     if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");
@@ -599,6 +609,8 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
 }
 
 int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {
+    if (c && c->last_nroots && c->last_mult == PPRPA_AB)
+        return set_error(PPRPA_ERR_UNSUPPORTED, "gradients of the alpha-beta subspace are not built");
     PP_TRY(check_ctx(c));
     PP_TRY(need_L(c));
     PairTable* t;
@@ -667,6 +679,8 @@ int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {
 }
 
 int pprpa_grad_vector(pprpa_ctx* c, int mult, const double* z, double* dL, double* deps, int where) {
+    if (mult == PPRPA_AB)
+        return set_error(PPRPA_ERR_UNSUPPORTED, "gradients of the alpha-beta subspace are not built");
     PP_TRY(check_ctx(c));
     PP_TRY(need_L(c));
     if (!z) return set_error(PPRPA_ERR_ARG, "grad_vector: null z");

@@ -62,7 +62,13 @@ struct pprpa_ctx {
     }
     double* d_L = nullptr;    // [naux][n][n]
 
-    pprpa::PairTable pairs[2];  // [0] singlet, [1] triplet
+    pprpa::PairTable pairs[3];  // [0] singlet, [1] triplet, [2] alpha-beta (unrestricted)
+    // beta set of the spin-unrestricted alpha-beta subspace (the context's own set is alpha)
+    double* d_Lb = nullptr;    // [naux][nb][nb]
+    double* d_epsb = nullptr;  // [nb]
+    int nob = 0, nvb = 0;
+    bool have_Lb = false;
+    int nb() const { return nob + nvb; }
 
     // BF16 copies of L for the tensor-core sigma
     pprpa::PadMap pm;
@@ -103,6 +109,11 @@ int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out);
 int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out);
 int ensure_bf16(pprpa_ctx* c);
 int sigma_f64(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma);
+// alpha-beta subspace of spin-unrestricted ppRPA (mult = PPRPA_AB): FP64 only
+int ensure_pairs_ab(pprpa_ctx* c, PairTable** out);
+int diag_ab(pprpa_ctx* c, PairTable* t, double* D);
+int build_ab(pprpa_ctx* c, PairTable* t, double* M);
+int sigma_ab_f64(pprpa_ctx* c, int k, const double* d_z, double* d_sigma);
 int sigma_tc(pprpa_ctx* c, int mult, int k, const double* d_z, double* d_sigma, int nterms,
              bool f8 = false);
 int ensure_fp8(pprpa_ctx* c);

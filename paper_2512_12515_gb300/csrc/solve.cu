@@ -180,9 +180,11 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     const double ws = hh ? -1.0 : 1.0;
     const int noo = pt->noo;
     const int npos = hh ? noo : nvv;  // roots of positive norm in the solved pencil
-    PP_TRY(build_explicit(c, pt, o->mult, eri, M));
+    if (o->mult == PPRPA_AB) PP_TRY(build_ab(c, pt, M));
+    else PP_TRY(build_explicit(c, pt, o->mult, eri, M));
     PP_TRY(launch_metric_matrix(W, N, nvv, st, ws));
-    PP_TRY(launch_diag(c->d_L, c->naux, n, c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
+    if (o->mult == PPRPA_AB) PP_TRY(diag_ab(c, pt, D));
+    else PP_TRY(launch_diag(c->d_L, c->naux, n, c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     PP_CUDA(cudaStreamSynchronize(st));
@@ -299,7 +301,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(ws_get(c, "dv_dom", sizeof(double) * m_max, (void**)&dom));
 
     // a3: diagonal, then the initial guess
-    PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
+    if (o->mult == PPRPA_AB) PP_TRY(diag_ab(c, pt, D));
+    else PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     PP_CUDA(cudaStreamSynchronize(st));
@@ -326,7 +329,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     auto run_sigma = [&](int k, const double* z, double* out) -> int {
         t_sig.start();
         int rc;
-        if (stage == 0) rc = sigma_f64(c, o->mult, k, z, out);
+        if (o->mult == PPRPA_AB) rc = sigma_ab_f64(c, k, z, out);
+        else if (stage == 0) rc = sigma_f64(c, o->mult, k, z, out);
         else if (stage == 3) rc = sigma_tc(c, o->mult, k, z, out, 1, true);
         else rc = sigma_tc(c, o->mult, k, z, out, stage == 1 ? 1 : 3);
         t_sig.stop();
@@ -571,7 +575,10 @@ extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, 
     if (!c || !o) return set_error(PPRPA_ERR_ARG, "solve: null argument");
     PP_CUDA(cudaSetDevice(c->device));
     if (!c->have_L) return set_error(PPRPA_ERR_STATE, "solve: integrals not set");
-    if (o->mult != 1 && o->mult != 3) return set_error(PPRPA_ERR_ARG, "solve: mult must be 1 or 3");
+    if (o->mult != 1 && o->mult != 3 && o->mult != PPRPA_AB)
+        return set_error(PPRPA_ERR_ARG, "solve: mult must be 1, 3 or PPRPA_AB");
+    if (o->mult == PPRPA_AB && o->method == PPRPA_METHOD_DAVIDSON && o->precision != PPRPA_PREC_FP64)
+        return set_error(PPRPA_ERR_UNSUPPORTED, "solve: the alpha-beta subspace runs in FP64 only");
     if (o->channel != PPRPA_CHANNEL_PP && o->channel != PPRPA_CHANNEL_HH)
         return set_error(PPRPA_ERR_ARG, "solve: channel must be PPRPA_CHANNEL_PP or PPRPA_CHANNEL_HH");
     if (o->method != PPRPA_METHOD_FULL && o->method != PPRPA_METHOD_DAVIDSON)
@@ -600,10 +607,14 @@ extern "C" int pprpa_build_matrix(pprpa_ctx* c, int mult, double* Mout, int wher
     const int64_t n2 = (int64_t)c->n() * c->n();
     const size_t mbytes = sizeof(double) * (size_t)pt->N * pt->N;
     double *eri, *M;
-    PP_TRY(ws_get(c, "bm_eri", sizeof(double) * n2 * n2, (void**)&eri));
     if (where == PPRPA_DEVICE) M = Mout;
     else PP_TRY(ws_get(c, "bm_M", mbytes, (void**)&M));
-    PP_TRY(build_explicit(c, pt, mult, eri, M));
+    if (mult == PPRPA_AB) {
+        PP_TRY(build_ab(c, pt, M));
+    } else {
+        PP_TRY(ws_get(c, "bm_eri", sizeof(double) * n2 * n2, (void**)&eri));
+        PP_TRY(build_explicit(c, pt, mult, eri, M));
+    }
     if (where != PPRPA_DEVICE)
         PP_CUDA(cudaMemcpyAsync(Mout, M, mbytes, cudaMemcpyDeviceToHost, c->stream));
     PP_CUDA(cudaStreamSynchronize(c->stream));

@@ -154,6 +154,43 @@ def test_fractional_path_reduces_to_integer_occupations():
     assert np.array_equal(e, s["eps"][orb])
 
 
+@pytest.mark.parametrize("no,nv", [(2, 3), (1, 4), (3, 3)])
+def test_alpha_beta_subspace_restricted_limit(no, nv):
+    """alpha = beta: the M_s = 0 pairs hold every singlet and one component of every
+    triplet, so the alpha-beta spectrum is the singlet roots plus the triplet roots."""
+    eps, L = small(no, nv, 6, 21 + no)
+    M, nvv, noo = oracle.build_matrix_ab(eps, no, L, eps, no, L)
+    ab = oracle.solve_full(M, nvv, noo)
+    s1 = oracle.solve_full(*oracle.build_matrix(eps, no, L, 1))
+    s3 = oracle.solve_full(*oracle.build_matrix(eps, no, L, 3))
+    for key in ("pp", "hh"):
+        ref = np.sort(np.concatenate([s1["omega_" + key], s3["omega_" + key]]))
+        assert np.allclose(np.sort(ab["omega_" + key]), ref, atol=1e-11)
+
+
+def test_unrestricted_three_subspaces_equal_spin_orbital_matrix():
+    """Different alpha and beta orbitals (and occupied counts): the spin-orbital spectrum is
+    alpha-alpha + beta-beta + alpha-beta (Sec. Implementation Details, three subspaces)."""
+    spec = synth.SystemSpec("t", 9, 3, 6, 3, 6, 81)
+    s = synth.make_system(spec)
+    rng = np.random.default_rng(82)
+    Q, _ = np.linalg.qr(rng.standard_normal((spec.nmo, spec.nmo)))
+    Cb = s["C"] @ Q  # different beta orbitals
+    ea = s["eps"]
+    eb = np.sort(s["eps"] + 0.05 * rng.standard_normal(spec.nmo))
+    oa, ob = 3, 2
+    La = oracle.ao_to_mo(s["ao3c"], s["C"], np.arange(spec.nmo))
+    Lb = oracle.ao_to_mo(s["ao3c"], Cb, np.arange(spec.nmo))
+    Mso, nvv, noo = oracle.spinorb_matrix_unrestricted(ea, oa, La, eb, ob, Lb)
+    so = oracle.solve_full(Mso, nvv, noo)
+    parts = [oracle.solve_full(*oracle.build_matrix(ea, oa, La, 3)),
+             oracle.solve_full(*oracle.build_matrix(eb, ob, Lb, 3)),
+             oracle.solve_full(*oracle.build_matrix_ab(ea, oa, La, eb, ob, Lb))]
+    for key in ("pp", "hh"):
+        ref = np.sort(np.concatenate([p["omega_" + key] for p in parts]))
+        assert np.allclose(np.sort(so["omega_" + key]), ref, atol=1e-10)
+
+
 @pytest.mark.parametrize("nv", [3, 5])
 def test_two_electrons_are_exact(nv):
     """No occupied orbitals: ppRPA roots equal the two-electron determinant CI."""
