@@ -329,7 +329,12 @@ def main():
     ms_per_step = elapsed / args.steps * 1e3
     value = replica_rate(world, args.steps, k, f_vec, elapsed)
 
-    # roofline of the tensor-core GEMM (all its launches in the timed region)
+    # roofline of the tensor-core GEMM (all its launches in the timed region).  DRAM traffic
+    # per launch from one ncu capture of this kernel build (four launches of one BF16 step
+    # of the same orbital space with naux 270: 5.895 GB; every term grows with naux), or
+    # None for a form that capture did not cover.
+    traffic = (5.895e9 / 4 / 270 * spec.naux
+               if args.precision == "bf16" and (spec.nocc_act, spec.nvir_act) == (50, 600) else None)
     tot_ms = float(prof[:, 1].sum())
     tot_launch = float(prof[:, 0].sum())
     alg = float(prof[:, 2].sum())
@@ -379,7 +384,8 @@ def main():
         "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel<1> (sigma sandwich, both stages)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "peak_source": peak_src,
-                     "traffic": None, "launches_per_step": tot_launch / args.steps,
+                     "traffic": traffic, "traffic_source": "profiles/tc_gemm_c2-naux270_full.md"
+                     if traffic else None, "launches_per_step": tot_launch / args.steps,
                      "avg_launch_ms": tot_ms / tot_launch if tot_launch else None,
                      "per_stage": per_stage},
     }
