@@ -652,6 +652,24 @@ int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int
         PP_TRY(tc_jobs(c, bp->prs[m], 0, c->naux, s1, s2, tiles, false));
         for (size_t t = s2_before; t < s2.size(); ++t) s2_tile_index.push_back((int)(before + (t - s2_before)));
     }
+    // The K slices of stage 2 were chosen per molecule (about four waves each); over a whole
+    // batch that splits far finer than the GPU needs, so re-split for four waves in total.
+    // The split form keeps its cap on auxiliary functions per accumulator.
+    if (env_int("PPRPA_BATCH_RESPLIT", 1) && !s2.empty()) {
+        int64_t base = 0;
+        for (const TcJobHost& h : s2) base += (int64_t)h.job.p.ntiles * h.job.p.nbatch;
+        const int64_t target = std::max<int64_t>(1, ceil_div(4LL * owner->num_sms, base));
+        const int pcap = env_int(nterms == 3 ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", nterms == 3 ? 2 : 128);
+        for (TcJobHost& h : s2) {
+            TcParams& p = h.job.p;
+            const int npc = p.kb_total / std::max(1, p.kq_blocks);
+            int64_t ns = std::min<int64_t>(target, std::max(1, p.kb_total / 8));
+            if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
+            const int64_t per = ceil_div(p.kb_total, std::max<int64_t>(1, ns));
+            p.nsplit = (int)ceil_div(p.kb_total, per);
+            p.total_items = p.ntiles * p.nbatch * p.nsplit;
+        }
+    }
     std::vector<TcJob> j1, j2;
     std::vector<TcItem> i1, i2;
     for (size_t j = 0; j < s1.size(); ++j) {
