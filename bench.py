@@ -190,7 +190,8 @@ def small_solve(pp, torch, stream):
 def batch_bench(pp, torch, stream, nmol, nvec, steps, warmup):
     """The 64-molecule batch workload: molecule m draws nocc ~ U{5..40}, nvir ~ U{50..400}
     (all active), naux = 3 nbasis, singlet if m is even; one step = one batched BF16
-    sigma of nvec vectors per molecule (one persistent launch per stage, CUDA graph)."""
+    sigma of nvec vectors per molecule (large molecules on their own clustered launches,
+    the rest in one persistent launch per stage replayed from a CUDA graph)."""
     ctxs, zs, outs, mults = [], [], [], []
     flops = 0.0
     t0 = time.perf_counter()

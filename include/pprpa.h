@@ -192,11 +192,12 @@ int pprpa_sigma(pprpa_ctx* ctx, int mult, int precision, int k, const double* z,
 
 /* pprpa_sigma_batch: sigma for many molecules at once (each its own context with its own
  * integrals; all on one device).  Molecule m applies its matrix (multiplicity mults[m]) to
- * ks[m] vectors z[m] -> sigma[m] (DEVICE pointers, layout of pprpa_sigma).  All stage-1
- * products of every molecule run in one persistent tensor-core launch and all stage-2
- * products in a second one; flags & 1 captures the device work in a CUDA graph that is
- * replayed while the arguments (pointers and sizes) stay the same.  Runs on ctxs[0]'s
- * stream; returns after the work completes.  precision: PPRPA_PREC_BF16 or
+ * ks[m] vectors z[m] -> sigma[m] (DEVICE pointers, layout of pprpa_sigma).  Molecules whose
+ * first stage alone fills the GPU many times over (about 26 waves of tiles) run on their own
+ * clustered launches; the stage-1 products of all other molecules run in one persistent
+ * tensor-core launch and their stage-2 products in a second one; flags & 1 captures that
+ * persistent part in a CUDA graph that is replayed while the arguments (pointers and sizes)
+ * stay the same.  Runs on ctxs[0]'s stream; returns after the work completes.  precision: PPRPA_PREC_BF16 or
  * PPRPA_PREC_BF16 + 16.  The tile widths are each context's autotuned ones (pprpa_autotune)
  * or the model's choice. */
 int pprpa_sigma_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,

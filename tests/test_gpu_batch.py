@@ -30,9 +30,16 @@ def molecule(no, nv, naux, seed):
     return spec, s, orb
 
 
+@pytest.mark.parametrize("seq_tiles", [None, "0", "500", "1000000"])
 @pytest.mark.parametrize("prec_name,tol", [("PREC_BF16", 2e-2), ("PREC_BF16_SPLIT", 2e-5)])
-def test_sigma_batch_matches_per_molecule(pp, prec_name, tol):
+def test_sigma_batch_matches_per_molecule(pp, monkeypatch, prec_name, tol, seq_tiles):
+    """seq_tiles: the first-stage tile count at which a molecule runs on its own launches
+    ("0": all of them; "500": the two largest here; default and huge: none, one persistent
+    launch)."""
     import torch
+
+    if seq_tiles is not None:
+        monkeypatch.setenv("PPRPA_BATCH_SEQ_TILES", seq_tiles)
 
     prec = getattr(pp, prec_name)
     ctxs, zs, outs, refs, scales, mults = [], [], [], [], [], []
