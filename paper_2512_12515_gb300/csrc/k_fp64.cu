@@ -17,9 +17,11 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int n0 = blockIdx.x * DG_BN, m0 = blockIdx.y * DG_BM;
+    // blockIdx.z = ((batch * rsplit) + rslice) * splitk + kslice
     const int z = blockIdx.z;
     const int split = z % g.splitk;
-    const int b = z / g.splitk;
+    const int rs = (z / g.splitk) % g.rsplit;
+    const int b = z / (g.splitk * g.rsplit);
     const int i2 = b % g.nb2, i1 = b / g.nb2;
     const double* A0 = g.A + i1 * g.sA1 + i2 * g.sA2;
     const double* B0 = g.B + i1 * g.sB1 + i2 * g.sB2;
@@ -37,7 +39,10 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-    for (int r = 0; r < g.nr; ++r) {
+    // this CTA's slice of the reduction over batches r (all of them unless rsplit > 1)
+    const int rper = (g.nr + g.rsplit - 1) / g.rsplit;
+    const int r0 = rs * rper, r1 = min(g.nr, r0 + rper);
+    for (int r = r0; r < r1; ++r) {
         const double* A = A0 + r * g.sAr;
         const double* B = B0 + r * g.sBr;
         for (int k0 = kbeg; k0 < kend; k0 += DG_BK) {
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
             const int64_t gn = n0 + tx + 16 * j;
             if (gn >= g.N) continue;
             double* c = C + gm * g.ldc + gn;
-            if (g.splitk > 1) {
+            if (g.splitk > 1 || g.rsplit > 1) {
                 atomicAdd(c, g.alpha * acc[i][j]);
             } else {
                 double v = g.alpha * acc[i][j];
@@ -106,9 +111,37 @@ int auto_splitk(int M, int N, int K, int batches) {
     return s < 1 ? 1 : (int)s;
 }
 
-int dgemm(const Dgemm& g, cudaStream_t st) {
+// C = beta * C over every output element of g (before the atomic accumulation of a launch
+// whose reduction over batches is split).
+__global__ void dgemm_scale_c_kernel(Dgemm g) {
+    const int64_t per = (int64_t)g.M * g.N;
+    const int64_t total = per * g.nb1 * g.nb2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / per, e = t % per;
+        const int i1 = (int)(b / g.nb2), i2 = (int)(b % g.nb2);
+        double* c = g.C + i1 * g.sC1 + i2 * g.sC2 + (e / g.N) * g.ldc + (e % g.N);
+        *c = g.beta == 0.0 ? 0.0 : g.beta * *c;
+    }
+}
+
+int dgemm(const Dgemm& gin, cudaStream_t st) {
+    Dgemm g = gin;
     if (g.M <= 0 || g.N <= 0) return PPRPA_OK;
-    const int64_t zb = (int64_t)g.nb1 * g.nb2 * g.splitk;
+    // FP64 arithmetic is scarce on this GPU: a launch with few output tiles and a long
+    // reduction over batches (sum_r A_r B_r) spreads that reduction over CTAs, which then add
+    // their partial sums atomically into C after C has been scaled by beta
+    g.rsplit = 1;
+    if (g.nr > 1 && g.splitk == 1) {
+        const int64_t tiles = ceil_div(g.N, DG_BN) * ceil_div(g.M, DG_BM) * (int64_t)g.nb1 * g.nb2;
+        if (tiles < 2 * 152) g.rsplit = (int)std::min<int64_t>(g.nr, ceil_div(2 * 152, tiles));
+    }
+    if (g.rsplit > 1) {
+        const int64_t total = (int64_t)g.M * g.N * g.nb1 * g.nb2;
+        dgemm_scale_c_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 8), 256, 0, st>>>(g);
+        PP_CHECK_LAUNCH();
+    }
+    const int64_t zb = (int64_t)g.nb1 * g.nb2 * g.splitk * g.rsplit;
     if (zb > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: too many batches");
     if (g.K <= 0 || g.nr <= 0) {
         // C = beta * C

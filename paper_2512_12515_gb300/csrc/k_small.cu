@@ -12,7 +12,10 @@
 namespace pprpa {
 
 constexpr int RR_THREADS = 1024;
-constexpr int RR_SMEM_MAX = 96;  // matrices up to 96 x 96 live in shared memory
+// Subspace matrices up to 112 x 112 keep H and U in shared memory (2 x 98 KB plus ~13 KB of
+// static shared memory, within the 227 KB a CTA may use); larger ones work in global memory,
+// where the Jacobi sweeps are several times slower.
+constexpr int RR_SMEM_MAX = 112;
 
 // In-place Cholesky of the lower triangle of K (m x m, ld).  Returns false on a
 // pivot <= rel_tol * scale.  All threads of the block must call it.

@@ -25,6 +25,7 @@ struct Dgemm {
     int nb1 = 1, nb2 = 1, nr = 1;
     double alpha = 1.0, beta = 0.0;
     int splitk = 1;
+    int rsplit = 1;  // set by dgemm(): CTAs sharing the reduction over r (atomic accumulation)
 };
 int dgemm(const Dgemm& g, cudaStream_t st);
 // Picks a split-K factor for a GEMM whose output has few tiles.

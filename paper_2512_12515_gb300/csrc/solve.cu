@@ -258,7 +258,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     const int nguess = std::min(npos_blk, std::max(2 * nroots, nroots + 8));
     // subspace cap and thick-restart size: unstable problems (complex pairs near the
     // targets) need a restart that keeps many Ritz vectors, so both are generous
-    int m_max = o->max_subspace > 0 ? o->max_subspace : 128;
+    // automatic cap: the largest subspace whose Rayleigh-Ritz matrices stay in shared memory
+    int m_max = o->max_subspace > 0 ? o->max_subspace : 112;
     m_max = std::min(m_max, 128);
     m_max = std::min(m_max, N);
     if (m_max < nguess + 1 && N > nguess) m_max = std::min(N, nguess + 1);
