@@ -150,7 +150,7 @@ extern "C" int pprpa_analyze(pprpa_ctx* c, int root, double* D2e, double* lam_p,
         PP_TRY(ws_get(c, "an_C1", sizeof(double) * mm, (void**)&C1));
         PP_TRY(ws_get(c, "an_C2", sizeof(double) * mm, (void**)&C2));
         PP_TRY(ws_get(c, "an_lam", sizeof(double) * mmax, (void**)&lam));
-        PP_TRY(ws_get(c, "an_work", sizeof(double) * 1152, (void**)&work));
+        PP_TRY(ws_get(c, "an_work", sizeof(double) * 8192, (void**)&work));
         PP_TRY(ws_get(c, "an_iwork", sizeof(int) * 1024, (void**)&iwork));
         for (int blk = 0; blk < 2; ++blk) {
             const bool want = blk == 0 ? want_p : want_h;

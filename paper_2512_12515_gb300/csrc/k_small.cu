@@ -17,6 +17,8 @@ constexpr int RR_THREADS = 1024;
 // where the Jacobi sweeps are several times slower.
 constexpr int RR_SMEM_MAX = 112;
 
+__host__ __device__ inline int rr_ld(int m, int pad) { return pad ? (m | 1) : m; }
+
 // In-place Cholesky of the lower triangle of K (m x m, ld).  Returns false on a
 // pivot <= rel_tol * scale.  All threads of the block must call it.
 __device__ bool block_cholesky(double* K, int m, int ld, double rel_tol, double scale,
@@ -137,6 +139,309 @@ __device__ int block_jacobi(double* H, double* U, int m, int ld, double* rot, in
     return sweep;
 }
 
+// The same parallel cyclic Jacobi with H <- J^T H J done in one pass over the 2 x 2 blocks of
+// the pairing: block (a, b), a <= b, gets the row rotation of pair a and the column rotation of
+// pair b, and is written to both triangles.  Distinct blocks touch disjoint entries, so the
+// update is in place; U <- U J runs in the same pass.  Two thirds of the FP64 operations and
+// two barriers per round instead of three.
+__device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot, int* pairs,
+                                double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        U[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    }
+    const int me = (m + 1) & ~1;
+    const int half = me / 2;
+    const int nblk = half * (half + 1) / 2;
+    int sweep = 0;
+    for (; sweep < 40; ++sweep) {
+        __syncthreads();
+        double off = 0.0, tot = 0.0;
+        for (int t = tid; t < m * m; t += nt) {
+            const int i = t / m, j = t % m;
+            const double h = H[i * ld + j];
+            tot += h * h;
+            if (i != j) off += h * h;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = off; red[2 * (tid >> 5) + 1] = tot; }
+        __syncthreads();
+        if (tid == 0) {
+            double x = 0.0, y = 0.0;
+            for (int w = 0; w < nt / 32; ++w) { x += red[2 * w]; y += red[2 * w + 1]; }
+            red[64] = x;
+            red[65] = y;
+        }
+        __syncthreads();
+        if (!(red[64] > 1e-30 * red[65]) || me < 2) break;
+        for (int s = 0; s < me - 1; ++s) {
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                if (i == 0) { p = me - 1; q = s; }
+                else { p = (s + i) % (me - 1); q = (s - i + (me - 1)) % (me - 1); }
+                if (p > q) { const int x = p; p = q; q = x; }
+                pairs[2 * i] = p;
+                pairs[2 * i + 1] = q;
+                double c = 1.0, sn = 0.0;
+                if (q < m) {
+                    const double apq = H[p * ld + q];
+                    const double app = H[p * ld + p], aqq = H[q * ld + q];
+                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = tt * c;
+                    }
+                }
+                rot[2 * i] = c;
+                rot[2 * i + 1] = sn;
+            }
+            __syncthreads();
+            // H: blocks (a, b), a <= b, in triangular order t = b (b + 1) / 2 + a
+            for (int t = tid; t < nblk; t += nt) {
+                int b = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+                while (b * (b + 1) / 2 > t) --b;
+                while ((b + 1) * (b + 2) / 2 <= t) ++b;
+                const int aa = t - b * (b + 1) / 2;
+                const int pa = pairs[2 * aa], qa = pairs[2 * aa + 1];
+                const int pb = pairs[2 * b], qb = pairs[2 * b + 1];
+                const bool va = qa < m, vb = qb < m;  // q = m marks the dummy player (odd m)
+                const double ca = rot[2 * aa], sa = rot[2 * aa + 1];
+                const double cb = rot[2 * b], sb = rot[2 * b + 1];
+                const double h00 = H[pa * ld + pb];
+                const double h01 = vb ? H[pa * ld + qb] : 0.0;
+                const double h10 = va ? H[qa * ld + pb] : 0.0;
+                const double h11 = (va && vb) ? H[qa * ld + qb] : 0.0;
+                // rows: (p, q) <- (c h_p - s h_q, s h_p + c h_q)
+                const double r00 = ca * h00 - sa * h10, r01 = ca * h01 - sa * h11;
+                const double r10 = sa * h00 + ca * h10, r11 = sa * h01 + ca * h11;
+                // columns, the same rotation form
+                const double o00 = cb * r00 - sb * r01, o01 = sb * r00 + cb * r01;
+                const double o10 = cb * r10 - sb * r11, o11 = sb * r10 + cb * r11;
+                if (aa == b) {
+                    const double od = 0.5 * (o01 + o10);
+                    H[pa * ld + pa] = o00;
+                    if (va) {
+                        H[pa * ld + qa] = od;
+                        H[qa * ld + pa] = od;
+                        H[qa * ld + qa] = o11;
+                    }
+                } else {
+                    H[pa * ld + pb] = o00;
+                    H[pb * ld + pa] = o00;
+                    if (vb) { H[pa * ld + qb] = o01; H[qb * ld + pa] = o01; }
+                    if (va) { H[qa * ld + pb] = o10; H[pb * ld + qa] = o10; }
+                    if (va && vb) { H[qa * ld + qb] = o11; H[qb * ld + qa] = o11; }
+                }
+            }
+            // U <- U J (one thread per row and pair; consecutive threads take consecutive rows)
+            for (int t = tid; t < half * m; t += nt) {
+                const int i = t / m, row = t % m;
+                const int p = pairs[2 * i], q = pairs[2 * i + 1];
+                if (q >= m) continue;
+                const double c = rot[2 * i], sn = rot[2 * i + 1];
+                const double up = U[row * ld + p], uq = U[row * ld + q];
+                U[row * ld + p] = c * up - sn * uq;
+                U[row * ld + q] = sn * up + c * uq;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    return sweep;
+}
+
+// Symmetric eigendecomposition by Householder reduction to tridiagonal form followed by the
+// implicit symmetric QR iteration with Wilkinson shifts (Golub and Van Loan, Matrix
+// Computations, Secs. 8.3.1 and 8.3.3).  FP64 arithmetic is scarce on this GPU, and this needs
+// a few times fewer operations than cyclic Jacobi sweeps, and O(m) CTA barriers: each QR step's
+// chain of rotations is formed by one thread and then applied to the rows of U in parallel.
+// Same contract as block_jacobi: H (m x m, ld, symmetric) is overwritten with its eigenvalues on
+// the diagonal (the rest is scratch), U (m x m, ld) receives the eigenvectors as columns.
+// vec: >= 6m doubles of scratch.  Returns the number of QR steps.
+__device__ int block_tridiag_eig(double* H, double* U, int m, int ld, double* vec) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double red_s[33];
+    __shared__ int lh_s[3];
+    double* d = vec;              // diagonal of T
+    double* e = vec + m;          // e[k] = T[k][k+1]
+    double* beta = vec + 2 * m;   // Householder scalars
+    double* cs = vec + 3 * m;     // rotation chain of one QR step
+    double* sn = vec + 4 * m;
+    double* pw = vec + 5 * m;     // p, then w, of one Householder step
+    auto block_sum = [&](double x) -> double {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        __syncthreads();
+        if ((tid & 31) == 0) red_s[tid >> 5] = x;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nt / 32; ++w) t += red_s[w];
+            red_s[32] = t;
+        }
+        __syncthreads();
+        return red_s[32];
+    };
+    // ---- Householder: column k below the subdiagonal is reflected onto e_{k+1} ----
+    for (int k = 0; k + 2 < m; ++k) {
+        const int r0 = k + 1, r = m - r0;  // trailing block rows/columns r0 .. m-1
+        double x2 = 0.0;
+        for (int i = tid; i < r; i += nt) x2 += H[(r0 + i) * ld + k] * H[(r0 + i) * ld + k];
+        x2 = block_sum(x2);
+        const double x0 = H[r0 * ld + k];
+        if (x2 <= 1e-300) {  // nothing to eliminate
+            if (tid == 0) { beta[k] = 0.0; e[k] = x0; d[k] = H[k * ld + k]; }
+            __syncthreads();
+            continue;
+        }
+        const double alpha = x0 >= 0.0 ? -sqrt(x2) : sqrt(x2);
+        const double bt = x2 - x0 * alpha;  // v^T v / 2 with v = x - alpha e_1
+        __syncthreads();
+        if (tid == 0) {
+            H[r0 * ld + k] = x0 - alpha;  // v stays in the column (v_i = x_i for i > 0)
+            beta[k] = bt;
+            e[k] = alpha;
+            d[k] = H[k * ld + k];
+        }
+        __syncthreads();
+        // p = A22 v / beta; A22 is symmetric, so thread i walks column i (coalesced)
+        for (int i = tid; i < r; i += nt) {
+            double acc = 0.0;
+            for (int j = 0; j < r; ++j) acc = fma(H[(r0 + j) * ld + r0 + i], H[(r0 + j) * ld + k], acc);
+            pw[i] = acc / bt;
+        }
+        __syncthreads();
+        double vp = 0.0;
+        for (int i = tid; i < r; i += nt) vp += H[(r0 + i) * ld + k] * pw[i];
+        vp = block_sum(vp);
+        const double kk = vp / (2.0 * bt);
+        for (int i = tid; i < r; i += nt) pw[i] -= kk * H[(r0 + i) * ld + k];  // w = p - K v
+        __syncthreads();
+        // A22 -= v w^T + w v^T
+        for (int t = tid; t < r * r; t += nt) {
+            const int i = t / r, j = t % r;
+            const double vi = H[(r0 + i) * ld + k], vj = H[(r0 + j) * ld + k];
+            H[(r0 + i) * ld + r0 + j] -= vi * pw[j] + pw[i] * vj;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (m >= 2) {
+            d[m - 2] = H[(m - 2) * ld + m - 2];
+            e[m - 2] = H[(m - 1) * ld + m - 2];
+            beta[m - 2] = 0.0;
+        }
+        d[m - 1] = H[(m - 1) * ld + m - 1];
+        e[m - 1] = 0.0;
+    }
+    // ---- Q = H_0 H_1 ... H_{m-3}, built from the right on the identity ----
+    for (int t = tid; t < m * m; t += nt) U[(t / m) * ld + t % m] = (t / m == t % m) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = m - 3; k >= 0; --k) {
+        const double bt = beta[k];
+        if (bt == 0.0) continue;
+        const int r0 = k + 1, r = m - r0;
+        // rows r0.. of U: U -= v (v^T U) / beta, columns r0.. (the others are still identity)
+        for (int j = tid; j < r; j += nt) {
+            double acc = 0.0;
+            for (int i = 0; i < r; ++i) acc = fma(H[(r0 + i) * ld + k], U[(r0 + i) * ld + r0 + j], acc);
+            pw[j] = acc / bt;
+        }
+        __syncthreads();
+        for (int t = tid; t < r * r; t += nt) {
+            const int i = t / r, j = t % r;
+            U[(r0 + i) * ld + r0 + j] -= H[(r0 + i) * ld + k] * pw[j];
+        }
+        __syncthreads();
+    }
+    // U now holds Q.  The rotations below act on pairs of columns of Q; they are applied to
+    // the rows of Q^T instead, so that the threads (one per row of Q) touch consecutive words.
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        if (i < j) {
+            const double x = U[i * ld + j];
+            U[i * ld + j] = U[j * ld + i];
+            U[j * ld + i] = x;
+        }
+    }
+    __syncthreads();
+    // ---- implicit QR steps with Wilkinson shifts on the unreduced trailing block ----
+    int steps = 0;
+    const int max_steps = 40 * m + 40;
+    for (;;) {
+        if (tid == 0) {
+            int h = lh_s[1] = -1;
+            // deflate from the bottom: the largest h whose e[h-1] is not negligible
+            for (h = m - 1; h > 0; --h) {
+                if (fabs(e[h - 1]) <= 2.2e-16 * (fabs(d[h - 1]) + fabs(d[h])) + 1e-300) e[h - 1] = 0.0;
+                else break;
+            }
+            int l = h;
+            while (l > 0 && fabs(e[l - 1]) > 2.2e-16 * (fabs(d[l - 1]) + fabs(d[l])) + 1e-300) --l;
+            if (l > 0) e[l - 1] = 0.0;
+            lh_s[0] = l;
+            lh_s[1] = h;
+            if (h > 0 && steps < max_steps) {
+                // Wilkinson shift from the trailing 2 x 2
+                const double a = d[h - 1], b = e[h - 1], c = d[h];
+                const double dl = 0.5 * (a - c);
+                const double den = dl + (dl >= 0.0 ? 1.0 : -1.0) * hypot(dl, b);
+                const double mu = den != 0.0 ? c - b * b / den : c;
+                double x = d[l] - mu, z = e[l];
+                for (int k = l; k < h; ++k) {
+                    const double r2 = fma(x, x, z * z);  // |x|, |z| are far from overflow here
+                    const double inv = r2 > 0.0 ? rsqrt(r2) : 0.0;
+                    const double rr = r2 * inv;
+                    const double cc = r2 > 0.0 ? x * inv : 1.0, ss = z * inv;
+                    if (k > l) e[k - 1] = rr;
+                    const double dk = d[k], ek = e[k], dk1 = d[k + 1];
+                    d[k] = cc * cc * dk + 2.0 * cc * ss * ek + ss * ss * dk1;
+                    d[k + 1] = ss * ss * dk - 2.0 * cc * ss * ek + cc * cc * dk1;
+                    e[k] = cc * ss * (dk1 - dk) + (cc * cc - ss * ss) * ek;
+                    if (k + 1 < h) {
+                        z = ss * e[k + 1];
+                        e[k + 1] = cc * e[k + 1];
+                        x = e[k];
+                    }
+                    cs[k] = cc;
+                    sn[k] = ss;
+                }
+            }
+        }
+        __syncthreads();
+        const int l = lh_s[0], h = lh_s[1];
+        if (h <= 0 || steps >= max_steps) break;
+        // Q <- Q G_l ... G_{h-1}: each thread applies the whole chain to its row of Q, stored
+        // as column `row` of Q^T
+        for (int row = tid; row < m; row += nt) {
+            double uk = U[l * ld + row];
+            for (int k = l; k < h; ++k) {
+                const double c = cs[k], s = sn[k], uk1 = U[(k + 1) * ld + row];
+                U[k * ld + row] = c * uk + s * uk1;
+                uk = -s * uk + c * uk1;
+            }
+            U[h * ld + row] = uk;
+        }
+        ++steps;
+        __syncthreads();
+    }
+    for (int t = tid; t < m * m; t += nt) {  // Q^T back to Q: eigenvectors as columns
+        const int i = t / m, j = t % m;
+        if (i < j) {
+            const double x = U[i * ld + j];
+            U[i * ld + j] = U[j * ld + i];
+            U[j * ld + i] = x;
+        }
+    }
+    for (int i = tid; i < m; i += nt) H[i * ld + i] = d[i];
+    __syncthreads();
+    return steps;
+}
+
 __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) {
     extern __shared__ double sm[];
     __shared__ double rot[2 * 512 + 2];
@@ -146,11 +451,14 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     __shared__ int npos_sh;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int m = a.m, ld = a.ld;
-    const int lw = m;  // leading dimension of work matrices
+    const int lw = m;  // leading dimension of the global work matrices
     const bool in_smem = m <= RR_SMEM_MAX;
+    // H and U in shared memory get an odd leading dimension: column-wise walks (one thread per
+    // row) then fall on distinct banks
+    const int lh = in_smem ? rr_ld(m, a.pad) : m;
     double* Kc = a.work;                          // Cholesky factor (global)
     double* H = in_smem ? sm : a.work + (size_t)m * m;
-    double* U = in_smem ? sm + (size_t)m * m : a.work + 2 * (size_t)m * m;
+    double* U = in_smem ? sm + (size_t)m * lh : a.work + 2 * (size_t)m * m;
     double* X = a.work + 3 * (size_t)m * m;       // triangular-solve scratch
     int* rank = (int*)(a.work + 4 * (size_t)m * m);
 
@@ -203,30 +511,33 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     for (int col = tid; col < m; col += nt) {
         for (int i = 0; i < m; ++i) {
             double v = X[col * lw + i];
-            for (int l = 0; l < i; ++l) v -= Kc[i * lw + l] * H[l * lw + col];
-            H[i * lw + col] = v / Kc[i * lw + i];
+            for (int l = 0; l < i; ++l) v -= Kc[i * lw + l] * H[l * lh + col];
+            H[i * lh + col] = v / Kc[i * lw + i];
         }
     }
     __syncthreads();
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
         if (i < j) {
-            const double v = 0.5 * (H[i * lw + j] + H[j * lw + i]);
-            H[i * lw + j] = v;
-            H[j * lw + i] = v;
+            const double v = 0.5 * (H[i * lh + j] + H[j * lh + i]);
+            H[i * lh + j] = v;
+            H[j * lh + i] = v;
         }
     }
-    const int sweeps = block_jacobi(H, U, m, lw, rot, pairs, red);
+    const int sweeps = a.eig == 0   ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
+                       : a.eig == 1 ? block_jacobi(H, U, m, lh, rot, pairs, red)
+                                    : block_tridiag_eig(H, U, m, lh,
+                                                        6 * m <= 2 * 512 + 2 ? rot : a.work + 4 * (size_t)m * m + m);
     // rank the positive kappas (descending) -> targets
     if (tid == 0) npos_sh = 0;
     __syncthreads();
     for (int i = tid; i < m; i += nt) {
-        const double ki = H[i * lw + i];
+        const double ki = H[i * lh + i];
         int r = -1;
         if (ki > 0.0) {
             r = 0;
             for (int j = 0; j < m; ++j) {
-                const double kj = H[j * lw + j];
+                const double kj = H[j * lh + j];
                 if (kj > 0.0 && (kj > ki || (kj == ki && j < i))) ++r;
             }
             atomicAdd(&npos_sh, 1);
@@ -240,10 +551,10 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     for (int i = tid; i < m; i += nt) {
         const int r = rank[i];
         if (r < 0 || r >= nk) continue;
-        const double kap = H[i * lw + i];
+        const double kap = H[i * lh + i];
         double* c = a.coef + (size_t)r * m;
         for (int row = m - 1; row >= 0; --row) {
-            double v = U[row * lw + i];
+            double v = U[row * lh + i];
             for (int l = row + 1; l < m; ++l) v -= Kc[l * lw + row] * c[l];
             c[row] = v / Kc[row * lw + row];
         }
@@ -255,7 +566,7 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     if (tid == 0) {
         double kmin = 0.0, kmax = 0.0;
         for (int i = 0; i < m; ++i) {
-            const double k = H[i * lw + i];
+            const double k = H[i * lh + i];
             if (k < kmin) kmin = k;
             if (k > kmax) kmax = k;
         }
@@ -268,13 +579,29 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     }
 }
 
-int launch_rayleigh_ritz(const RRArgs& a, cudaStream_t st) {
+// Eigensolver of the one-CTA kernels: 0 Jacobi with the fused symmetric update (default),
+// 1 Jacobi with separate row and column passes, 2 Householder + implicit QR (PPRPA_EIG).
+static int eig_method() {
+    const char* v = getenv("PPRPA_EIG");
+    return v ? atoi(v) : 0;
+}
+
+// Odd leading dimension of the shared-memory matrices unless PPRPA_RR_PAD=0.
+static int rr_pad() {
+    const char* v = getenv("PPRPA_RR_PAD");
+    return v ? atoi(v) : 1;
+}
+
+int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
+    RRArgs a = ain;
+    a.eig = eig_method();
     if (a.m <= 0 || a.m > 1024) return set_error(PPRPA_ERR_ARG, "rayleigh_ritz: size must be 1..1024");
-    const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * a.m : 0;
+    a.pad = rr_pad();
+    const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * sizeof(double) * RR_SMEM_MAX * RR_SMEM_MAX);
+                             2 * sizeof(double) * RR_SMEM_MAX * (RR_SMEM_MAX + 1));
         attr_set = true;
     }
     rayleigh_ritz_kernel<<<1, RR_THREADS, smem, st>>>(a);
@@ -341,19 +668,21 @@ int launch_cholqr_small(const double* Gm, int k, double tol, double* T, int* kee
 // Symmetric eigendecomposition of `batch` matrices H (m x m each, row-major, `stride` doubles
 // apart) by the one-CTA parallel Jacobi above, one CTA per matrix: H is overwritten (the
 // eigenvalues end on its diagonal) and U receives the eigenvectors as columns.
-// work: batch x 1152 doubles, iwork: batch x 1024 ints (m <= 1024).
+// work: batch x 8192 doubles, iwork: batch x 1024 ints (m <= 1024).
 __global__ void __launch_bounds__(1024, 1) sym_eig_kernel(double* H, double* U, int m, int64_t stride,
-                                                          double* work, int* iwork) {
+                                                          double* work, int* iwork, int eig) {
     const int b = blockIdx.x;
-    double* rot = work + (int64_t)b * 1152;
-    block_jacobi(H + b * stride, U + b * stride, m, m, rot, iwork + (int64_t)b * 1024, rot + 1024);
+    double* w = work + (int64_t)b * 8192;
+    if (eig == 0) block_jacobi_sym(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
+    else if (eig == 1) block_jacobi(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
+    else block_tridiag_eig(H + b * stride, U + b * stride, m, m, w);
 }
 
 int launch_sym_eig(double* H, double* U, int m, int batch, int64_t stride, double* work, int* iwork,
                    cudaStream_t st) {
     if (m <= 0 || batch <= 0) return PPRPA_OK;
     if (m > 1024) return set_error(PPRPA_ERR_ARG, "sym_eig: order above 1024");
-    sym_eig_kernel<<<batch, 1024, 0, st>>>(H, U, m, stride, work, iwork);
+    sym_eig_kernel<<<batch, 1024, 0, st>>>(H, U, m, stride, work, iwork, eig_method());
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }

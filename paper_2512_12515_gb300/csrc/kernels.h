@@ -103,7 +103,9 @@ struct RRArgs {
     int nmu = 0;
     int nwant = 0;    // targets (lowest positive-norm roots)
     int nkeep = 0;    // Ritz vectors returned (>= nwant)
-    double* work = nullptr;  // >= 4*m*m + m doubles
+    double* work = nullptr;  // >= 4*m*m + 8*m doubles
+    int eig = 0;             // set by the launcher: 0 Jacobi (fused update), 1 Jacobi, 2 Householder + QR
+    int pad = 1;             // set by the launcher: odd leading dimension of H and U in shared memory
     double* omega = nullptr;   // nkeep
     double* coef = nullptr;    // nkeep x m (row j = coefficients of Ritz vector j)
     double* info = nullptr;    // [0]=status, [1]=mu used, [2]=npos, [3]=omega_min_pp,
@@ -134,7 +136,7 @@ int launch_rr_general(const RRGenArgs& a, cudaStream_t st);
 // T * X orthonormal rows; rows whose residual pivot is below tol are zeroed and flagged
 // keep[j] = 0.
 // Symmetric eigendecomposition (one CTA per m x m matrix, m <= 1024): eigenvalues on the
-// diagonal of H, eigenvectors as the columns of U.  work: batch*1152 doubles, iwork: batch*1024.
+// diagonal of H, eigenvectors as the columns of U.  work: batch*8192 doubles, iwork: batch*1024.
 int launch_sym_eig(double* H, double* U, int m, int batch, int64_t stride, double* work, int* iwork,
                    cudaStream_t st);
 int launch_cholqr_small(const double* Gm, int k, double tol, double* T, int* keep,

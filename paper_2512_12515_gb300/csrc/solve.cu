@@ -166,7 +166,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     PP_TRY(ws_get(c, "full_eri", sizeof(double) * n2 * n2, (void**)&eri));
     PP_TRY(ws_get(c, "full_M", sizeof(double) * (size_t)N * N, (void**)&M));
     PP_TRY(ws_get(c, "full_W", sizeof(double) * (size_t)N * N, (void**)&W));
-    PP_TRY(ws_get(c, "full_work", sizeof(double) * (4 * (size_t)N * N + N), (void**)&work));
+    PP_TRY(ws_get(c, "full_work", sizeof(double) * (4 * (size_t)N * N + 8 * (size_t)N), (void**)&work));
     PP_TRY(ws_get(c, "full_om", sizeof(double) * N, (void**)&om));
     PP_TRY(ws_get(c, "full_coef", sizeof(double) * (size_t)N * N, (void**)&coef));
     PP_TRY(ws_get(c, "full_info", sizeof(double) * 8, (void**)&rinfo));
@@ -287,7 +287,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(ws_get(c, "dv_Dn", sizeof(double) * (size_t)nbuf * N, (void**)&Dn));
     PP_TRY(ws_get(c, "dv_Dn2", sizeof(double) * (size_t)nbuf * N, (void**)&Dn2));
     PP_TRY(ws_get(c, "dv_H", sizeof(double) * m_max * m_max, (void**)&H));
-    PP_TRY(ws_get(c, "dv_rwork", sizeof(double) * (4 * (size_t)m_max * m_max + m_max), (void**)&rwork));
+    PP_TRY(ws_get(c, "dv_rwork", sizeof(double) * (4 * (size_t)m_max * m_max + 8 * (size_t)m_max), (void**)&rwork));
     PP_TRY(ws_get(c, "dv_om", sizeof(double) * m_max, (void**)&om));
     PP_TRY(ws_get(c, "dv_coef", sizeof(double) * m_max * m_max, (void**)&coef));
     PP_TRY(ws_get(c, "dv_info", sizeof(double) * 8, (void**)&rinfo));
@@ -459,8 +459,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         }
         if (ntg < nroots) rmax = std::max(rmax, 1e300);  // not enough real roots yet
         if (env_int("PPRPA_LOG", 0))
-            fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e\n", it, stage, m,
-                    mu_prev, h_om[0], rmax);
+            fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e sweeps %d\n", it, stage,
+                    m, mu_prev, h_om[0], rmax, general ? -1 : (int)hinfo[5]);
         if (info) info->max_resid = rmax;
         if (stage == 1 || stage == 3) {
             ++stage1_iters;
