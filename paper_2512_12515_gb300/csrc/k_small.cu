@@ -139,17 +139,27 @@ __device__ int block_jacobi(double* H, double* U, int m, int ld, double* rot, in
     return sweep;
 }
 
+__device__ inline double jsqrt(double x) { return sqrt(x); }
+__device__ inline float jsqrt(float x) { return sqrtf(x); }
+__device__ inline double jabs(double x) { return fabs(x); }
+__device__ inline float jabs(float x) { return fabsf(x); }
+__device__ inline double jrsqrt(double x) { return rsqrt(x); }
+__device__ inline float jrsqrt(float x) { return rsqrtf(x); }
+
 // The same parallel cyclic Jacobi with H <- J^T H J done in one pass over the 2 x 2 blocks of
 // the pairing: block (a, b), a <= b, gets the row rotation of pair a and the column rotation of
 // pair b, and is written to both triangles.  Distinct blocks touch disjoint entries, so the
 // update is in place; U <- U J runs in the same pass.  Two thirds of the FP64 operations and
-// two barriers per round instead of three.
-__device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot, int* pairs,
-                                double* red) {
+// two barriers per round instead of three.  T = float serves the first pass of the mixed
+// solver below.  Sweeps stop once off-diagonal^2 <= tol2 * total^2 (Frobenius); rotations
+// with |h_pq| <= skip * sqrt|h_pp h_qq| are skipped.
+template <typename T>
+__device__ int jacobi_sym_t(T* H, T* U, int m, int ld, T* rot, int* pairs, double* red, double tol2,
+                            T skip, T tiny) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
-        U[i * ld + j] = (i == j) ? 1.0 : 0.0;
+        U[i * ld + j] = (i == j) ? T(1) : T(0);
     }
     const int me = (m + 1) & ~1;
     const int half = me / 2;
@@ -157,18 +167,19 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
     int sweep = 0;
     for (; sweep < 40; ++sweep) {
         __syncthreads();
-        double off = 0.0, tot = 0.0;
+        T off = 0, tot = 0;
         for (int t = tid; t < m * m; t += nt) {
             const int i = t / m, j = t % m;
-            const double h = H[i * ld + j];
+            const T h = H[i * ld + j];
             tot += h * h;
             if (i != j) off += h * h;
         }
+        double offd = off, totd = tot;
         for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            offd += __shfl_xor_sync(0xffffffffu, offd, o);
+            totd += __shfl_xor_sync(0xffffffffu, totd, o);
         }
-        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = off; red[2 * (tid >> 5) + 1] = tot; }
+        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = offd; red[2 * (tid >> 5) + 1] = totd; }
         __syncthreads();
         if (tid == 0) {
             double x = 0.0, y = 0.0;
@@ -177,7 +188,7 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
             red[65] = y;
         }
         __syncthreads();
-        if (!(red[64] > 1e-30 * red[65]) || me < 2) break;
+        if (!(red[64] > tol2 * red[65]) || me < 2) break;
         for (int s = 0; s < me - 1; ++s) {
             for (int i = tid; i < half; i += nt) {
                 int p, q;
@@ -186,14 +197,16 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
                 if (p > q) { const int x = p; p = q; q = x; }
                 pairs[2 * i] = p;
                 pairs[2 * i + 1] = q;
-                double c = 1.0, sn = 0.0;
+                T c = 1, sn = 0;
                 if (q < m) {
-                    const double apq = H[p * ld + q];
-                    const double app = H[p * ld + p], aqq = H[q * ld + q];
-                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + tt * tt);
+                    const T apq = H[p * ld + q];
+                    const T app = H[p * ld + p], aqq = H[q * ld + q];
+                    if (jabs(apq) > tiny && jabs(apq) > skip * jsqrt(jabs(app * aqq))) {
+                        // tan of the smaller annihilating angle, t = sgn(d) 2 h_pq / (|d| + sqrt(d^2 + 4 h_pq^2))
+                        // with d = h_qq - h_pp: one division, one square root and one reciprocal root
+                        const T d = aqq - app, a2 = T(2) * apq;
+                        const T tt = (d >= T(0) ? a2 : -a2) / (jabs(d) + jsqrt(d * d + a2 * a2));
+                        c = jrsqrt(T(1) + tt * tt);
                         sn = tt * c;
                     }
                 }
@@ -210,20 +223,20 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
                 const int pa = pairs[2 * aa], qa = pairs[2 * aa + 1];
                 const int pb = pairs[2 * b], qb = pairs[2 * b + 1];
                 const bool va = qa < m, vb = qb < m;  // q = m marks the dummy player (odd m)
-                const double ca = rot[2 * aa], sa = rot[2 * aa + 1];
-                const double cb = rot[2 * b], sb = rot[2 * b + 1];
-                const double h00 = H[pa * ld + pb];
-                const double h01 = vb ? H[pa * ld + qb] : 0.0;
-                const double h10 = va ? H[qa * ld + pb] : 0.0;
-                const double h11 = (va && vb) ? H[qa * ld + qb] : 0.0;
+                const T ca = rot[2 * aa], sa = rot[2 * aa + 1];
+                const T cb = rot[2 * b], sb = rot[2 * b + 1];
+                const T h00 = H[pa * ld + pb];
+                const T h01 = vb ? H[pa * ld + qb] : T(0);
+                const T h10 = va ? H[qa * ld + pb] : T(0);
+                const T h11 = (va && vb) ? H[qa * ld + qb] : T(0);
                 // rows: (p, q) <- (c h_p - s h_q, s h_p + c h_q)
-                const double r00 = ca * h00 - sa * h10, r01 = ca * h01 - sa * h11;
-                const double r10 = sa * h00 + ca * h10, r11 = sa * h01 + ca * h11;
+                const T r00 = ca * h00 - sa * h10, r01 = ca * h01 - sa * h11;
+                const T r10 = sa * h00 + ca * h10, r11 = sa * h01 + ca * h11;
                 // columns, the same rotation form
-                const double o00 = cb * r00 - sb * r01, o01 = sb * r00 + cb * r01;
-                const double o10 = cb * r10 - sb * r11, o11 = sb * r10 + cb * r11;
+                const T o00 = cb * r00 - sb * r01, o01 = sb * r00 + cb * r01;
+                const T o10 = cb * r10 - sb * r11, o11 = sb * r10 + cb * r11;
                 if (aa == b) {
-                    const double od = 0.5 * (o01 + o10);
+                    const T od = T(0.5) * (o01 + o10);
                     H[pa * ld + pa] = o00;
                     if (va) {
                         H[pa * ld + qa] = od;
@@ -243,8 +256,8 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
                 const int i = t / m, row = t % m;
                 const int p = pairs[2 * i], q = pairs[2 * i + 1];
                 if (q >= m) continue;
-                const double c = rot[2 * i], sn = rot[2 * i + 1];
-                const double up = U[row * ld + p], uq = U[row * ld + q];
+                const T c = rot[2 * i], sn = rot[2 * i + 1];
+                const T up = U[row * ld + p], uq = U[row * ld + q];
                 U[row * ld + p] = c * up - sn * uq;
                 U[row * ld + q] = sn * up + c * uq;
             }
@@ -253,6 +266,86 @@ __device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot
     }
     __syncthreads();
     return sweep;
+}
+
+__device__ int block_jacobi_sym(double* H, double* U, int m, int ld, double* rot, int* pairs,
+                                double* red, double tol2 = 1e-30) {
+    return jacobi_sym_t<double>(H, U, m, ld, rot, pairs, red, tol2, 1e-18, 1e-300);
+}
+
+// C (m x m, ldc) = op(A) B with op(A) = A or A^T; A (lda), B (ldb) row-major.  One thread per
+// output element; the FP64 pipe, not latency, bounds it with a full CTA of threads.
+__device__ void block_gemm(double* C, int ldc, const double* A, int lda, bool transA, const double* B,
+                           int ldb, int m) {
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const int i = t / m, j = t % m;
+        double acc = 0.0;
+        if (transA)
+            for (int k = 0; k < m; ++k) acc = fma(A[k * lda + i], B[k * ldb + j], acc);
+        else
+            for (int k = 0; k < m; ++k) acc = fma(A[i * lda + k], B[k * ldb + j], acc);
+        C[i * ldc + j] = acc;
+    }
+}
+
+// Mixed-precision symmetric eigensolver, same contract as block_jacobi (H in, eigenvalues on
+// its diagonal; eigenvectors as the columns of U; both m x m with leading dimension ld).
+//  1. Jacobi in FP32 on a float copy of H (stored in U's space): rotations on the FP32 pipe,
+//     which has many times the FP64 rate, to an off-diagonal norm near FP32 rounding.
+//  2. Its eigenvector matrix G is orthonormalised in FP64 by two Newton-Schulz steps
+//     G <- G (3 I - G^T G) / 2 (quadratic: FP32-level 1e-6 -> 1e-12 -> rounding).
+//  3. H' = G^T H G in FP64 is diagonal up to FP32-level terms; FP64 Jacobi sweeps finish it
+//     (quadratic convergence: one or two sweeps) and U = G U'.
+// G and T are m x m FP64 scratch (leading dimension m) outside H and U.  Returns
+// 100 * FP32 sweeps + FP64 sweeps.
+__device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, double* T, double* rot,
+                               int* pairs, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
+    float* U32 = H32 + (size_t)m * ld;
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        H32[i * ld + j] = (float)H[i * ld + j];
+    }
+    const int s32 = jacobi_sym_t<float>(H32, U32, m, ld, reinterpret_cast<float*>(rot), pairs, red, 1e-10,
+                                        1e-9f, 1e-30f);
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        G[t] = (double)U32[i * ld + j];
+    }
+    __syncthreads();
+    for (int ns = 0; ns < 2; ++ns) {
+        block_gemm(T, m, G, m, true, G, m, m);  // T = G^T G
+        __syncthreads();
+        for (int t = tid; t < m * m; t += nt) T[t] = (t / m == t % m ? 1.5 : 0.0) - 0.5 * T[t];
+        __syncthreads();
+        block_gemm(U, ld, G, m, false, T, m, m);  // U = G (3 I - G^T G) / 2
+        __syncthreads();
+        for (int t = tid; t < m * m; t += nt) G[t] = U[(t / m) * ld + t % m];
+        __syncthreads();
+    }
+    block_gemm(T, m, H, ld, false, G, m, m);  // T = H G
+    __syncthreads();
+    // H' = G^T T, upper triangle mirrored (t = j (j + 1) / 2 + i, i <= j)
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], T[k * m + j], acc);
+        H[i * ld + j] = acc;
+        H[j * ld + i] = acc;
+    }
+    __syncthreads();
+    // off-diagonal <= 1e-13 of the total (Frobenius): the eigenvalues are then exact to
+    // rounding (their error is second order) and the eigenvectors to about 1e-13 / gap
+    const int s64 = block_jacobi_sym(H, U, m, ld, rot, pairs, red, 1e-26);
+    block_gemm(T, m, G, m, false, U, ld, m);  // eigenvectors G U'
+    __syncthreads();
+    for (int t = tid; t < m * m; t += nt) U[(t / m) * ld + t % m] = T[t];
+    __syncthreads();
+    return 100 * s32 + s64;
 }
 
 // Symmetric eigendecomposition by Householder reduction to tridiagonal form followed by the
@@ -462,6 +555,8 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     double* X = a.work + 3 * (size_t)m * m;       // triangular-solve scratch
     int* rank = (int*)(a.work + 4 * (size_t)m * m);
 
+    __shared__ long long clk[6];  // phase clocks of thread 0 (PPRPA_RR_PROF)
+    if (tid == 0) clk[0] = clock64();
     if (tid == 0) a.info[0] = DEV_NOTPD;
     // scale for the pivot test
     double sc = 0.0;
@@ -499,6 +594,7 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         if (tid == 0) { a.info[0] = DEV_NOTPD; a.info[1] = mu; }
         return;
     }
+    if (tid == 0) clk[1] = clock64();
     // X = Lc^-1 S (column per thread), then H = Lc^-1 X^T
     for (int col = tid; col < m; col += nt) {
         for (int i = 0; i < m; ++i) {
@@ -524,10 +620,16 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
             H[j * lh + i] = v;
         }
     }
-    const int sweeps = a.eig == 0   ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
-                       : a.eig == 1 ? block_jacobi(H, U, m, lh, rot, pairs, red)
+    __syncthreads();
+    if (tid == 0) clk[2] = clock64();
+    const int sweeps = (a.eig == 3 && in_smem)
+                           ? block_mixed_eig(H, U, m, lh, a.work + (size_t)m * m, a.work + 2 * (size_t)m * m, rot,
+                                             pairs, red)
+                       : (a.eig == 0 || a.eig == 3) ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
+                       : a.eig == 1                 ? block_jacobi(H, U, m, lh, rot, pairs, red)
                                     : block_tridiag_eig(H, U, m, lh,
                                                         6 * m <= 2 * 512 + 2 ? rot : a.work + 4 * (size_t)m * m + m);
+    if (tid == 0) clk[3] = clock64();
     // rank the positive kappas (descending) -> targets
     if (tid == 0) npos_sh = 0;
     __syncthreads();
@@ -547,6 +649,7 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     __syncthreads();
     const int npos = npos_sh;
     const int nk = min(a.nkeep, npos);
+    if (tid == 0) clk[4] = clock64();
     // Ritz coefficients c_j = Lc^-T u_j / sqrt(kappa_j) for the kept roots
     for (int i = tid; i < m; i += nt) {
         const int r = rank[i];
@@ -576,14 +679,20 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         a.info[3] = kmax > 0.0 ? mu + 1.0 / kmax : 1e300;
         a.info[4] = kmin < 0.0 ? mu + 1.0 / kmin : -1e300;
         a.info[5] = sweeps;
+        if (a.prof) {
+            clk[5] = clock64();
+            printf("[rr] m %d sweeps %d cycles: factor %lld solves %lld eig %lld rank %lld ritz %lld\n", m, sweeps,
+                   clk[1] - clk[0], clk[2] - clk[1], clk[3] - clk[2], clk[4] - clk[3], clk[5] - clk[4]);
+        }
     }
 }
 
-// Eigensolver of the one-CTA kernels: 0 Jacobi with the fused symmetric update (default),
-// 1 Jacobi with separate row and column passes, 2 Householder + implicit QR (PPRPA_EIG).
+// Eigensolver of the one-CTA kernels (PPRPA_EIG): 3 mixed FP32 / FP64 Jacobi where H and U fit
+// in shared memory, else 0 (default); 0 FP64 Jacobi with the fused symmetric update; 1 FP64
+// Jacobi with separate row and column passes; 2 Householder + implicit QR.
 static int eig_method() {
     const char* v = getenv("PPRPA_EIG");
-    return v ? atoi(v) : 0;
+    return v ? atoi(v) : 3;
 }
 
 // Odd leading dimension of the shared-memory matrices unless PPRPA_RR_PAD=0.
@@ -597,6 +706,8 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
     a.eig = eig_method();
     if (a.m <= 0 || a.m > 1024) return set_error(PPRPA_ERR_ARG, "rayleigh_ritz: size must be 1..1024");
     a.pad = rr_pad();
+    const char* pv = getenv("PPRPA_RR_PROF");
+    a.prof = pv ? atoi(pv) : 0;
     const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
     static bool attr_set = false;
     if (!attr_set) {
@@ -673,7 +784,7 @@ __global__ void __launch_bounds__(1024, 1) sym_eig_kernel(double* H, double* U, 
                                                           double* work, int* iwork, int eig) {
     const int b = blockIdx.x;
     double* w = work + (int64_t)b * 8192;
-    if (eig == 0) block_jacobi_sym(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
+    if (eig == 0 || eig == 3) block_jacobi_sym(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
     else if (eig == 1) block_jacobi(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
     else block_tridiag_eig(H + b * stride, U + b * stride, m, m, w);
 }
