@@ -155,7 +155,7 @@ __device__ inline float jrsqrt(float x) { return rsqrtf(x); }
 // with |h_pq| <= skip * sqrt|h_pp h_qq| are skipped.
 template <typename T>
 __device__ int jacobi_sym_t(T* H, T* U, int m, int ld, T* rot, int* pairs, double* red, double tol2,
-                            T skip, T tiny) {
+                            T skip, T tiny, int max_sweeps = 40, bool stop_on_stall = false) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
@@ -165,7 +165,8 @@ __device__ int jacobi_sym_t(T* H, T* U, int m, int ld, T* rot, int* pairs, doubl
     const int half = me / 2;
     const int nblk = half * (half + 1) / 2;
     int sweep = 0;
-    for (; sweep < 40; ++sweep) {
+    double prev_off = 0.0;
+    for (; sweep < max_sweeps; ++sweep) {
         __syncthreads();
         T off = 0, tot = 0;
         for (int t = tid; t < m * m; t += nt) {
@@ -189,6 +190,9 @@ __device__ int jacobi_sym_t(T* H, T* U, int m, int ld, T* rot, int* pairs, doubl
         }
         __syncthreads();
         if (!(red[64] > tol2 * red[65]) || me < 2) break;
+        // rounding floor of a low precision: quadratic convergence has stopped
+        if (stop_on_stall && sweep >= 2 && red[64] > 0.25 * prev_off) break;
+        prev_off = red[64];
         for (int s = 0; s < me - 1; ++s) {
             for (int i = tid; i < half; i += nt) {
                 int p, q;
@@ -299,7 +303,7 @@ __device__ void block_gemm(double* C, int ldc, const double* A, int lda, bool tr
 // G and T are m x m FP64 scratch (leading dimension m) outside H and U.  Returns
 // 100 * FP32 sweeps + FP64 sweeps.
 __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, double* T, double* rot,
-                               int* pairs, double* red) {
+                               int* pairs, double* red, double tol32) {
     const int tid = threadIdx.x, nt = blockDim.x;
     float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
     float* U32 = H32 + (size_t)m * ld;
@@ -307,8 +311,8 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
         const int i = t / m, j = t % m;
         H32[i * ld + j] = (float)H[i * ld + j];
     }
-    const int s32 = jacobi_sym_t<float>(H32, U32, m, ld, reinterpret_cast<float*>(rot), pairs, red, 1e-10,
-                                        1e-9f, 1e-30f);
+    const int s32 = jacobi_sym_t<float>(H32, U32, m, ld, reinterpret_cast<float*>(rot), pairs, red, tol32,
+                                        1e-9f, 1e-30f, 16, true);
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
         G[t] = (double)U32[i * ld + j];
@@ -595,20 +599,41 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         return;
     }
     if (tid == 0) clk[1] = clock64();
-    // X = Lc^-1 S (column per thread), then H = Lc^-1 X^T
+    // reciprocal pivots (after the eigensolver's scratch at 4 m^2 + m .. 4 m^2 + 7 m)
+    double* rdiag = a.work + 4 * (size_t)m * m + 7 * (size_t)m;
+    for (int i = tid; i < m; i += nt) rdiag[i] = 1.0 / Kc[i * lw + i];
+    __syncthreads();
+    // X = Lc^-1 S (column per thread), then H = Lc^-1 X^T.  Four partial sums per row keep
+    // four independent FMA chains in flight (the FP64 latency would otherwise bound a row).
     for (int col = tid; col < m; col += nt) {
         for (int i = 0; i < m; ++i) {
-            double v = (i <= col) ? a.S[i * ld + col] : a.S[col * ld + i];
-            for (int l = 0; l < i; ++l) v -= Kc[i * lw + l] * X[l * lw + col];
-            X[i * lw + col] = v / Kc[i * lw + i];
+            double v0 = (i <= col) ? a.S[i * ld + col] : a.S[col * ld + i], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            const double* kr = Kc + (size_t)i * lw;
+            int l = 0;
+            for (; l + 4 <= i; l += 4) {
+                v0 = fma(-kr[l], X[l * lw + col], v0);
+                v1 = fma(-kr[l + 1], X[(l + 1) * lw + col], v1);
+                v2 = fma(-kr[l + 2], X[(l + 2) * lw + col], v2);
+                v3 = fma(-kr[l + 3], X[(l + 3) * lw + col], v3);
+            }
+            for (; l < i; ++l) v0 = fma(-kr[l], X[l * lw + col], v0);
+            X[i * lw + col] = ((v0 + v1) + (v2 + v3)) * rdiag[i];
         }
     }
     __syncthreads();
     for (int col = tid; col < m; col += nt) {
         for (int i = 0; i < m; ++i) {
-            double v = X[col * lw + i];
-            for (int l = 0; l < i; ++l) v -= Kc[i * lw + l] * H[l * lh + col];
-            H[i * lh + col] = v / Kc[i * lw + i];
+            double v0 = X[col * lw + i], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            const double* kr = Kc + (size_t)i * lw;
+            int l = 0;
+            for (; l + 4 <= i; l += 4) {
+                v0 = fma(-kr[l], H[l * lh + col], v0);
+                v1 = fma(-kr[l + 1], H[(l + 1) * lh + col], v1);
+                v2 = fma(-kr[l + 2], H[(l + 2) * lh + col], v2);
+                v3 = fma(-kr[l + 3], H[(l + 3) * lh + col], v3);
+            }
+            for (; l < i; ++l) v0 = fma(-kr[l], H[l * lh + col], v0);
+            H[i * lh + col] = ((v0 + v1) + (v2 + v3)) * rdiag[i];
         }
     }
     __syncthreads();
@@ -624,7 +649,7 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     if (tid == 0) clk[2] = clock64();
     const int sweeps = (a.eig == 3 && in_smem)
                            ? block_mixed_eig(H, U, m, lh, a.work + (size_t)m * m, a.work + 2 * (size_t)m * m, rot,
-                                             pairs, red)
+                                             pairs, red, a.tol32)
                        : (a.eig == 0 || a.eig == 3) ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
                        : a.eig == 1                 ? block_jacobi(H, U, m, lh, rot, pairs, red)
                                     : block_tridiag_eig(H, U, m, lh,
@@ -657,9 +682,16 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         const double kap = H[i * lh + i];
         double* c = a.coef + (size_t)r * m;
         for (int row = m - 1; row >= 0; --row) {
-            double v = U[row * lh + i];
-            for (int l = row + 1; l < m; ++l) v -= Kc[l * lw + row] * c[l];
-            c[row] = v / Kc[row * lw + row];
+            double v0 = U[row * lh + i], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            int l = row + 1;
+            for (; l + 4 <= m; l += 4) {
+                v0 = fma(-Kc[l * lw + row], c[l], v0);
+                v1 = fma(-Kc[(l + 1) * lw + row], c[l + 1], v1);
+                v2 = fma(-Kc[(l + 2) * lw + row], c[l + 2], v2);
+                v3 = fma(-Kc[(l + 3) * lw + row], c[l + 3], v3);
+            }
+            for (; l < m; ++l) v0 = fma(-Kc[l * lw + row], c[l], v0);
+            c[row] = ((v0 + v1) + (v2 + v3)) * rdiag[row];
         }
         const double f = 1.0 / sqrt(kap);
         for (int row = 0; row < m; ++row) c[row] *= f;
@@ -706,6 +738,8 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
     a.eig = eig_method();
     if (a.m <= 0 || a.m > 1024) return set_error(PPRPA_ERR_ARG, "rayleigh_ritz: size must be 1..1024");
     a.pad = rr_pad();
+    const char* tv = getenv("PPRPA_RR_TOL32");
+    a.tol32 = tv ? atof(tv) : 1e-10;
     const char* pv = getenv("PPRPA_RR_PROF");
     a.prof = pv ? atoi(pv) : 0;
     const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
@@ -722,56 +756,73 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
 
 // ---------------------------------------------------------------------------
 // Block orthonormalisation helper (Cholesky QR with dropping).
-__global__ void cholqr_small_kernel(const double* __restrict__ Gm, int k, double tol,
-                                    double* __restrict__ T, int* __restrict__ keep,
-                                    double* __restrict__ work) {
-    // single thread: k is small (<= 64)
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(256) cholqr_small_kernel(const double* __restrict__ Gm, int k, double tol,
+                                                           double* __restrict__ T, int* __restrict__ keep,
+                                                           double* __restrict__ work) {
+    // One CTA; every serial chain is O(k): the right-looking Cholesky takes k steps of parallel
+    // column scaling and trailing updates, the inverse one column per thread.
+    const int tid = threadIdx.x, nt = blockDim.x;
     double* Lc = work;            // k x k
     double* s = work + k * k;     // k
-    for (int i = 0; i < k; ++i) {
+    __shared__ int drop_sh;
+    for (int i = tid; i < k; i += nt) {
         const double d = Gm[i * k + i];
         s[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
         keep[i] = d > 0.0 ? 1 : 0;
     }
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) Lc[i * k + j] = (j <= i) ? Gm[i * k + j] * s[i] * s[j] : 0.0;
+    __syncthreads();
+    for (int t = tid; t < k * k; t += nt) {
+        const int i = t / k, j = t % k;
+        Lc[t] = (j <= i) ? Gm[t] * s[i] * s[j] : 0.0;
+    }
+    __syncthreads();
     for (int j = 0; j < k; ++j) {
-        double d = Lc[j * k + j];
-        for (int l = 0; l < j; ++l) d -= Lc[j * k + l] * Lc[j * k + l];
-        if (!keep[j] || !(d > tol)) {
-            keep[j] = 0;
-            for (int l = 0; l < j; ++l) Lc[j * k + l] = 0.0;
-            Lc[j * k + j] = 1.0;
-            for (int i = j + 1; i < k; ++i) Lc[i * k + j] = 0.0;
+        if (tid == 0) {
+            const double d = Lc[j * k + j];  // the trailing updates of columns < j are applied
+            drop_sh = (!keep[j] || !(d > tol)) ? 1 : 0;
+            if (drop_sh) keep[j] = 0;
+            else Lc[j * k + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (drop_sh) {  // dependent direction: row and column j become those of the identity
+            for (int l = tid; l < k; l += nt) {
+                if (l < j) Lc[j * k + l] = 0.0;
+                if (l > j) Lc[l * k + j] = 0.0;
+            }
+            if (tid == 0) Lc[j * k + j] = 1.0;
+            __syncthreads();
             continue;
         }
-        const double piv = sqrt(d);
-        Lc[j * k + j] = piv;
-        for (int i = j + 1; i < k; ++i) {
-            double v = Lc[i * k + j];
-            for (int l = 0; l < j; ++l) v -= Lc[i * k + l] * Lc[j * k + l];
-            Lc[i * k + j] = v / piv;
+        const double piv = Lc[j * k + j];
+        for (int i = j + 1 + tid; i < k; i += nt) Lc[i * k + j] /= piv;
+        __syncthreads();
+        const int r = k - j - 1;
+        for (int t = tid; t < r * r; t += nt) {
+            const int i = j + 1 + t / r, l = j + 1 + t % r;
+            if (l <= i) Lc[i * k + l] -= Lc[i * k + j] * Lc[l * k + j];
         }
+        __syncthreads();
     }
-    // T = Lc^-1 diag(s); dropped rows zero
-    for (int col = 0; col < k; ++col) {
+    // T = Lc^-1 diag(s), one column per thread; dropped rows zero
+    for (int col = tid; col < k; col += nt) {
         for (int i = 0; i < k; ++i) {
             double v = (i == col) ? 1.0 : 0.0;
-            for (int l = 0; l < i; ++l) v -= Lc[i * k + l] * T[l * k + col];
-            T[i * k + col] = v / Lc[i * k + i];
+            for (int l = col; l < i; ++l) v -= Lc[i * k + l] * T[l * k + col];  // T[l][col] = 0 for l < col
+            T[i * k + col] = (i < col) ? 0.0 : v / Lc[i * k + i];
         }
     }
-    for (int i = 0; i < k; ++i)
-        for (int col = 0; col < k; ++col)
-            T[i * k + col] = keep[i] ? T[i * k + col] * s[col] : 0.0;
+    __syncthreads();
+    for (int t = tid; t < k * k; t += nt) {
+        const int i = t / k, col = t % k;
+        T[t] = keep[i] ? T[t] * s[col] : 0.0;
+    }
 }
 
 int launch_cholqr_small(const double* Gm, int k, double tol, double* T, int* keep, double* work,
                         cudaStream_t st) {
     if (k <= 0) return PPRPA_OK;
     if (k > 256) return set_error(PPRPA_ERR_ARG, "cholqr_small: block too large");
-    cholqr_small_kernel<<<1, 32, 0, st>>>(Gm, k, tol, T, keep, work);
+    cholqr_small_kernel<<<1, 256, 0, st>>>(Gm, k, tol, T, keep, work);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }

@@ -107,6 +107,7 @@ struct RRArgs {
     int eig = 0;             // set by the launcher: 0 Jacobi (fused update), 1 Jacobi, 2 Householder + QR
     int pad = 1;             // set by the launcher: odd leading dimension of H and U in shared memory
     int prof = 0;            // set by the launcher: print the phase clocks of each call (PPRPA_RR_PROF)
+    double tol32 = 1e-10;    // set by the launcher: FP32 stage stops at off^2 <= tol32 total^2
     double* omega = nullptr;   // nkeep
     double* coef = nullptr;    // nkeep x m (row j = coefficients of Ritz vector j)
     double* info = nullptr;    // [0]=status, [1]=mu used, [2]=npos, [3]=omega_min_pp,
