@@ -173,9 +173,12 @@ def small_solve(pp, torch, stream):
         for name, prec, tol in (("fp64", pp.PREC_FP64, 1e-7), ("mixed", pp.PREC_BF16, 1e-5),
                                 ("mixed_fp8", pp.PREC_FP8, 1e-5)):
             c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
+            torch.cuda.nvtx.range_push("solve_" + name)
             t0 = time.perf_counter()
             r = c.solve(mult=1, nroots=10, precision=prec, conv_tol=tol)
-            out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "omega": r["omega"],
+            dt = (time.perf_counter() - t0) * 1e3
+            torch.cuda.nvtx.range_pop()
+            out[name] = {"ms": dt, "omega": r["omega"],
                          "iters": r["info"]["iters"], "converged": r["info"]["converged"]}
     d = float(np.abs(out["mixed"]["omega"] - out["fp64"]["omega"]).max())
     d8 = float(np.abs(out["mixed_fp8"]["omega"] - out["fp64"]["omega"]).max())
@@ -260,6 +263,9 @@ def main():
                     help="form of the timed sigma: BF16 both stages, or E4M3 first stage")
     ap.add_argument("--batch-molecules", type=int, default=0,
                     help="also time the batched multi-molecule sigma over this many molecules")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time only the small Davidson solves (FP64, mixed BF16, mixed FP8) and print them; "
+                         "each timed solve sits in an NVTX range solve_<form>")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -285,6 +291,9 @@ def main():
     # the library runs on a stream of ours, so events on it bracket its kernels
     lib_stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(lib_stream)
+    if args.only_solve:
+        print(json.dumps({"solve_small": small_solve(pp, torch, lib_stream)}))
+        return
     c, ao2mo_ms, head = setup_context(pp, torch, spec, device, lib_stream)
     n, naux, nvv, noo = c.dims(1)
     N = nvv + noo

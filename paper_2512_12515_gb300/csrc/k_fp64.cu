@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
 
     __shared__ double As[DG_BK][DG_BM + 1];
     __shared__ double Bs[DG_BK][DG_BN + 1];
+    const int imax = min(4, (g.M - m0 + 15) / 16), jmax = min(4, (g.N - n0 + 15) / 16);
     double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -72,10 +73,17 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
                 for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+                // 16-row / 16-column groups wholly outside C are skipped (uniform over the
+                // CTA): an FP64 FMA is expensive here, and small outputs fill a fraction of a tile
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= imax) break;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+                    for (int j = 0; j < 4; ++j) {
+                        if (j >= jmax) break;
+                        acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+                    }
+                }
             }
             __syncthreads();
         }
@@ -105,7 +113,7 @@ int auto_splitk(int M, int N, int K, int batches) {
     const int64_t target = 4 * 152;
     if (tiles >= target) return 1;
     int64_t s = ceil_div(target, tiles);
-    const int64_t kmax = ceil_div(K, 4 * DG_BK);  // keep >= 4 k-slabs per split
+    const int64_t kmax = ceil_div(K, DG_BK);  // at least one k-slab per split
     if (s > kmax) s = kmax;
     if (s > 1024) s = 1024;
     return s < 1 ? 1 : (int)s;
@@ -132,11 +140,17 @@ int dgemm(const Dgemm& gin, cudaStream_t st) {
     // reduction over batches (sum_r A_r B_r) spreads that reduction over CTAs, which then add
     // their partial sums atomically into C after C has been scaled by beta
     g.rsplit = 1;
+    bool split = false;
+    const int64_t tiles = ceil_div(g.N, DG_BN) * ceil_div(g.M, DG_BM) * (int64_t)g.nb1 * g.nb2;
     if (g.nr > 1 && g.splitk == 1) {
-        const int64_t tiles = ceil_div(g.N, DG_BN) * ceil_div(g.M, DG_BM) * (int64_t)g.nb1 * g.nb2;
         if (tiles < 2 * 152) g.rsplit = (int)std::min<int64_t>(g.nr, ceil_div(2 * 152, tiles));
+        split = g.rsplit > 1;
+    } else if (g.nr == 1 && g.splitk == 1 && tiles < 152 && g.K >= 4 * DG_BK) {
+        // the same for a single long product: its K range is split instead
+        g.splitk = auto_splitk(g.M, g.N, g.K, g.nb1 * g.nb2);
+        split = g.splitk > 1;
     }
-    if (g.rsplit > 1) {
+    if (split) {
         const int64_t total = (int64_t)g.M * g.N * g.nb1 * g.nb2;
         dgemm_scale_c_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 8), 256, 0, st>>>(g);
         PP_CHECK_LAUNCH();
