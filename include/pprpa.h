@@ -80,7 +80,8 @@ typedef struct pprpa_options {
     int nroots;        /* roots wanted: 1..nvv lowest N+2 roots (pp), 1..noo highest N-2 roots (hh) */
     double conv_tol;   /* residual 2-norm ||M z - omega W z|| for converged roots */
     int max_iter;      /* Davidson iteration cap */
-    int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic (112) */
+    int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic: 112, with restarts at 72
+                          below 8192 pairs while the shifted pencil is definite */
     int want_ec;       /* FULL only: also return the correlation energy */
 } pprpa_options;
 

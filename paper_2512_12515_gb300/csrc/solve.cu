@@ -265,6 +265,10 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     if (m_max < nguess + 1 && N > nguess) m_max = std::min(N, nguess + 1);
     int nkeep = std::max(nguess, std::max(4 * nroots, 40));
     nkeep = std::min(nkeep, std::max(1, m_max - std::max(nroots, 8)));
+    // automatic cap of a small problem (N < 8192 pairs) on the definite (shift-Cholesky) path:
+    // restart at 72, since there the one-CTA Rayleigh-Ritz step, O(m^3) FP64 on one SM,
+    // outweighs the few extra sigma products; the general path keeps the full cap
+    const int m_soft = (o->max_subspace > 0 || N >= 8192) ? m_max : std::min(m_max, std::max(72, nkeep + nroots));
     const int max_new = nroots;
     Timer t_all(st), t_sig(st);
     t_all.start();
@@ -491,7 +495,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         const int kn = (int)todo.size();
         PP_CUDA(cudaMemcpyAsync(sel, todo.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, st));
         PP_TRY(launch_correction(R, D, om, sel, kn, N, nvv, Dn, st, ws));
-        if (m + kn > m_max) {
+        if (m + kn > (general ? m_max : m_soft)) {
             PP_TRY(collapse(nk_avail, m, false));
             m = nk_avail;
         }
