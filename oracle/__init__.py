@@ -19,6 +19,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   second-order (MP2-type) limit.
 * grad_omega: pinned by central finite differences and by the trace rule of
   the two-electron density matrix.
+* grad_omega_ab (alpha-beta subspace): pinned by central finite differences of its
+  roots (addition and removal) and by the uniform-shift rule (each spin's energy
+  gradient sums to 1).
 * grad_ao: pinned by central finite differences of a root through the whole
   chain (AO integrals or MO coefficients -> L -> M -> omega).
 * ri_sigma / davidson: pinned by the explicit matrix (sigma) and by full
@@ -53,6 +56,7 @@ from .pprpa_ref import (  # noqa: F401
     solve_full_shifted,
     correlation_energy,
     grad_omega,
+    grad_omega_ab,
     two_e_density_diag,
     two_e_density,
     nto,

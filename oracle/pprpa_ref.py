@@ -368,6 +368,46 @@ def grad_omega(eps_act, nocc_act, L_act, mult, z):
     return d_eps, d_L
 
 
+def grad_omega_ab(eps_a, nocc_a, L_a, eps_b, nocc_b, L_b, z):
+    """Hellmann-Feynman gradient of one root of the (alpha alpha; beta beta) subspace.
+
+    Sec. Analytic Gradient applied to the matrix of ``build_matrix_ab``: d omega =
+    s z^T (dM) z with s = z^T W z = +-1.  dM is formed element by element from that
+    matrix's definitions: the diagonal carries +(eps_a + eps_b) on virtual pairs and
+    -(eps_i + eps_j) on occupied pairs, and every element carries
+    (pr|qs) = sum_P L^{alpha P}_pr L^{beta P}_qs, whose chain rule gives the derivative
+    with respect to every entry of L^alpha and L^beta (entries treated as independent).
+
+    Returns ``(d_eps_a (na,), d_eps_b (nb,), d_La (naux, na, na), d_Lb (naux, nb, nb))``.
+    """
+    ea = np.asarray(eps_a, dtype=np.float64)
+    eb = np.asarray(eps_b, dtype=np.float64)
+    La = np.asarray(L_a, dtype=np.float64)
+    Lb = np.asarray(L_b, dtype=np.float64)
+    na, nb = ea.shape[0], eb.shape[0]
+    vv = [(a, b) for a in range(nocc_a, na) for b in range(nocc_b, nb)]
+    oo = [(i, j) for i in range(nocc_a) for j in range(nocc_b)]
+    pairs = vv + oo
+    nvv = len(vv)
+    w = np.concatenate([np.ones(nvv), -np.ones(len(oo))])
+    z = np.asarray(z, dtype=np.float64)
+    s = float(np.sign(z @ (w * z)))
+    gamma = s * np.outer(z, z)  # d omega / d M_IJ
+    d_ea = np.zeros(na)
+    d_eb = np.zeros(nb)
+    for I, (p, q) in enumerate(pairs):
+        d_ea[p] += w[I] * gamma[I, I]
+        d_eb[q] += w[I] * gamma[I, I]
+    # M_IJ = V[p_I, q_I, p_J, q_J] + diagonal, V[p, q, r, t] = sum_P La[P, p, r] Lb[P, q, t]
+    P1 = np.array([x[0] for x in pairs])
+    P2 = np.array([x[1] for x in pairs])
+    g4 = np.zeros((na, nb, na, nb))  # d omega / d V[p, q, r, t]
+    np.add.at(g4, (P1[:, None], P2[:, None], P1[None, :], P2[None, :]), gamma)
+    d_La = np.einsum("pqrt,Pqt->Ppr", g4, Lb, optimize=True)
+    d_Lb = np.einsum("pqrt,Ppr->Pqt", g4, La, optimize=True)
+    return d_ea, d_eb, d_La, d_Lb
+
+
 def _triangular(vec, n, mult):
     """Pair vector -> n x n upper-triangular matrix (Sec. Natural Transition
     Orbital: X and Y viewed as triangular matrices)."""

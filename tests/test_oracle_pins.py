@@ -191,6 +191,80 @@ def test_unrestricted_three_subspaces_equal_spin_orbital_matrix():
         assert np.allclose(np.sort(so["omega_" + key]), ref, atol=1e-10)
 
 
+def unrestricted_small(seed=83):
+    """Different alpha and beta orbitals, energies and occupied counts (2 alpha, 1 beta)."""
+    spec = synth.SystemSpec("t", 8, 3, 6, 3, 5, seed)
+    s = synth.make_system(spec)
+    rng = np.random.default_rng(seed + 1)
+    Q, _ = np.linalg.qr(rng.standard_normal((spec.nmo, spec.nmo)))
+    Cb = s["C"] @ (np.eye(spec.nmo) + 0.2 * (Q - np.eye(spec.nmo)))
+    Cb, _ = np.linalg.qr(Cb)
+    oa, va, ob, vb = 2, 4, 1, 4
+    orb_a = np.arange(3 - oa, 3 + va)
+    orb_b = np.arange(2 - ob, 2 + vb)
+    eb_full = np.sort(s["eps"] + 0.04 * rng.standard_normal(spec.nmo))
+    La = oracle.ao_to_mo(s["ao3c"], s["C"], orb_a)
+    Lb = oracle.ao_to_mo(s["ao3c"], Cb, orb_b)
+    return s["eps"][orb_a], oa, La, eb_full[orb_b], ob, Lb
+
+
+def test_alpha_beta_gradient_matches_finite_differences():
+    """grad_omega_ab: d omega / d eps (alpha, beta) and d omega / d L (alpha, beta) against
+    central differences (h = 1e-4) of roots of the alpha-beta matrix, addition and removal."""
+    ea, oa, La, eb, ob, Lb = unrestricted_small()
+    M, nvv, noo = oracle.build_matrix_ab(ea, oa, La, eb, ob, Lb)
+    sol = oracle.solve_full(M, nvv, noo)
+    assert sol["max_imag"] == 0.0
+    h = 1e-4
+    rng = np.random.default_rng(5)
+    for key, r in (("pp", 0), ("pp", 3), ("hh", -1)):
+        z = sol["z_" + key][:, r]
+        dea, deb, dLa, dLb = oracle.grad_omega_ab(ea, oa, La, eb, ob, Lb, z)
+
+        def root(xa, Xa, xb, Xb):
+            sx = oracle.solve_full(*oracle.build_matrix_ab(xa, oa, Xa, xb, ob, Xb))
+            return sx["omega_" + key][r]
+
+        for p in (0, 2, 4):
+            for side in ("a", "b"):
+                e = (ea if side == "a" else eb).copy()
+                ep, em = e.copy(), e.copy()
+                ep[p] += h
+                em[p] -= h
+                if side == "a":
+                    fd = (root(ep, La, eb, Lb) - root(em, La, eb, Lb)) / (2 * h)
+                    an = dea[p]
+                else:
+                    fd = (root(ea, La, ep, Lb) - root(ea, La, em, Lb)) / (2 * h)
+                    an = deb[p]
+                assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+        for _ in range(2):
+            for side in ("a", "b"):
+                X = La if side == "a" else Lb
+                D = rng.standard_normal(X.shape)
+                D = D + D.transpose(0, 2, 1)
+                D /= np.linalg.norm(D)
+                if side == "a":
+                    fd = (root(ea, La + h * D, eb, Lb) - root(ea, La - h * D, eb, Lb)) / (2 * h)
+                    an = float(np.sum(dLa * D))
+                else:
+                    fd = (root(ea, La, eb, Lb + h * D) - root(ea, La, eb, Lb - h * D)) / (2 * h)
+                    an = float(np.sum(dLb * D))
+                assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+
+
+def test_alpha_beta_gradient_uniform_shift_rule():
+    """Shifting every alpha (or every beta) orbital energy by d adds d W to M, which moves
+    every root by d: the alpha and the beta energy gradients of any root each sum to 1."""
+    ea, oa, La, eb, ob, Lb = unrestricted_small(85)
+    M, nvv, noo = oracle.build_matrix_ab(ea, oa, La, eb, ob, Lb)
+    sol = oracle.solve_full(M, nvv, noo)
+    for key in ("pp", "hh"):
+        for r in range(sol["z_" + key].shape[1]):
+            dea, deb, _, _ = oracle.grad_omega_ab(ea, oa, La, eb, ob, Lb, sol["z_" + key][:, r])
+            assert abs(dea.sum() - 1.0) < 1e-10 and abs(deb.sum() - 1.0) < 1e-10
+
+
 @pytest.mark.parametrize("nv", [3, 5])
 def test_two_electrons_are_exact(nv):
     """No occupied orbitals: ppRPA roots equal the two-electron determinant CI."""
