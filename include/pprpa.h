@@ -157,10 +157,25 @@ int pprpa_set_mo(pprpa_ctx* ctx, int naux, const double* L, int where);
  * B_{ab,kl} = (ak|bl), C_{ij,kl} = -d d (eps_i + eps_j) + (ik|jl) and
  * (pr|qs) = sum_P L^{alpha P}_pr L^{beta P}_qs (no exchange between opposite spins).  The
  * same-spin subspaces are the PPRPA_TRIPLET problem of one spin's orbitals and integrals
- * (a context per spin).  Gradients and analysis of the alpha-beta subspace are not built
- * (PPRPA_ERR_UNSUPPORTED). */
+ * (a context per spin).  Gradients of alpha-beta roots: pprpa_grad_ab; the analysis
+ * outputs (pprpa_analyze) of the alpha-beta subspace are not built (PPRPA_ERR_UNSUPPORTED). */
 int pprpa_set_beta(pprpa_ctx* ctx, int nocc_b, int nvir_b, int naux, const double* eps_b,
                    const double* L_b, int where);
+
+/* pprpa_grad_ab: Hellmann-Feynman gradient (Sec. "Analytic Gradient") of root `root` of the
+ * last pprpa_solve, which must have been of the alpha-beta subspace (mult = PPRPA_AB; either
+ * channel, the sign z^T W z = -1 of a removal root applied).  With Zt the n_alpha x n_beta
+ * matrix of the root's pair vector (X on its virtual block, Y on its occupied block) and
+ * s = z^T W z:
+ *   dLa[P] = d omega / d L^{alpha P} = s Zt L^{beta P} Zt^T      (naux x n_alpha x n_alpha)
+ *   dLb[P] = d omega / d L^{beta P}  = s Zt^T L^{alpha P} Zt     (naux x n_beta x n_beta)
+ *   deps_a[p] = d omega / d eps^alpha_p,  deps_b[q] = d omega / d eps^beta_q
+ * (entries of L treated as independent; n_alpha = nocc_act + nvir_act, n_beta = nocc_b +
+ * nvir_b, occupied first).  Any output may be NULL; all live on the host or all on the
+ * device per `where`.  Errors: PPRPA_ERR_STATE without an alpha-beta solve,
+ * PPRPA_ERR_ARG for a root index out of range. */
+int pprpa_grad_ab(pprpa_ctx* ctx, int root, double* dLa, double* dLb, double* deps_a, double* deps_b,
+                  int where);
 
 /* pprpa_get_L: copy the active-space L^P_pq (naux x n x n, n = nocc_act +
  * nvir_act, hole slots first; with fractional occupations the weighted L~ that the

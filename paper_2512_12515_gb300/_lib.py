@@ -91,6 +91,7 @@ SIGNATURES = {
     "pprpa_grad_ao": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I]),
     "pprpa_analyze": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "pprpa_set_beta": (_I, [_P, _I, _I, _I, _P, _P, _I]),
+    "pprpa_grad_ab": (_I, [_P, _I, _P, _P, _P, _P, _I]),
     "pprpa_strerror": (ctypes.c_char_p, [_I]),
     "pprpa_last_error": (ctypes.c_char_p, []),
     "pprpa_kernel_launches": (ctypes.c_longlong, []),
@@ -236,6 +237,7 @@ class Context:
         if we != wl:
             raise ValueError("eps_b and L_b must both be host or both be device arrays")
         _check(self.lib.pprpa_set_beta(self._h, int(nocc_b), int(nvir_b), int(L_b.shape[0]), pe, pl, wl))
+        self._nb = int(nocc_b) + int(nvir_b)
 
     def set_mo(self, L):
         p, w = _ptr(L)
@@ -383,6 +385,21 @@ class Context:
         _check(self.lib.pprpa_profile(self._h, -1 if enable is None else int(bool(enable)),
                                       out.ctypes.data))
         return out.reshape(4, 3)
+
+    def grad_ab(self, root):
+        """Gradient of alpha-beta root `root` of the last solve (mult = AB): host arrays
+        (dLa [naux][na][na], dLb [naux][nb][nb], deps_a [na], deps_b [nb])."""
+        na, naux, _, _ = self.dims(1)
+        nb = getattr(self, "_nb", 0)
+        if nb == 0:
+            raise PprpaError(-7, "grad_ab: call set_beta first")
+        dLa = np.empty((naux, na, na))
+        dLb = np.empty((naux, nb, nb))
+        dea = np.empty(na)
+        deb = np.empty(nb)
+        _check(self.lib.pprpa_grad_ab(self._h, int(root), _ptr(dLa, True)[0], _ptr(dLb, True)[0],
+                                      _ptr(dea, True)[0], _ptr(deb, True)[0], HOST))
+        return dLa, dLb, dea, deb
 
     def grad(self, root, dL=None, deps=None):
         n, naux, _, _ = self.dims(1)

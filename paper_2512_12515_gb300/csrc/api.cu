@@ -596,7 +596,7 @@ extern "C" {
 
 int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
     if (c && c->last_nroots && c->last_mult == PPRPA_AB)
-        return set_error(PPRPA_ERR_UNSUPPORTED, "gradients of the alpha-beta subspace are not built");
+        return set_error(PPRPA_ERR_UNSUPPORTED, "grad: roots of the alpha-beta subspace take pprpa_grad_ab");
     PP_TRY(check_ctx(c));
     PP_TRY(need_L(c));
     if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");

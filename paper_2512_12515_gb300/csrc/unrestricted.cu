@@ -77,6 +77,18 @@ __global__ void build_ab_kernel(const double* __restrict__ La, int na, const dou
     }
 }
 
+// d omega / d eps of one alpha-beta pair vector z (Sec. Analytic Gradient): pair I = (p, q)
+// adds w_I s z_I^2 to alpha orbital p and to beta orbital q (w = +1 virtual, -1 occupied).
+__global__ void grad_eps_ab_kernel(const double* __restrict__ z, int N, int nvv, const int* __restrict__ pp,
+                                   const int* __restrict__ pq, double s, double* __restrict__ da,
+                                   double* __restrict__ db) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
+        const double v = (I < nvv ? s : -s) * z[I] * z[I];
+        if (da) atomicAdd(&da[pp[I]], v);
+        if (db) atomicAdd(&db[pq[I]], v);
+    }
+}
+
 unsigned grid_for(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 152 * 16)); }
 
 }  // namespace
@@ -189,9 +201,110 @@ int sigma_ab_f64(pprpa_ctx* c, int k, const double* d_z, double* d_sigma) {
     return PPRPA_OK;
 }
 
+// Hellmann-Feynman gradient of one alpha-beta root (Sec. Analytic Gradient): with Zt the
+// na x nb matrix of z and s = z^T W z,
+//   d omega / d L^{alpha P} = s Zt L^{beta P} Zt^T,  d omega / d L^{beta P} = s Zt^T L^{alpha P} Zt,
+// two batched FP64 GEMMs each per chunk of P.
+int grad_ab(pprpa_ctx* c, const double* z, double s, double* dLa, double* dLb, double* dea, double* deb,
+            int where) {
+    PairTable* t;
+    PP_TRY(ensure_pairs_ab(c, &t));
+    const int na = c->n(), nb = c->nb(), naux = c->naux;
+    const int64_t na2 = (int64_t)na * na, nb2 = (int64_t)nb * nb, nab = (int64_t)na * nb;
+    cudaStream_t st = c->stream;
+    const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dea || deb) {
+        double* d;
+        PP_TRY(ws_get(c, "gab_eps", sizeof(double) * (na + nb), (void**)&d));
+        PP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (na + nb), st));
+        if (t->N) {
+            grad_eps_ab_kernel<<<grid_for(t->N), 256, 0, st>>>(z, t->N, t->nvv, t->d_pp, t->d_pq, s, d, d + na);
+            PP_CHECK_LAUNCH();
+        }
+        if (dea) PP_CUDA(cudaMemcpyAsync(dea, d, sizeof(double) * na, kind, st));
+        if (deb) PP_CUDA(cudaMemcpyAsync(deb, d + na, sizeof(double) * nb, kind, st));
+    }
+    if (dLa || dLb) {
+        double *Zt, *T, *out = nullptr;
+        PP_TRY(ws_get(c, "gab_Zt", sizeof(double) * nab, (void**)&Zt));
+        PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * nab, st));
+        if (t->N) {
+            unpack_ab_kernel<<<grid_for(t->N), 256, 0, st>>>(z, 1, t->N, t->d_pp, t->d_pq, na, nb, Zt);
+            PP_CHECK_LAUNCH();
+        }
+        const int64_t per_p = std::max(na2, std::max(nb2, nab));
+        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * per_p)));
+        PP_TRY(ws_get(c, "gab_T", sizeof(double) * nab * pc, (void**)&T));
+        if (where == PPRPA_HOST) PP_TRY(ws_get(c, "gab_out", sizeof(double) * per_p * pc, (void**)&out));
+        for (int P0 = 0; P0 < naux; P0 += pc) {
+            const int np = std::min(pc, naux - P0);
+            if (dLa) {
+                Dgemm g1;  // T^P = L^{beta P} Zt^T (nb x na)
+                g1.M = nb; g1.N = na; g1.K = nb;
+                g1.A = c->d_Lb + (size_t)P0 * nb2; g1.lda = nb; g1.sA1 = nb2;
+                g1.B = Zt; g1.ldb = nb; g1.transB = 1;
+                g1.C = T; g1.ldc = na; g1.sC1 = nab;
+                g1.nb1 = np;
+                PP_TRY(dgemm(g1, st));
+                Dgemm g2;  // d L^{alpha P} = s Zt T^P (na x na)
+                g2.M = na; g2.N = na; g2.K = nb;
+                g2.A = Zt; g2.lda = nb;
+                g2.B = T; g2.ldb = na; g2.sB1 = nab;
+                g2.C = where == PPRPA_DEVICE ? dLa + (size_t)P0 * na2 : out; g2.ldc = na; g2.sC1 = na2;
+                g2.nb1 = np;
+                g2.alpha = s;
+                PP_TRY(dgemm(g2, st));
+                if (where == PPRPA_HOST) {
+                    PP_CUDA(cudaMemcpyAsync(dLa + (size_t)P0 * na2, out, sizeof(double) * na2 * np,
+                                            cudaMemcpyDeviceToHost, st));
+                    PP_CUDA(cudaStreamSynchronize(st));
+                }
+            }
+            if (dLb) {
+                Dgemm g1;  // T^P = L^{alpha P} Zt (na x nb)
+                g1.M = na; g1.N = nb; g1.K = na;
+                g1.A = c->d_L + (size_t)P0 * na2; g1.lda = na; g1.sA1 = na2;
+                g1.B = Zt; g1.ldb = nb;
+                g1.C = T; g1.ldc = nb; g1.sC1 = nab;
+                g1.nb1 = np;
+                PP_TRY(dgemm(g1, st));
+                Dgemm g2;  // d L^{beta P} = s Zt^T T^P (nb x nb)
+                g2.M = nb; g2.N = nb; g2.K = na;
+                g2.A = Zt; g2.lda = nb; g2.transA = 1;
+                g2.B = T; g2.ldb = nb; g2.sB1 = nab;
+                g2.C = where == PPRPA_DEVICE ? dLb + (size_t)P0 * nb2 : out; g2.ldc = nb; g2.sC1 = nb2;
+                g2.nb1 = np;
+                g2.alpha = s;
+                PP_TRY(dgemm(g2, st));
+                if (where == PPRPA_HOST) {
+                    PP_CUDA(cudaMemcpyAsync(dLb + (size_t)P0 * nb2, out, sizeof(double) * nb2 * np,
+                                            cudaMemcpyDeviceToHost, st));
+                    PP_CUDA(cudaStreamSynchronize(st));
+                }
+            }
+        }
+    }
+    PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
 }  // namespace pprpa
 
 using namespace pprpa;
+
+extern "C" int pprpa_grad_ab(pprpa_ctx* c, int root, double* dLa, double* dLb, double* deps_a, double* deps_b,
+                             int where) {
+    if (!c) return set_error(PPRPA_ERR_ARG, "grad_ab: null context");
+    PP_CUDA(cudaSetDevice(c->device));
+    if (where != PPRPA_HOST && where != PPRPA_DEVICE) return set_error(PPRPA_ERR_ARG, "grad_ab: bad `where`");
+    if (!c->have_L || !c->have_Lb) return set_error(PPRPA_ERR_STATE, "grad_ab: set the alpha and beta integrals first");
+    if (c->last_nroots == 0 || !c->d_lastZ || c->last_mult != PPRPA_AB)
+        return set_error(PPRPA_ERR_STATE, "grad_ab: no alpha-beta solve to differentiate");
+    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad_ab: root index out of range");
+    // addition roots have z^T W z = +1, removal roots (hh channel) -1
+    const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
+    return grad_ab(c, c->d_lastZ + (size_t)root * c->last_N, s, dLa, dLb, deps_a, deps_b, where);
+}
 
 extern "C" int pprpa_set_beta(pprpa_ctx* c, int nocc_b, int nvir_b, int naux, const double* eps_b,
                               const double* L_b, int where) {

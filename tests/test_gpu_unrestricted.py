@@ -118,3 +118,27 @@ def test_three_subspace_correlation_energy(pp):
         _, _, nvv_b, _ = cb.dims(3)
         ec += cb.solve(mult=3, nroots=nvv_b, method=pp.METHOD_FULL, want_ec=True)["ec"]
     assert abs(ec - ec_ref) <= 1e-8
+
+
+def test_alpha_beta_gradient(pp):
+    """pprpa_grad_ab of addition and removal roots against oracle.grad_omega_ab (pinned by
+    finite differences and the uniform-shift rule)."""
+    spec, s, La, ea, Lb, eb = unrestricted_system(16, 4, 14, 3, 6, 2, 7, 91)
+    M, nvv, noo = oracle.build_matrix_ab(ea, 3, La, eb, 2, Lb)
+    ref = oracle.solve_full(M, nvv, noo)
+    cases = []
+    with ab_ctx(pp, spec, s, 3, 6, 2, Lb, eb) as c:
+        c.solve(mult=pp.AB, nroots=nvv, method=pp.METHOD_FULL)
+        for r in (0, 3):
+            cases.append((c.grad_ab(r), ref["z_pp"][:, r], ref["omega_pp"], r))
+        c.solve(mult=pp.AB, nroots=noo, method=pp.METHOD_FULL, channel=pp.CHANNEL_HH)
+        cases.append((c.grad_ab(0), ref["z_hh"][:, -1], ref["omega_hh"], len(ref["omega_hh"]) - 1))
+        with pytest.raises(pp.PprpaError):
+            c.grad_ab(noo)
+    for (dLa, dLb, dea, deb), z, omegas, r in cases:
+        gaps = np.abs(np.delete(omegas, r) - omegas[r])
+        assert gaps.min() > 1e-4  # a non-degenerate root: z and its gradient are unique
+        rea, reb, ra, rb = oracle.grad_omega_ab(ea, 3, La, eb, 2, Lb, z)
+        for got, want in ((dLa, ra), (dLb, rb), (dea, rea), (deb, reb)):
+            assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
+        assert abs(dea.sum() - 1.0) <= 1e-10 and abs(deb.sum() - 1.0) <= 1e-10
