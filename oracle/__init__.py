@@ -37,6 +37,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
 * two_e_density, nto: pinned by the trace rule, by the epsilon gradient (the
   diagonal), by reconstructing X and Y from their NTOs and by the identity
   X X^T + X^T X = C^p1 L C^p1^T + C^p2 L C^p2^T between the two definitions.
+* two_e_density_ab, nto_ab (alpha-beta subspace): pinned by each spin's trace rule,
+  by the alpha and beta energy gradients of grad_omega_ab (the diagonals), by
+  reconstructing X and Y from their NTOs and by the weight sum rule.
 * eigenvector phase: fixed by convention (largest-magnitude component
   positive); parity unpinned beyond that convention.
 """
@@ -59,7 +62,9 @@ from .pprpa_ref import (  # noqa: F401
     grad_omega_ab,
     two_e_density_diag,
     two_e_density,
+    two_e_density_ab,
     nto,
+    nto_ab,
     nto_weights,
     diag_of_matrix,
 )

@@ -467,6 +467,58 @@ def nto(z, nocc_act, nvir_act, mult):
     return tuple(out)
 
 
+def _rect_ab(z, nocc_a, nvir_a, nocc_b, nvir_b):
+    """Alpha-beta pair vector -> X (nvir_a x nvir_b) and Y (nocc_a x nocc_b), the pair
+    lists of ``build_matrix_ab`` (row-major) read as rectangles."""
+    z = np.asarray(z, dtype=np.float64)
+    nvv = nvir_a * nvir_b
+    return z[:nvv].reshape(nvir_a, nvir_b), z[nvv:].reshape(nocc_a, nocc_b)
+
+
+def two_e_density_ab(z, nocc_a, nvir_a, nocc_b, nvir_b):
+    """Two-electron density of an alpha-beta root (Sec. Density Matrix with the two orbital
+    slots of a pair resolved by spin): D^alpha has X X^T on its virtual block and -Y Y^T on
+    its occupied block, D^beta has X^T X and -Y^T Y.  Returned as the block-diagonal
+    (na + nb) x (na + nb) matrix diag(D^alpha, D^beta), each spin in active-orbital order
+    (occupied first)."""
+    X, Y = _rect_ab(z, nocc_a, nvir_a, nocc_b, nvir_b)
+    na, nb = nocc_a + nvir_a, nocc_b + nvir_b
+    D = np.zeros((na + nb, na + nb))
+    D[:nocc_a, :nocc_a] = -(Y @ Y.T)
+    D[nocc_a:na, nocc_a:na] = X @ X.T
+    D[na:na + nocc_b, na:na + nocc_b] = -(Y.T @ Y)
+    D[na + nocc_b:, na + nocc_b:] = X.T @ X
+    return D
+
+
+def nto_ab(z, nocc_a, nvir_a, nocc_b, nvir_b):
+    """Natural transition orbitals of an alpha-beta root (Eqs. nto_pp, nto_hh with X and Y
+    the rectangles of the pair vector): X = C^p1 sqrt(lambda^p) C^p2^T with C^p1 over alpha
+    virtuals and C^p2 over beta virtuals (likewise Y).  lam has one entry per alpha orbital
+    of the block (descending, zero beyond the rank); C1 is square (alpha), C2 is
+    (beta x alpha) with zero columns where the weight is zero.  Phase: the largest-magnitude
+    entry of each C1 column is positive.  Returns (lam_p, Cp1, Cp2, lam_h, Ch1, Ch2)."""
+    out = []
+    for T in _rect_ab(z, nocc_a, nvir_a, nocc_b, nvir_b):
+        m1, m2 = T.shape
+        if m1 == 0:
+            out += [np.zeros(0), np.zeros((0, 0)), np.zeros((m2, 0))]
+            continue
+        U, sv, Vt = np.linalg.svd(T, full_matrices=True)
+        lam = np.zeros(m1)
+        lam[: sv.shape[0]] = sv ** 2
+        C2 = np.zeros((m2, m1))
+        r = min(m1, m2)
+        C2[:, :r] = Vt[:r].T
+        C2[:, lam <= 1e-28 * max(lam.max(), 1e-300)] = 0.0
+        for k in range(m1):
+            if U[np.argmax(np.abs(U[:, k])), k] < 0:
+                U[:, k] *= -1
+                C2[:, k] *= -1
+        out += [lam, U, C2]
+    return tuple(out)
+
+
 def nto_weights(z, nocc_act, nvir_act, mult):
     """NTO weights lambda^p, lambda^h: squared singular values of the
     triangular X and Y (Eqs. nto_pp, nto_hh)."""

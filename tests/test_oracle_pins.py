@@ -265,6 +265,32 @@ def test_alpha_beta_gradient_uniform_shift_rule():
             assert abs(dea.sum() - 1.0) < 1e-10 and abs(deb.sum() - 1.0) < 1e-10
 
 
+def test_alpha_beta_density_and_ntos():
+    """two_e_density_ab / nto_ab: each spin's block traces to s = z^T W z, s times the
+    diagonal of D^alpha (D^beta) is the alpha (beta) energy gradient of grad_omega_ab (pinned
+    by finite differences), the NTOs rebuild X and Y, and sum(lam_p) - sum(lam_h) = s."""
+    ea, oa, La, eb, ob, Lb = unrestricted_small(87)
+    va, vb = len(ea) - oa, len(eb) - ob
+    M, nvv, noo = oracle.build_matrix_ab(ea, oa, La, eb, ob, Lb)
+    sol = oracle.solve_full(M, nvv, noo)
+    na = len(ea)
+    for key, r, sgn in (("pp", 0, 1.0), ("pp", 2, 1.0), ("hh", -1, -1.0)):
+        z = sol["z_" + key][:, r]
+        D = oracle.two_e_density_ab(z, oa, va, ob, vb)
+        assert abs(np.trace(D[:na, :na]) - sgn) < 1e-12 and abs(np.trace(D[na:, na:]) - sgn) < 1e-12
+        assert np.abs(D[:na, na:]).max() == 0.0
+        dea, deb, _, _ = oracle.grad_omega_ab(ea, oa, La, eb, ob, Lb, z)
+        assert np.abs(sgn * np.diag(D)[:na] - dea).max() < 1e-13
+        assert np.abs(sgn * np.diag(D)[na:] - deb).max() < 1e-13
+        lp, Cp1, Cp2, lh, Ch1, Ch2 = oracle.nto_ab(z, oa, va, ob, vb)
+        X = z[:nvv].reshape(va, vb)
+        Y = z[nvv:].reshape(oa, ob)
+        assert np.abs(Cp1 @ np.diag(np.sqrt(lp)) @ Cp2.T - X).max() < 1e-12
+        assert np.abs(Ch1 @ np.diag(np.sqrt(lh)) @ Ch2.T - Y).max() < 1e-12
+        assert abs(lp.sum() - lh.sum() - sgn) < 1e-12
+        assert np.all(np.diff(lp) <= 1e-15) and np.all(np.diff(lh) <= 1e-15)
+
+
 @pytest.mark.parametrize("nv", [3, 5])
 def test_two_electrons_are_exact(nv):
     """No occupied orbitals: ppRPA roots equal the two-electron determinant CI."""
