@@ -157,8 +157,8 @@ int pprpa_set_mo(pprpa_ctx* ctx, int naux, const double* L, int where);
  * B_{ab,kl} = (ak|bl), C_{ij,kl} = -d d (eps_i + eps_j) + (ik|jl) and
  * (pr|qs) = sum_P L^{alpha P}_pr L^{beta P}_qs (no exchange between opposite spins).  The
  * same-spin subspaces are the PPRPA_TRIPLET problem of one spin's orbitals and integrals
- * (a context per spin).  Gradients of alpha-beta roots: pprpa_grad_ab; the analysis
- * outputs (pprpa_analyze) of the alpha-beta subspace are not built (PPRPA_ERR_UNSUPPORTED). */
+ * (a context per spin).  Gradients of alpha-beta roots: pprpa_grad_ab; analysis outputs:
+ * pprpa_analyze (spin-resolved density blocks, rectangular NTOs). */
 int pprpa_set_beta(pprpa_ctx* ctx, int nocc_b, int nvir_b, int naux, const double* eps_b,
                    const double* L_b, int where);
 
@@ -286,7 +286,16 @@ int pprpa_grad(pprpa_ctx* ctx, int root, double* dL, double* deps, int where);
  *     (Eq. nto_hh).  sum(lam_p) - sum(lam_h) = +-1.  Each Cp1 / Ch1 column has its
  *     largest-magnitude entry positive; columns of Cp2 / Ch2 with zero weight are zero.
  * Any output may be NULL; NTOs need nv (no) <= 1024.  FP64 on the device (the NTOs through a
- * one-CTA Jacobi eigensolver of X X^T); outputs host or device per `where`. */
+ * one-CTA Jacobi eigensolver of X X^T); outputs host or device per `where`.
+ * Alpha-beta roots (last solve with mult = PPRPA_AB): X is the full nv_alpha x nv_beta
+ * rectangle and Y the no_alpha x no_beta one; the two orbital slots are told apart by spin:
+ *   D2e[(na+nb)][(na+nb)] = diag(D^alpha, D^beta), alpha orbitals first, each spin occupied
+ *     first; D^alpha has X X^T on its virtual block and -Y Y^T on its occupied block, D^beta
+ *     X^T X and -Y^T Y; each block traces to z^T W z, and its diagonal times z^T W z is that
+ *     spin's d omega / d eps (pprpa_grad_ab).
+ *   lam_p[nv_alpha], Cp1[nv_alpha][nv_alpha], Cp2[nv_beta][nv_alpha] (zero weights beyond the
+ *     rank of X, zero Cp2 columns there); lam_h[no_alpha], Ch1[no_alpha][no_alpha],
+ *     Ch2[no_beta][no_alpha] likewise. */
 int pprpa_analyze(pprpa_ctx* ctx, int root, double* D2e, double* lam_p, double* lam_h,
                   double* Cp1, double* Cp2, double* Ch1, double* Ch2, int where);
 

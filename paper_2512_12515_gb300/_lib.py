@@ -238,6 +238,7 @@ class Context:
             raise ValueError("eps_b and L_b must both be host or both be device arrays")
         _check(self.lib.pprpa_set_beta(self._h, int(nocc_b), int(nvir_b), int(L_b.shape[0]), pe, pl, wl))
         self._nb = int(nocc_b) + int(nvir_b)
+        self._nob, self._nvb = int(nocc_b), int(nvir_b)
 
     def set_mo(self, L):
         p, w = _ptr(L)
@@ -326,15 +327,21 @@ class Context:
         _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
         return dL, deps
 
-    def analyze(self, root):
+    def analyze(self, root, ab=False):
         """Two-electron density matrix and NTOs of root `root` of the last solve (host arrays):
-        dict with D2e (n x n), lam_p, Cp1, Cp2 (virtual block) and lam_h, Ch1, Ch2 (occupied)."""
+        dict with D2e (n x n), lam_p, Cp1, Cp2 (virtual block) and lam_h, Ch1, Ch2 (occupied).
+        ab=True for a root of the alpha-beta subspace: D2e is diag(D^alpha, D^beta) and Cp2 / Ch2
+        run over beta orbitals (beta x alpha)."""
         n, _, nvv1, _ = self.dims(1)
         nv = int(round((np.sqrt(8.0 * nvv1 + 1.0) - 1.0) / 2.0))  # singlet nvv = nv (nv + 1) / 2
         no = n - nv
-        out = {"D2e": np.empty((n, n)), "lam_p": np.empty(nv), "lam_h": np.empty(no),
-               "Cp1": np.empty((nv, nv)), "Cp2": np.empty((nv, nv)),
-               "Ch1": np.empty((no, no)), "Ch2": np.empty((no, no))}
+        nob, nvb, nd = no, nv, n
+        if ab:
+            nob, nvb = getattr(self, "_nob", 0), getattr(self, "_nvb", 0)
+            nd = n + nob + nvb
+        out = {"D2e": np.empty((nd, nd)), "lam_p": np.empty(nv), "lam_h": np.empty(no),
+               "Cp1": np.empty((nv, nv)), "Cp2": np.empty((nvb, nv)),
+               "Ch1": np.empty((no, no)), "Ch2": np.empty((nob, no))}
         ptr = lambda a: a.ctypes.data if a.size else None
         _check(self.lib.pprpa_analyze(self._h, int(root), ptr(out["D2e"]), ptr(out["lam_p"]),
                                       ptr(out["lam_h"]), ptr(out["Cp1"]), ptr(out["Cp2"]),

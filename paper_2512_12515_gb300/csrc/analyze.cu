@@ -7,19 +7,24 @@
 // Jacobi), weights descending, with C^p2 = X^T C^p1 / sqrt(lambda^p).
 // Sec. "Density Matrix": D^2e has the virtual block X X^T + X^T X and the occupied block
 // -(Y Y^T + Y^T Y), zero occupied-virtual blocks.
+// Alpha-beta roots: X (alpha virtuals x beta virtuals) and Y (alpha x beta occupied) are full
+// rectangles; the two orbital slots of a pair are told apart by spin, so D^2e is
+// diag(D^alpha, D^beta) with D^alpha = (X X^T, -Y Y^T) and D^beta = (X^T X, -Y^T Y), and
+// C^p2 = X^T C^p1 / sqrt(lambda^p) runs over beta virtuals.
 #include "ctx.h"
 
 namespace pprpa {
 namespace {
 
-// z (one root, pair order: virtual pairs then occupied pairs) -> triangular X and Y (zeroed
-// by the caller).
+// z (one root, pair order: virtual pairs then occupied pairs) -> X (nva x nvb) and Y
+// (noa x nob), zeroed by the caller: the upper triangles of square matrices for a restricted
+// multiplicity (nva = nvb, noa = nob), full rectangles for the alpha-beta subspace.
 __global__ void triangular_kernel(const double* __restrict__ z, int N, int nvv, const int* __restrict__ pp,
-                                  const int* __restrict__ pq, int no, int nv, double* __restrict__ X,
-                                  double* __restrict__ Y) {
+                                  const int* __restrict__ pq, int noa, int nob, int nvb,
+                                  double* __restrict__ X, double* __restrict__ Y) {
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
-        if (I < nvv) X[(int64_t)(pp[I] - no) * nv + (pq[I] - no)] = z[I];
-        else Y[(int64_t)pp[I] * no + pq[I]] = z[I];
+        if (I < nvv) X[(int64_t)(pp[I] - noa) * nvb + (pq[I] - nob)] = z[I];
+        else Y[(int64_t)pp[I] * nob + pq[I]] = z[I];
     }
 }
 
@@ -47,10 +52,10 @@ __global__ void nto_order_kernel(const double* __restrict__ H, const double* __r
     }
 }
 
-// C2[:, k] = (X^T C1)[:, k] / sqrt(lam_k), or zero when lam_k is negligible.
-__global__ void nto_scale_kernel(double* __restrict__ C2, const double* __restrict__ lam, int m) {
+// C2[:, k] = (T^T C1)[:, k] / sqrt(lam_k), or zero when lam_k is negligible (C2: m2 x m).
+__global__ void nto_scale_kernel(double* __restrict__ C2, const double* __restrict__ lam, int m, int m2) {
     const double lmax = lam[0];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m2; t += gridDim.x * blockDim.x) {
         const int k = t % m;
         const double l = lam[k];
         C2[t] = (l > 1e-28 * lmax && l > 0.0) ? C2[t] / sqrt(l) : 0.0;
@@ -65,27 +70,28 @@ int to_caller(pprpa_ctx* c, double* dst, const double* src, size_t count, int wh
     return PPRPA_OK;
 }
 
-// NTOs of one triangular matrix T (m x m, device): lam[m], C1 and C2 [m][m] (device).
-int ntos_of(pprpa_ctx* c, const double* T, int m, double* lam, double* C1, double* C2, double* H,
+// NTOs of one block T (m x m2, device): lam[m], C1 [m][m] and C2 [m2][m] (device).
+int ntos_of(pprpa_ctx* c, const double* T, int m, int m2, double* lam, double* C1, double* C2, double* H,
             double* U, double* work, int* iwork) {
     if (m == 0) return PPRPA_OK;
     cudaStream_t st = c->stream;
     Dgemm g;  // H = T T^T
-    g.M = m; g.N = m; g.K = m;
-    g.A = T; g.lda = m;
-    g.B = T; g.ldb = m; g.transB = 1;
+    g.M = m; g.N = m; g.K = m2;
+    g.A = T; g.lda = m2;
+    g.B = T; g.ldb = m2; g.transB = 1;
     g.C = H; g.ldc = m;
     PP_TRY(dgemm(g, st));
     PP_TRY(launch_sym_eig(H, U, m, 1, (int64_t)m * m, work, iwork, st));
     nto_order_kernel<<<1, 1024, 0, st>>>(H, U, m, lam, C1);
     PP_CHECK_LAUNCH();
+    if (m2 == 0) return PPRPA_OK;
     Dgemm g2;  // C2 = T^T C1
-    g2.M = m; g2.N = m; g2.K = m;
-    g2.A = T; g2.lda = m; g2.transA = 1;
+    g2.M = m2; g2.N = m; g2.K = m;
+    g2.A = T; g2.lda = m2; g2.transA = 1;
     g2.B = C1; g2.ldb = m;
     g2.C = C2; g2.ldc = m;
     PP_TRY(dgemm(g2, st));
-    nto_scale_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 1024), 256, 0, st>>>(C2, lam, m);
+    nto_scale_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * m2, 256), 1024), 256, 0, st>>>(C2, lam, m, m2);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
@@ -102,47 +108,53 @@ extern "C" int pprpa_analyze(pprpa_ctx* c, int root, double* D2e, double* lam_p,
     if (where != PPRPA_HOST && where != PPRPA_DEVICE) return set_error(PPRPA_ERR_ARG, "analyze: bad `where`");
     if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "analyze: no solve to analyse");
     if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "analyze: root index out of range");
-    if (c->last_mult == PPRPA_AB)
-        return set_error(PPRPA_ERR_UNSUPPORTED, "analyze: the alpha-beta subspace is not built here");
+    const bool ab = c->last_mult == PPRPA_AB;
     PairTable* pt;
-    PP_TRY(ensure_pairs(c, c->last_mult, &pt));
-    const int no = c->no, nv = c->nv, n = c->n();
+    if (ab) PP_TRY(ensure_pairs_ab(c, &pt));
+    else PP_TRY(ensure_pairs(c, c->last_mult, &pt));
+    // X is nva x nvb and Y noa x nob: square triangles (restricted) or rectangles (alpha-beta)
+    const int noa = c->no, nva = c->nv, nob = ab ? c->nob : c->no, nvb = ab ? c->nvb : c->nv;
+    const int na = c->n(), nd = ab ? na + c->nb() : na;  // D2e is nd x nd
     const bool want_p = lam_p || Cp1 || Cp2, want_h = lam_h || Ch1 || Ch2;
-    if ((want_p && nv > 1024) || (want_h && no > 1024))
+    if ((want_p && nva > 1024) || (want_h && noa > 1024))
         return set_error(PPRPA_ERR_ARG, "analyze: NTOs are limited to 1024 orbitals per block");
     cudaStream_t st = c->stream;
     const double* z = c->d_lastZ + (size_t)root * pt->N;
-    const int mmax = std::max(no, nv);
+    const int mmax = std::max(std::max(noa, nva), std::max(nob, nvb));
     const size_t mm = (size_t)mmax * mmax;
     double *X, *Y, *D, *H, *U, *lam, *C1, *C2, *work;
     int* iwork;
-    PP_TRY(ws_get(c, "an_X", sizeof(double) * std::max<size_t>(1, (size_t)nv * nv), (void**)&X));
-    PP_TRY(ws_get(c, "an_Y", sizeof(double) * std::max<size_t>(1, (size_t)no * no), (void**)&Y));
-    PP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)nv * nv, st));
-    PP_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)no * no, st));
+    PP_TRY(ws_get(c, "an_X", sizeof(double) * std::max<size_t>(1, (size_t)nva * nvb), (void**)&X));
+    PP_TRY(ws_get(c, "an_Y", sizeof(double) * std::max<size_t>(1, (size_t)noa * nob), (void**)&Y));
+    PP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * (size_t)nva * nvb, st));
+    PP_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)noa * nob, st));
     triangular_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(pt->N, 256), 1024)), 256, 0, st>>>(
-        z, pt->N, pt->nvv, pt->d_pp, pt->d_pq, no, nv, X, Y);
+        z, pt->N, pt->nvv, pt->d_pp, pt->d_pq, noa, nob, nvb, X, Y);
     PP_CHECK_LAUNCH();
     if (D2e) {
-        PP_TRY(ws_get(c, "an_D", sizeof(double) * (size_t)n * n, (void**)&D));
-        PP_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, st));
-        for (int blk = 0; blk < 2; ++blk) {  // virtual block X X^T + X^T X, occupied -(Y Y^T + Y^T Y)
-            const int m = blk == 0 ? nv : no, off = blk == 0 ? no : 0;
-            if (m == 0) continue;
+        PP_TRY(ws_get(c, "an_D", sizeof(double) * (size_t)nd * nd, (void**)&D));
+        PP_CUDA(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)nd * nd, st));
+        // restricted: virtual block X X^T + X^T X, occupied -(Y Y^T + Y^T Y);
+        // alpha-beta: D^alpha = (X X^T, -Y Y^T), D^beta = (X^T X, -Y^T Y) on the diagonal of D2e
+        for (int blk = 0; blk < 2; ++blk) {
             const double* T = blk == 0 ? X : Y;
+            const int m1 = blk == 0 ? nva : noa, m2 = blk == 0 ? nvb : nob;
             const double a = blk == 0 ? 1.0 : -1.0;
-            for (int t = 0; t < 2; ++t) {
+            for (int t = 0; t < 2; ++t) {  // t = 0: T T^T (alpha side), t = 1: T^T T (beta side)
+                const int m = t == 0 ? m1 : m2, k = t == 0 ? m2 : m1;
+                if (m == 0) continue;
+                const int off = ab ? (t == 0 ? (blk == 0 ? noa : 0) : na + (blk == 0 ? nob : 0)) : (blk == 0 ? noa : 0);
                 Dgemm g;
-                g.M = m; g.N = m; g.K = m;
-                g.A = T; g.lda = m; g.transA = t;
-                g.B = T; g.ldb = m; g.transB = 1 - t;
-                g.C = D + (size_t)off * n + off; g.ldc = n;
+                g.M = m; g.N = m; g.K = k;
+                g.A = T; g.lda = m2; g.transA = t;
+                g.B = T; g.ldb = m2; g.transB = 1 - t;
+                g.C = D + (size_t)off * nd + off; g.ldc = nd;
                 g.alpha = a;
-                g.beta = t == 0 ? 0.0 : 1.0;
+                g.beta = (!ab && t == 1) ? 1.0 : 0.0;
                 PP_TRY(dgemm(g, st));
             }
         }
-        PP_TRY(to_caller(c, D2e, D, (size_t)n * n, where));
+        PP_TRY(to_caller(c, D2e, D, (size_t)nd * nd, where));
     }
     if (want_p || want_h) {
         PP_TRY(ws_get(c, "an_H", sizeof(double) * mm, (void**)&H));
@@ -154,12 +166,12 @@ extern "C" int pprpa_analyze(pprpa_ctx* c, int root, double* D2e, double* lam_p,
         PP_TRY(ws_get(c, "an_iwork", sizeof(int) * 1024, (void**)&iwork));
         for (int blk = 0; blk < 2; ++blk) {
             const bool want = blk == 0 ? want_p : want_h;
-            const int m = blk == 0 ? nv : no;
+            const int m = blk == 0 ? nva : noa, m2 = blk == 0 ? nvb : nob;
             if (!want || m == 0) continue;
-            PP_TRY(ntos_of(c, blk == 0 ? X : Y, m, lam, C1, C2, H, U, work, iwork));
+            PP_TRY(ntos_of(c, blk == 0 ? X : Y, m, m2, lam, C1, C2, H, U, work, iwork));
             PP_TRY(to_caller(c, blk == 0 ? lam_p : lam_h, lam, m, where));
             PP_TRY(to_caller(c, blk == 0 ? Cp1 : Ch1, C1, (size_t)m * m, where));
-            PP_TRY(to_caller(c, blk == 0 ? Cp2 : Ch2, C2, (size_t)m * m, where));
+            PP_TRY(to_caller(c, blk == 0 ? Cp2 : Ch2, C2, (size_t)m2 * m, where));
             PP_CUDA(cudaStreamSynchronize(st));  // the buffers are reused by the next block
         }
     }

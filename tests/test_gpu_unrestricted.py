@@ -142,3 +142,30 @@ def test_alpha_beta_gradient(pp):
         for got, want in ((dLa, ra), (dLb, rb), (dea, rea), (deb, reb)):
             assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
         assert abs(dea.sum() - 1.0) <= 1e-10 and abs(deb.sum() - 1.0) <= 1e-10
+
+
+def test_alpha_beta_analysis(pp):
+    """pprpa_analyze of alpha-beta roots (addition and removal) against the pinned oracle:
+    spin-resolved density blocks and the NTOs of the rectangular X and Y."""
+    spec, s, La, ea, Lb, eb = unrestricted_system(16, 4, 14, 3, 6, 2, 7, 91)
+    M, nvv, noo = oracle.build_matrix_ab(ea, 3, La, eb, 2, Lb)
+    ref = oracle.solve_full(M, nvv, noo)
+    got = []
+    with ab_ctx(pp, spec, s, 3, 6, 2, Lb, eb) as c:
+        c.solve(mult=pp.AB, nroots=nvv, method=pp.METHOD_FULL)
+        got.append((c.analyze(1, ab=True), ref["z_pp"][:, 1]))
+        c.solve(mult=pp.AB, nroots=noo, method=pp.METHOD_FULL, channel=pp.CHANNEL_HH)
+        got.append((c.analyze(0, ab=True), ref["z_hh"][:, -1]))
+    for a, z in got:
+        D = oracle.two_e_density_ab(z, 3, 6, 2, 7)
+        assert a["D2e"].shape == D.shape
+        assert np.abs(a["D2e"] - D).max() <= 1e-12 * max(1.0, np.abs(D).max())
+        lp, Cp1, Cp2, lh, Ch1, Ch2 = oracle.nto_ab(z, 3, 6, 2, 7)
+        for lam_g, lam_r, C1g, C1r, C2g, C2r in ((a["lam_p"], lp, a["Cp1"], Cp1, a["Cp2"], Cp2),
+                                                 (a["lam_h"], lh, a["Ch1"], Ch1, a["Ch2"], Ch2)):
+            assert np.abs(lam_g - lam_r).max() <= 1e-11
+            big = lam_r > 1e-8 * lam_r.max()
+            gaps = np.abs(lam_r[:, None] - lam_r[None, :]) + np.eye(len(lam_r))
+            uniq = big & (gaps.min(axis=1) > 1e-6)
+            assert np.abs(C1g[:, uniq] - C1r[:, uniq]).max() <= 1e-8
+            assert np.abs(C2g[:, uniq] - C2r[:, uniq]).max() <= 1e-8
