@@ -183,3 +183,86 @@ def test_ab_density_pins_accept_the_oracle():
 @pytest.mark.parametrize("mutant", [_density_with_positive_occupied_blocks, _density_with_spins_summed])
 def test_ab_density_pins_reject_planted_mistakes(mutant):
     assert not _ab_density_pins_hold(mutant)
+
+
+# ---- restricted RI sigma, correlation energy and gradient ----------------------------------
+
+def _ri_pin_holds(ri):
+    eps, L = small(2, 4, 6, 31)
+    rng = np.random.default_rng(4)
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, 2, L, mult)
+        Z = rng.standard_normal((3, nvv + noo))
+        if not np.allclose(ri(eps, 2, L, mult, Z), Z @ M.T, atol=1e-12):
+            return False
+    return True
+
+
+def _ri_sigma_without_sqrt2(eps, no, L, mult, Z):
+    # Zt_cc = X_cc instead of sqrt(2) X_cc on the singlet diagonal pairs
+    if mult != 1:
+        return oracle.ri_sigma(eps, no, L, mult, Z)
+    n = len(eps)
+    pairs = [(no + a, no + b) for (a, b) in oracle.pair_list(n - no, 1)] + oracle.pair_list(no, 1)
+    d = np.array([1.0 / np.sqrt(2.0) if p == q else 1.0 for p, q in pairs])
+    S = oracle.ri_sigma(eps, no, L, mult, Z * d)
+    E, _ = _energy_diag(eps, no, 1)
+    return S + (Z - Z * d) * E  # the orbital-energy term keeps the unscaled vector
+
+
+def _ec_identity_holds(ce):
+    eps, L = small(2, 3, 6, 33)
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, 2, L, mult)
+        e1, e2 = ce(M, nvv, noo)
+        if abs(e1 - e2) > 1e-10:
+            return False
+    return True
+
+
+def _ec_with_wrong_trace_sign(M, nvv, noo, sol=None):
+    e1, e2 = oracle.correlation_energy(M, nvv, noo, sol)
+    return e1, e2 + 2.0 * float(np.trace(M[nvv:, nvv:]))  # -sum(omega) + Tr C
+
+
+def _restricted_gradient_pin_holds(grad):
+    eps, L = small(2, 4, 5, 17)
+    h = 1e-4
+    for mult in (1, 3):
+        M, nvv, noo = oracle.build_matrix(eps, 2, L, mult)
+        sol = oracle.solve_full(M, nvv, noo)
+        for key, r in (("pp", 0), ("hh", -1)):
+            de, _ = grad(eps, 2, L, mult, sol["z_" + key][:, r])
+            for p in (0, 1, 4):
+                ep, em = eps.copy(), eps.copy()
+                ep[p] += h
+                em[p] -= h
+                fd = (oracle.solve_full(*oracle.build_matrix(ep, 2, L, mult))["omega_" + key][r]
+                      - oracle.solve_full(*oracle.build_matrix(em, 2, L, mult))["omega_" + key][r]) / (2 * h)
+                if abs(fd - de[p]) > 1e-5 * max(1.0, abs(de[p])):
+                    return False
+    return True
+
+
+def _restricted_gradient_without_metric_sign(eps, no, L, mult, z):
+    de, dL = oracle.grad_omega(eps, no, L, mult, z)
+    n = len(eps)
+    nvv = len(oracle.pair_list(n - no, mult))
+    s = np.sign(z[:nvv] @ z[:nvv] - z[nvv:] @ z[nvv:])
+    corr = np.zeros(n)
+    for I, (i, j) in enumerate(oracle.pair_list(no, mult)):
+        corr[i] += 2.0 * s * z[nvv + I] ** 2  # +s z^2 instead of -s z^2 on occupied pairs
+        corr[j] += 2.0 * s * z[nvv + I] ** 2
+    return de + corr, dL
+
+
+def test_restricted_pins_accept_the_oracle():
+    assert _ri_pin_holds(oracle.ri_sigma)
+    assert _ec_identity_holds(oracle.correlation_energy)
+    assert _restricted_gradient_pin_holds(oracle.grad_omega)
+
+
+def test_restricted_pins_reject_planted_mistakes():
+    assert not _ri_pin_holds(_ri_sigma_without_sqrt2)
+    assert not _ec_identity_holds(_ec_with_wrong_trace_sign)
+    assert not _restricted_gradient_pin_holds(_restricted_gradient_without_metric_sign)
