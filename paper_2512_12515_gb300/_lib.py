@@ -304,6 +304,8 @@ class Context:
         rc = self.lib.pprpa_solve(self._h, ctypes.byref(o), omega.ctypes.data, X.ctypes.data,
                                   Y.ctypes.data, ec.ctypes.data if want_ec else None,
                                   ctypes.byref(info))
+        if rc in (OK, ERR_NOCONV):  # the library now holds this solve's vectors
+            self._last_mult = mult
         if rc != OK and not (rc == ERR_NOCONV and not raise_noconv):
             _check(rc)
         return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
@@ -327,11 +329,15 @@ class Context:
         _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
         return dL, deps
 
-    def analyze(self, root, ab=False):
+    def analyze(self, root, ab=None):
         """Two-electron density matrix and NTOs of root `root` of the last solve (host arrays):
         dict with D2e (n x n), lam_p, Cp1, Cp2 (virtual block) and lam_h, Ch1, Ch2 (occupied).
-        ab=True for a root of the alpha-beta subspace: D2e is diag(D^alpha, D^beta) and Cp2 / Ch2
-        run over beta orbitals (beta x alpha)."""
+        For a root of the alpha-beta subspace (the last solve had mult = AB; `ab`, if given,
+        must agree) D2e is diag(D^alpha, D^beta) and Cp2 / Ch2 run over beta orbitals."""
+        last_ab = getattr(self, "_last_mult", None) == AB
+        if ab is not None and bool(ab) != last_ab:
+            raise ValueError("analyze: `ab` does not match the subspace of the last solve")
+        ab = last_ab
         n, _, nvv1, _ = self.dims(1)
         nv = int(round((np.sqrt(8.0 * nvv1 + 1.0) - 1.0) / 2.0))  # singlet nvv = nv (nv + 1) / 2
         no = n - nv

@@ -112,6 +112,7 @@ extern "C" int pprpa_analyze(pprpa_ctx* c, int root, double* D2e, double* lam_p,
     PairTable* pt;
     if (ab) PP_TRY(ensure_pairs_ab(c, &pt));
     else PP_TRY(ensure_pairs(c, c->last_mult, &pt));
+    if (pt->N != c->last_N) return set_error(PPRPA_ERR_STATE, "analyze: the pair space changed since the solve");
     // X is nva x nvb and Y noa x nob: square triangles (restricted) or rectangles (alpha-beta)
     const int noa = c->no, nva = c->nv, nob = ab ? c->nob : c->no, nvb = ab ? c->nvb : c->nv;
     const int na = c->n(), nd = ab ? na + c->nb() : na;  // D2e is nd x nd

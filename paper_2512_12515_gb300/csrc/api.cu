@@ -603,6 +603,7 @@ int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
     if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
     PairTable* t;
     PP_TRY(ensure_pairs(c, c->last_mult, &t));
+    if (t->N != c->last_N) return set_error(PPRPA_ERR_STATE, "grad: the pair space changed since the solve");
     // addition roots have z^T W z = +1, removal roots (hh channel) -1
     const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
     return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, s, dL, deps, where);
@@ -616,6 +617,7 @@ int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {
     PairTable* t;
     if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad_ec: no solve to differentiate");
     PP_TRY(ensure_pairs(c, c->last_mult, &t));
+    if (t->N != c->last_N) return set_error(PPRPA_ERR_STATE, "grad_ec: the pair space changed since the solve");
     if (!c->last_all_roots)
         return set_error(PPRPA_ERR_STATE, "grad_ec: needs every addition root (a FULL solve with nroots = nvv)");
     const int mult = c->last_mult, n = c->n(), naux = c->naux, nr = c->last_nroots;

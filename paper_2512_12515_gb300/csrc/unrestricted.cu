@@ -301,6 +301,9 @@ extern "C" int pprpa_grad_ab(pprpa_ctx* c, int root, double* dLa, double* dLb, d
     if (c->last_nroots == 0 || !c->d_lastZ || c->last_mult != PPRPA_AB)
         return set_error(PPRPA_ERR_STATE, "grad_ab: no alpha-beta solve to differentiate");
     if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad_ab: root index out of range");
+    PairTable* t;
+    PP_TRY(ensure_pairs_ab(c, &t));
+    if (t->N != c->last_N) return set_error(PPRPA_ERR_STATE, "grad_ab: the pair space changed since the solve");
     // addition roots have z^T W z = +1, removal roots (hh channel) -1
     const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
     return grad_ab(c, c->d_lastZ + (size_t)root * c->last_N, s, dLa, dLb, deps_a, deps_b, where);
@@ -332,5 +335,10 @@ extern "C" int pprpa_set_beta(pprpa_ctx* c, int nocc_b, int nvir_b, int naux, co
     c->nvb = nvir_b;
     c->pairs[2].ready = false;
     c->have_Lb = true;
+    if (c->last_mult == PPRPA_AB) {  // a stored alpha-beta solve no longer matches the pair table
+        if (c->d_lastZ) cudaFree(c->d_lastZ);
+        c->d_lastZ = nullptr;
+        c->last_nroots = 0;
+    }
     return PPRPA_OK;
 }

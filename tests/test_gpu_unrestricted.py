@@ -169,3 +169,18 @@ def test_alpha_beta_analysis(pp):
             uniq = big & (gaps.min(axis=1) > 1e-6)
             assert np.abs(C1g[:, uniq] - C1r[:, uniq]).max() <= 1e-8
             assert np.abs(C2g[:, uniq] - C2r[:, uniq]).max() <= 1e-8
+
+
+def test_new_beta_space_invalidates_the_alpha_beta_solve(pp):
+    """A new beta space changes the alpha-beta pair table: the stored solve is dropped and its
+    gradient and analysis are refused (no read of vectors of the old pair space)."""
+    spec, s, La, ea, Lb, eb = unrestricted_system(16, 4, 14, 3, 6, 2, 7, 91)
+    with ab_ctx(pp, spec, s, 3, 6, 2, Lb, eb) as c:
+        c.solve(mult=pp.AB, nroots=4, method=pp.METHOD_FULL)
+        c.grad_ab(0)
+        c.set_beta(3, 6, np.ascontiguousarray(eb), np.ascontiguousarray(Lb))  # 3 occupied now
+        with pytest.raises(pp.PprpaError) as e:
+            c.grad_ab(0)
+        assert e.value.code == -7
+        with pytest.raises(pp.PprpaError):
+            c.analyze(0)
