@@ -148,9 +148,41 @@ def _ptr(a, writable=False):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _need(a, shape, what):
+    """The library reads and writes exactly these extents through raw pointers: refuse any
+    other shape before the call."""
+    if a is not None and tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{what}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
+
+
+def _vectors(z, N, what):
+    """k of a (k, N) block or of one (N,) vector."""
+    if z.ndim == 1:
+        _need(z, (N,), what)
+        return 1
+    if z.ndim != 2 or z.shape[1] != N:
+        raise ValueError(f"{what}: expected shape (k, {N}) or ({N},), got {tuple(z.shape)}")
+    return int(z.shape[0])
+
+
+def pair_counts(nocc_act, nvir_act, mult):
+    """(nvv, noo) of the restricted pair lists: a <= b for singlets, a < b for triplets."""
+    if mult == SINGLET:
+        return nvir_act * (nvir_act + 1) // 2, nocc_act * (nocc_act + 1) // 2
+    if mult == TRIPLET:
+        return nvir_act * (nvir_act - 1) // 2, nocc_act * (nocc_act - 1) // 2
+    raise ValueError("mult must be SINGLET or TRIPLET")
+
+
 def sigma_batch(contexts, mults, zs, outs, precision=PREC_BF16, graph=True):
     """Batched sigma over molecules (pprpa_sigma_batch); zs / outs are CUDA tensors."""
     n = len(contexts)
+    if not (len(mults) == len(zs) == len(outs) == n):
+        raise ValueError("sigma_batch: one mult, z and out per context")
+    for c, m, z, o in zip(contexts, mults, zs, outs):
+        _, _, nvv, noo = c.dims(m)
+        _vectors(z, nvv + noo, "sigma_batch z")
+        _need(o, z.shape, "sigma_batch out")
     ctxs = (_P * n)(*[c._h.value for c in contexts])
     mu = (_I * n)(*[int(m) for m in mults])
     ks = (_I * n)(*[int(z.shape[0]) for z in zs])
@@ -170,7 +202,11 @@ def sigma_noalloc(mult, nocc_act, nvir_act, L, eps, z, out, stream=None):
         p, w = _ptr(a)
         if w != DEVICE:
             raise TypeError("sigma_noalloc takes device tensors only")
-    k = z.shape[0] if z.ndim == 2 else 1
+    n = int(nocc_act) + int(nvir_act)
+    _need(L, (L.shape[0], n, n), "sigma_noalloc L")
+    _need(eps, (n,), "sigma_noalloc eps")
+    k = _vectors(z, sum(pair_counts(int(nocc_act), int(nvir_act), int(mult))), "sigma_noalloc z")
+    _need(out, z.shape, "sigma_noalloc out")
     _check(load().pprpa_sigma_noalloc(int(mult), int(nocc_act), int(nvir_act), int(L.shape[0]),
                                       L.data_ptr(), eps.data_ptr(), k, z.data_ptr(),
                                       out.data_ptr(), stream))
@@ -215,6 +251,7 @@ class Context:
         if occ.shape != eps.shape or occ.ndim != 1:
             raise ValueError("occ and eps must be 1-D of equal length")
         _check(self.lib.pprpa_set_orbitals(self._h, occ.shape[0], occ.ctypes.data, eps.ctypes.data))
+        self._nmo = int(occ.shape[0])
 
     def set_active(self, nocc_act, nvir_act):
         _check(self.lib.pprpa_set_active(self._h, int(nocc_act), int(nvir_act)))
@@ -227,6 +264,7 @@ class Context:
         naux, nb, nb2 = ao3c.shape
         if nb != nb2 or C.shape[0] != nb:
             raise ValueError("shape mismatch between C and ao3c")
+        _need(C, (nb, getattr(self, "_nmo", C.shape[1])), "set_ao C (nbasis x nmo of set_orbitals)")
         _check(self.lib.pprpa_set_ao(self._h, nb, naux, pc, pa, wa))
 
     def set_beta(self, nocc_b, nvir_b, eps_b, L_b):
@@ -236,11 +274,16 @@ class Context:
         pl, wl = _ptr(L_b)
         if we != wl:
             raise ValueError("eps_b and L_b must both be host or both be device arrays")
+        nb = int(nocc_b) + int(nvir_b)
+        _need(eps_b, (nb,), "set_beta eps_b")
+        _need(L_b, (L_b.shape[0], nb, nb), "set_beta L_b")
         _check(self.lib.pprpa_set_beta(self._h, int(nocc_b), int(nvir_b), int(L_b.shape[0]), pe, pl, wl))
         self._nb = int(nocc_b) + int(nvir_b)
         self._nob, self._nvb = int(nocc_b), int(nvir_b)
 
     def set_mo(self, L):
+        nmo = getattr(self, "_nmo", L.shape[1])
+        _need(L, (L.shape[0], nmo, nmo), "set_mo L (naux x nmo x nmo of set_orbitals)")
         p, w = _ptr(L)
         _check(self.lib.pprpa_set_mo(self._h, L.shape[0], p, w))
 
@@ -254,6 +297,7 @@ class Context:
         n, naux, _, _ = self.dims(1)
         if out is None:
             out = np.empty((naux, n, n))
+        _need(out, (naux, n, n), "get_L out")
         p, w = _ptr(out, True)
         _check(self.lib.pprpa_get_L(self._h, p, w))
         return out
@@ -263,15 +307,18 @@ class Context:
         _, _, nvv, noo = self.dims(mult)
         if out is None:
             out = np.empty(nvv + noo)
+        _need(out, (nvv + noo,), "diag out")
         p, w = _ptr(out, True)
         _check(self.lib.pprpa_diag(self._h, int(mult), p, w))
         return out
 
     def sigma(self, mult, z, precision=PREC_FP64, out=None):
         pz, wz = _ptr(z)
-        k = z.shape[0] if z.ndim == 2 else 1
+        _, _, nvv, noo = self.dims(mult)
+        k = _vectors(z, nvv + noo, "sigma z")
         if out is None:
             out = np.empty_like(z) if isinstance(z, np.ndarray) else z.new_empty(z.shape)
+        _need(out, z.shape, "sigma out")
         po, wo = _ptr(out, True)
         if wz != wo:
             raise ValueError("z and out must live on the same side")
@@ -283,6 +330,7 @@ class Context:
         N = nvv + noo
         if out is None:
             out = np.empty((N, N))
+        _need(out, (N, N), "build_matrix out")
         p, w = _ptr(out, True)
         _check(self.lib.pprpa_build_matrix(self._h, int(mult), p, w))
         return out
@@ -324,8 +372,12 @@ class Context:
             dL = np.empty((naux, n, n))
         if deps is None:
             deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        _need(dL, (naux, n, n), "grad_ec dL")
+        _need(deps, (n,), "grad_ec deps")
         p1, w1 = _ptr(dL, True)
         p2, w2 = _ptr(deps, True)
+        if w1 != w2:
+            raise ValueError("dL and deps must live on the same side")
         _check(self.lib.pprpa_grad_ec(self._h, p1, p2, w1))
         return dL, deps
 
@@ -358,8 +410,13 @@ class Context:
         """Adjoint of the AO->MO transform: (d/d(P|mu nu), d/dC) from d/dL^P_pq.
 
         Arrays are all host (NumPy) or all device (torch); ``ao3c`` is needed for dC only."""
+        n_ = self.dims(1)[0]  # valid before any integrals are set: naux comes from dL
+        _need(dL, (dL.shape[0], n_, n_), "grad_ao dL")
         naux, n, _ = dL.shape
         nb, nmo = C.shape
+        _need(C, (nb, getattr(self, "_nmo", nmo)), "grad_ao C (nbasis x nmo of set_orbitals)")
+        if ao3c is not None:
+            _need(ao3c, (naux, nb, nb), "grad_ao ao3c")
         if want_dc and ao3c is None:
             raise ValueError("dC needs ao3c")
         host = isinstance(dL, np.ndarray)
@@ -383,6 +440,10 @@ class Context:
             dL = np.empty((naux, n, n)) if isinstance(z, np.ndarray) else z.new_empty((naux, n, n))
         if deps is None:
             deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        _, _, nvv, noo = self.dims(mult)
+        _need(z, (nvv + noo,), "grad_vector z")
+        _need(dL, (naux, n, n), "grad_vector dL")
+        _need(deps, (n,), "grad_vector deps")
         pz, wz = _ptr(z)
         p1, w1 = _ptr(dL, True)
         p2, w2 = _ptr(deps, True)
@@ -420,6 +481,8 @@ class Context:
             dL = np.empty((naux, n, n))
         if deps is None:
             deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        _need(dL, (naux, n, n), "grad dL")
+        _need(deps, (n,), "grad deps")
         p1, w1 = _ptr(dL, True)
         p2, w2 = _ptr(deps, True)
         if w1 != w2:

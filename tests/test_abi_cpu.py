@@ -75,3 +75,28 @@ def test_options_struct_layout_matches_header():
     # int, int, int, int, int, double, int, int, int  -> 48 bytes with alignment
     assert ctypes.sizeof(_lib.Options) == 48
     assert ctypes.sizeof(_lib.Info) == 4 * 4 + 6 * 8
+
+
+def test_binding_pair_counts_match_the_oracle_pair_lists():
+    import oracle
+    from paper_2512_12515_gb300 import _lib
+
+    for no, nv in ((0, 3), (2, 5), (5, 20)):
+        for mult in (1, 3):
+            nvv, noo = _lib.pair_counts(no, nv, mult)
+            assert nvv == len(oracle.pair_list(nv, mult)) and noo == len(oracle.pair_list(no, mult))
+
+
+def test_binding_refuses_wrong_extents():
+    import numpy as np
+    import pytest
+    from paper_2512_12515_gb300 import _lib
+
+    _lib._need(np.empty((2, 3)), (2, 3), "x")
+    with pytest.raises(ValueError):
+        _lib._need(np.empty((2, 3)), (3, 2), "x")
+    assert _lib._vectors(np.empty(7), 7, "z") == 1
+    assert _lib._vectors(np.empty((4, 7)), 7, "z") == 4
+    for bad in (np.empty(6), np.empty((4, 6)), np.empty((2, 2, 7))):
+        with pytest.raises(ValueError):
+            _lib._vectors(bad, 7, "z")
