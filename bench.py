@@ -232,22 +232,6 @@ def batch_bench(pp, torch, stream, nmol, nvec, steps, warmup):
             "autotuned_tiles_first4": tiles}
 
 
-def reduce_max(x, dist, device):
-    """Largest value of x over all ranks (the whole job takes as long as its slowest rank)."""
-    if dist is None:
-        return x
-    import torch
-
-    t = torch.tensor([x], device=device, dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def replica_rate(world, steps, k, f_vec, elapsed):
-    """Whole-job sigma TFLOP/s: every replica applies sigma to k vectors per step."""
-    return world * steps * k * f_vec / elapsed / 1e12
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -270,21 +254,20 @@ def main():
     spec = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        # the CPU oracle: one process prints the line, any other rank has nothing to do
         run_reference(args, spec, rank)
         return
+    if args.gpus != 1 or world != 1:
+        # The sigma kernels share operand tiles inside thread-block clusters by TMA multicast,
+        # which this library only issues in single-GPU processes; there is no multi-GPU form.
+        sys.exit(f"bench.py: runs on one GPU only (--gpus {args.gpus}, WORLD_SIZE {world}); "
+                 "multi-GPU runs are not supported")
 
     import torch
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    device = torch.device("cuda", local)
+    device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     import paper_2512_12515_gb300 as pp
 
@@ -311,16 +294,11 @@ def main():
     for _ in range(max(3, args.warmup)):
         step(timed_prec)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
     # ---------------- timed region: BF16 sigma of the 10-vector block ----------------
     stream = lib_stream
-    clk = ClockSampler(local)
+    clk = ClockSampler(0)
     c.profile(True)
     launches0 = pp.kernel_launches()
-    barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -331,13 +309,12 @@ def main():
     ev1.record(stream)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    barrier()
     clocks = clk.stop()
     launches = pp.kernel_launches() - launches0
     prof = c.profile(False)
-    elapsed = reduce_max(ev0.elapsed_time(ev1) / 1e3, dist, device)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
     ms_per_step = elapsed / args.steps * 1e3
-    value = replica_rate(world, args.steps, k, f_vec, elapsed)
+    value = args.steps * k * f_vec / elapsed / 1e12
 
     # roofline of the tensor-core GEMM (all its launches in the timed region).  DRAM traffic
     # per launch from one ncu capture of this kernel build (four launches of one BF16 step
@@ -372,7 +349,7 @@ def main():
                             if prof[i, 1] > 0 else None} for i in range(2)}
 
     out = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "e4m3+bf16" if args.precision == "fp8" else "bf16",
@@ -384,7 +361,7 @@ def main():
                                   else "(BF16 tensor-core sandwich")
                                + ", FP32 accumulation, FP64 in/out)",
                    "flops_per_vector": f_vec,
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "parallelism": "single GPU",
                    "l2": "inputs larger than L2 (BF16 L "
                          f"{spec.naux * (spec.n_act + 8) ** 2 * 2 / 1e9:.1f} GB, T "
                          f"{spec.naux * (spec.n_act + 8) ** 2 * k * 2 / 1e9:.0f} GB)"},
@@ -400,7 +377,7 @@ def main():
                      "per_stage": per_stage},
     }
 
-    if rank == 0:
+    if True:
         # ---- end to end through the C ABI with host buffers (z in, sigma out) ----
         zh = torch.from_numpy(z).pin_memory()
         sh = torch.empty_like(zh).pin_memory()
@@ -456,15 +433,12 @@ def main():
         if args.batch_molecules:
             out["batch"] = batch_bench(pp, torch, lib_stream, args.batch_molecules, 8, 5, 2)
         # ---- CPU oracle baseline (bounded sample) ----
-        if world == 1:
+        if True:
             t_sig, sample = cpu_sample(spec, args.cpu_frac)
             out["cpu_baseline"] = {"value": f_vec / t_sig / 1e12, "unit": "TFLOP/s",
                                    "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
         print(json.dumps(out), flush=True)
     c.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

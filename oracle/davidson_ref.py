@@ -60,14 +60,10 @@ def ri_sigma(eps_act, nocc_act, L_act, mult, Z):
     else:
         Zt[:, p, q] = Z
         Zt[:, q, p] = -Z
-    naux = L.shape[0]
-    Lrows = L.reshape(naux * n, n)  # rows (P, b)
     O = np.zeros((k, n, n))
-    for j in range(k):
-        # sum_P L^P Zt L^P as two matrix products over the stacked index (P, b):
-        # T^P = L^P Zt for all P at once, then O[a, c] = sum_{P, b} T^P[a, b] L^P[b, c].
-        T = (Lrows @ Zt[j]).reshape(naux, n, n)
-        O[j] = T.transpose(1, 0, 2).reshape(n, naux * n) @ Lrows
+    for P in range(L.shape[0]):
+        # O_j += L^P Zt_j L^P, one auxiliary function at a time, all k vectors together
+        O += L[P] @ Zt @ L[P]
     two_e = O[:, p, q]
     if mult == 1:
         two_e = two_e / np.where(p == q, np.sqrt(2.0), 1.0)[None, :]

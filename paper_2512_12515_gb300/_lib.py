@@ -198,10 +198,16 @@ def sigma_noalloc(mult, nocc_act, nvir_act, L, eps, z, out, stream=None):
     For callers that cannot allocate device memory; all arrays are CUDA float64
     tensors on the current device and the work is only enqueued on ``stream``.
     """
+    import torch
+
+    dev = torch.cuda.current_device()
     for a in (L, eps, z, out):
         p, w = _ptr(a)
         if w != DEVICE:
             raise TypeError("sigma_noalloc takes device tensors only")
+        if a.device.index != dev:
+            # the library runs on the current device and looks up its scratch there
+            raise ValueError(f"sigma_noalloc: tensor on cuda:{a.device.index}, current device is cuda:{dev}")
     n = int(nocc_act) + int(nvir_act)
     _need(L, (L.shape[0], n, n), "sigma_noalloc L")
     _need(eps, (n,), "sigma_noalloc eps")

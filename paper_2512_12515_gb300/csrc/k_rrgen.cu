@@ -9,8 +9,12 @@
 //   2. Householder reduction X = Q Hh Q^T (Hh upper Hessenberg), Q kept.
 //   3. Eigenvalues of Hh by the Francis double-shift QR iteration
 //      (implicit bulge chase with 3x3 reflectors, deflation on small
-//      subdiagonals, ad hoc exceptional shifts), following the textbook
-//      formulation (Golub & Van Loan, "Matrix Computations", Sec. 7.5).
+//      subdiagonals, exceptional shifts), following the textbook
+//      formulation (Golub & Van Loan, "Matrix Computations", Sec. 7.5).  The
+//      exceptional shift is the published one of the Handbook's hqr procedure
+//      (Martin, Peters & Wilkinson, "The QR algorithm for real Hessenberg
+//      matrices", Numer. Math. 14 (1970), Wilkinson & Reinsch, Handbook for
+//      Automatic Computation II/14; EISPACK HQR).
 //   4. Real eigenvalues in ascending order; for each, inverse iteration on
 //      the Hessenberg form (O(m^2) LU with partial pivoting), c = Q x.
 //   5. Roots of positive norm c^T S c (two-electron addition, Eq. xy_norm)
@@ -104,8 +108,10 @@ __device__ bool francis_eigs(double* A, int ld, int n, double* wr, double* wi, i
             continue;
         }
         if (++iter > 60) return false;
-        // shifts: eigenvalues of the trailing 2x2 block (sum s, product t), or an ad hoc
-        // shift every 10 iterations without deflation
+        // shifts: eigenvalues of the trailing 2x2 block (sum s, product t), or, every 10
+        // iterations without deflation, the exceptional shift of the Handbook's hqr (shift
+        // the diagonal by h22, then sum 1.5 w and product w^2 with w the two trailing
+        // subdiagonal magnitudes)
         double s, t;
         const double h11 = A[(hi - 1) * ld + hi - 1], h12 = A[(hi - 1) * ld + hi];
         const double h21 = A[hi * ld + hi - 1], h22 = A[hi * ld + hi];
