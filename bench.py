@@ -108,34 +108,132 @@ def cpu_sample(spec, frac=0.1, seed=3):
     return dt * spec.naux / nP, f"1 FP64 RI sigma over {nP} of {spec.naux} aux functions (oracle), scaled by naux"
 
 
+def oracle_integrals(spec):
+    """The oracle's own FP64 AO->MO transform of the whole workload, slice by slice."""
+    import oracle
+
+    head = synth.make_system(spec, with_ao=False)
+    orb = oracle.active_orbitals(head["occ"], spec.nocc_act, spec.nvir_act)
+    L = np.empty((spec.naux, spec.n_act, spec.n_act))
+    for p0, blk in synth.ao_slices(spec, 64):
+        L[p0:p0 + blk.shape[0]] = oracle.ao_to_mo(blk, head["C"], orb)
+    return head["eps"][orb], L
+
+
 def run_reference(args, spec, rank):
-    """The oracle as the reference arm: FP64 RI sigma on a bounded sample."""
+    """The oracle as the reference arm: one step = one FP64 RI sigma (oracle.ri_sigma, the
+    plain sum over P of L^P Zt L^P) of one trial vector over the whole workload, timed on the
+    host cores.  The integrals come from the oracle's own AO->MO transform before timing."""
     if rank != 0:
         return
+    import oracle
+
     f_vec = 3.0 * spec.naux * spec.n_act * (spec.nvir_act ** 2 + spec.nocc_act ** 2)
-    for _ in range(args.warmup):
-        cpu_sample(spec, args.cpu_frac)
-    times = []
-    sample = ""
+    eps, L = oracle_integrals(spec)
+    nvv = spec.nvir_act * (spec.nvir_act + 1) // 2
+    noo = spec.nocc_act * (spec.nocc_act + 1) // 2
+    z = synth.random_trial_vectors(nvv + noo, 1, 11)
+    z /= np.linalg.norm(z)
+    for _ in range(min(args.warmup, 1)):  # one untimed step warms the BLAS threads and caches
+        oracle.ri_sigma(eps, spec.nocc_act, L, 1, z)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        t, sample = cpu_sample(spec, args.cpu_frac)
-        times.append(t)
-    t_vec = float(np.mean(times))
-    value = f_vec / t_vec / 1e12
+        oracle.ri_sigma(eps, spec.nocc_act, L, 1, z)
+    t_step = (time.perf_counter() - t0) / args.steps
+    value = f_vec / t_step / 1e12
+    sample = f"one full FP64 RI sigma of one singlet trial vector per step (oracle.ri_sigma, all {spec.naux} aux functions)"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": 0,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_vec * 1e3,
+        "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{spec.name}: nbasis={spec.nbasis} nocc={spec.nocc} "
                                f"nocc_act={spec.nocc_act} nvir_act={spec.nvir_act} naux={spec.naux}; "
-                               "one step = oracle FP64 sigma of one trial vector (sampled over naux)",
+                               "one step = oracle FP64 sigma of one trial vector",
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def library_gemm_peaks(torch):
+    """Dense library GEMM rates on this GPU, for the rooflines of the FP64 and FP8 forms:
+    cuBLAS DGEMM (torch.matmul float64) and cuBLASLt E4M3 (torch._scaled_mm), 8192^3, best of
+    several CUDA-event-timed calls.  None where the library call is unavailable."""
+    out = {}
+    n = 8192
+
+    def best(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return min(ts)
+
+    try:
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        out["fp64_dgemm_tflops"] = 2.0 * n ** 3 / best(lambda: a @ b, 3) / 1e12
+        del a, b
+    except Exception as e:  # noqa: BLE001
+        out["fp64_dgemm_tflops"] = None
+        out["fp64_error"] = str(e)[:200]
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        out["fp8_e4m3_tflops"] = 2.0 * n ** 3 / best(
+            lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16), 10) / 1e12
+        del a, b
+    except Exception as e:  # noqa: BLE001
+        out["fp8_e4m3_tflops"] = None
+        out["fp8_error"] = str(e)[:200]
+    torch.cuda.empty_cache()
+    out["how"] = "8192^3, best of 3 (FP64) / 10 (E4M3) calls, CUDA events"
+    return out
+
+
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "tc_gemm_c2-naux270_full.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2512_12515_gb300", "csrc", "k_tc.cu")
+
+
+def measured_traffic(spec, precision):
+    """DRAM bytes per launch of the tensor-core GEMM, scaled from the committed ncu capture.
+
+    The capture summary carries machine-readable lines
+    ``traffic_bytes_per_launch: <bytes>``, ``traffic_naux: <naux>``, ``orbital_space:
+    <nocc_act> <nvir_act>``, ``precision: <form>`` and ``kernel_source_sha256: <hash of
+    k_tc.cu>``.  Returns (bytes or None, note)."""
+    import hashlib
+
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None, "no capture summary"
+    kv = {}
+    for line in text.splitlines():
+        if ":" in line and line.split(":", 1)[0].strip() in (
+                "traffic_bytes_per_launch", "traffic_naux", "orbital_space", "precision",
+                "kernel_source_sha256"):
+            k_, v = line.split(":", 1)
+            kv[k_.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha256") != src:
+        return None, "kernel changed since the ncu capture (profiles/tc_gemm_c2-naux270_full.md)"
+    if kv.get("precision") != precision or kv.get("orbital_space") != f"{spec.nocc_act} {spec.nvir_act}":
+        return None, "the ncu capture covers another form or orbital space"
+    per = float(kv["traffic_bytes_per_launch"]) * spec.naux / float(kv["traffic_naux"])
+    return per, (f"profiles/tc_gemm_c2-naux270_full.md: ncu dram bytes per launch at naux "
+                 f"{kv['traffic_naux']}, scaled by naux")
 
 
 # ---------------------------------------------------------------------------
@@ -242,7 +340,6 @@ def main():
     ap.add_argument("--nroots", type=int, default=10)
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--no-extra", action="store_true", help="skip the FP64 / solve side measurements")
-    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp8"],
                     help="form of the timed sigma: BF16 both stages, or E4M3 first stage")
     ap.add_argument("--batch-molecules", type=int, default=0,
@@ -317,11 +414,10 @@ def main():
     value = args.steps * k * f_vec / elapsed / 1e12
 
     # roofline of the tensor-core GEMM (all its launches in the timed region).  DRAM traffic
-    # per launch from one ncu capture of this kernel build (four launches of one BF16 step
-    # of the same orbital space with naux 270: 5.895 GB; every term grows with naux), or
-    # None for a form that capture did not cover.
-    traffic = (5.895e9 / 4 / 270 * spec.naux
-               if args.precision == "bf16" and (spec.nocc_act, spec.nvir_act) == (50, 600) else None)
+    # per launch from the committed ncu capture of this kernel build (a smaller auxiliary
+    # basis of the same orbital space; every term grows with naux), or None when the kernel
+    # source changed since that capture or the capture does not cover this form.
+    traffic, traffic_note = measured_traffic(spec, args.precision)
     tot_ms = float(prof[:, 1].sum())
     tot_launch = float(prof[:, 0].sum())
     alg = float(prof[:, 2].sum())
@@ -330,10 +426,12 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    peak = peaks.get("bf16_tflops_sustained")
-    peak_src = "of measured (sustained bf16)"
+    # the timed region is a fraction of a second of back-to-back steps of ~20 ms: the burst
+    # peak (a kernel timed alone), not the multi-second sustained one
+    peak = peaks.get("bf16_tflops")
+    peak_src = "of measured (burst bf16)"
     if peak is None:
-        peak, peak_src = 1700.0, "of fallback (sustained bf16)"
+        peak, peak_src = 1900.0, "of fallback (burst bf16)"
     if args.precision == "fp8":
         # stage 1 runs on E4M3 operands: its peak is the BF16 one times the nominal
         # FP8/BF16 dense ratio (4.5 / 2.25); the step's peak is the rate at which both
@@ -371,24 +469,25 @@ def main():
         "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel<1> (sigma sandwich, both stages)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "peak_source": peak_src,
-                     "traffic": traffic, "traffic_source": "profiles/tc_gemm_c2-naux270_full.md"
-                     if traffic else None, "launches_per_step": tot_launch / args.steps,
+                     "traffic": traffic, "traffic_source": traffic_note,
+                     "launches_per_step": tot_launch / args.steps,
                      "avg_launch_ms": tot_ms / tot_launch if tot_launch else None,
                      "per_stage": per_stage},
     }
 
     if True:
-        # ---- end to end through the C ABI with host buffers (z in, sigma out) ----
+        # ---- end to end through the C ABI with host buffers (z in, sigma out), over the
+        #      same number of steps as the device-timed value ----
         zh = torch.from_numpy(z).pin_memory()
         sh = torch.empty_like(zh).pin_memory()
         for _ in range(1):
             c.sigma(1, zh, timed_prec, out=sh)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(args.steps):
             c.sigma(1, zh, timed_prec, out=sh)
             chk = float(sh[0, 0])  # the result is on the host
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e_s = (time.perf_counter() - t0) / args.steps
         out["e2e"] = {"value": k * f_vec / e2e_s / 1e12, "unit": "TFLOP/s",
                       "h2d_bytes_per_step": int(z.nbytes), "d2h_bytes_per_step": int(z.nbytes),
                       "path": "pprpa_sigma with pinned host z and sigma (copies inside the call)"}
@@ -420,10 +519,15 @@ def main():
             t64 = time.perf_counter() - t0
             s64 = s1.cpu().numpy()[0]
             ref = np.abs(s64).max()
+            lib = library_gemm_peaks(torch)
+            out["library_gemm_peaks"] = lib
+            f64_rate = f_vec / t64 / 1e12
             out["precision_forms"] = {
                 "bf16x3_split_tflops": k * f_vec / t_split / 1e12,
                 "fp8_stage1_tflops": k * f_vec / t_fp8 / 1e12,
-                "fp64_tflops": f_vec / t64 / 1e12,
+                "fp64_tflops": f64_rate,
+                "fp64_frac_of_library_dgemm": (f64_rate / lib["fp64_dgemm_tflops"]
+                                               if lib.get("fp64_dgemm_tflops") else None),
                 "fp64_ms_per_vector": t64 * 1e3,
                 "max_rel_err_vs_fp64": {"bf16": float(np.abs(s_bf16[0] - s64).max() / ref),
                                         "bf16x3_split": float(np.abs(s_split[0] - s64).max() / ref),

@@ -82,7 +82,8 @@ typedef struct pprpa_options {
     int max_iter;      /* Davidson iteration cap */
     int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic: 112, with restarts at 72
                           below 8192 pairs while the shifted pencil is definite */
-    int want_ec;       /* FULL only: also return the correlation energy */
+    int want_ec;       /* also return the correlation energy: FULL, or Davidson asked for every
+                          root of its channel (nroots = nvv for pp, noo for hh) */
 } pprpa_options;
 
 typedef struct pprpa_info {
@@ -96,6 +97,9 @@ typedef struct pprpa_info {
     double t_sigma_ms;    /* device time in sigma (CUDA events) */
     double t_total_ms;    /* device time of the whole solve */
     double sigma_flops;   /* algorithmic sigma flops 3*naux*n*(nv^2+no^2) per vector, summed */
+    int nconv;            /* returned roots whose residual met conv_tol (the lowest ones need
+                             not be among them when the solve did not converge) */
+    int n_real;           /* Davidson: real positive-norm Ritz values in the last subspace */
 } pprpa_info;
 
 /* ---- context ------------------------------------------------------------
@@ -256,15 +260,35 @@ int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int naux, const do
  * roots, omega descending, X^T X - Y^T Y = -1 (the lower sign of Eq. xy_norm);
  * they are found as the lowest positive-norm roots of the pencil (M, -W).
  * X[nroots][nvv] and Y[nroots][noo] (either may be NULL), largest-magnitude
- * component positive; ec (may be NULL, FULL only): correlation energy of Eq.
- * correlation_energy for this multiplicity, sum(Omega^{N+2}) - Tr A from every
- * addition root (pp) or -sum(Omega^{N-2}) - Tr C from every removal root (hh);
- * the two agree for a stable problem.  info may be NULL.
+ * component positive; ec (may be NULL; written when opts->want_ec is set): correlation
+ * energy of Eq. correlation_energy for this multiplicity, sum(Omega^{N+2}) - Tr A from every
+ * addition root (pp) or -sum(Omega^{N-2}) - Tr C from every removal root (hh), summed in
+ * FP64 on the device; the two agree for a stable problem.  FULL always has every root;
+ * Davidson gives ec only when nroots is every root of its channel (noo for hh, the
+ * affordable form when the occupied block is small) and they converged, NaN otherwise.
+ * info may be NULL.
  * Host output pointers.  Returns PPRPA_ERR_NOCONV (outputs filled with the
  * last iterate) or PPRPA_ERR_UNSTABLE when no positive-definite shift
  * exists.  The converged eigenvectors stay on the device for pprpa_grad. */
 int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double* X,
                 double* Y, double* ec, pprpa_info* info);
+
+/* pprpa_solve_batch: pprpa_solve (Davidson) for nmol molecules at once, each its own context
+ * on one device with its own options opts[m] (multiplicity, channel, precision, roots,
+ * tolerance; method must be PPRPA_METHOD_DAVIDSON).  Every molecule's iteration runs on its
+ * own host thread and its context's stream, so the per-molecule FP64 steps (projections,
+ * the Rayleigh-Ritz eigensolve, residuals, corrections) of different molecules overlap on
+ * the GPU; their BF16 and BF16x3 sigma products (precision PPRPA_PREC_BF16) are gathered
+ * into one batched tensor-core sigma per round (pprpa_sigma_batch's launches, replayed from a
+ * CUDA graph while the set of molecules and block sizes stays the same) once every molecule
+ * still iterating has asked for one.  FP64 and FP8 solves compute their sigma alone.
+ * Outputs per molecule as pprpa_solve: omega[m][nroots], X[m], Y[m] (X, Y or any X[m], Y[m]
+ * may be NULL), infos[m] (NULL allowed), host pointers; rcs[m] receives each molecule's
+ * return code.  The correlation energy is not returned here.  Returns PPRPA_OK when every
+ * molecule returned PPRPA_OK, otherwise the first failing molecule's code (its message
+ * names the molecule).  The contexts must not be used by other threads during the call. */
+int pprpa_solve_batch(int nmol, pprpa_ctx* const* ctxs, const pprpa_options* opts, double* const* omega,
+                      double* const* X, double* const* Y, pprpa_info* infos, int* rcs);
 
 /* pprpa_grad: Hellmann-Feynman gradient (Sec. "Analytic Gradient") of root
  * `root` of the last pprpa_solve (either channel; the sign z^T W z = -1 of a
@@ -313,14 +337,26 @@ int pprpa_analyze(pprpa_ctx* ctx, int root, double* D2e, double* lam_p, double* 
 int pprpa_grad_ao(pprpa_ctx* ctx, int nbasis, int naux, const double* C, const double* ao3c,
                   const double* dL, double* dAO, double* dC, int where);
 
-/* pprpa_grad_ec: gradient of the correlation energy E_c = sum(Omega^{N+2}) - Tr A
- * (Eq. correlation_energy) of the last solve's multiplicity, with respect to L^P_pq
- * (dL[naux][n][n], entries independent) and eps_p (deps[n]): the sum of every addition
- * root's Hellmann-Feynman gradient minus the derivative of Tr A.  Needs a preceding FULL
- * solve of the pp channel that returned every addition root (nroots = nvv);
- * PPRPA_ERR_STATE otherwise.
- * FP64 on the device; outputs host or device per `where`, either may be NULL. */
+/* pprpa_grad_ec: gradient of the correlation energy of Eq. correlation_energy of the last
+ * solve's multiplicity, with respect to L^P_pq (dL[naux][n][n], entries independent) and
+ * eps_p (deps[n]).  After a solve of the pp channel that returned every addition root
+ * (nroots = nvv): the sum of their Hellmann-Feynman gradients z^T (dM) z minus the
+ * derivative of Tr A (E_c = sum(Omega^{N+2}) - Tr A).  After a solve of the hh channel that
+ * returned every removal root (nroots = noo, FULL or converged Davidson): E_c =
+ * -sum(Omega^{N-2}) - Tr C, i.e. the sum of z^T (dM) z over the removal roots (their
+ * d Omega is -z^T (dM) z) minus the derivative of Tr C.  PPRPA_ERR_STATE without such a
+ * solve.  FP64 on the device (batched over roots); outputs host or device per `where`,
+ * either may be NULL. */
 int pprpa_grad_ec(pprpa_ctx* ctx, double* dL, double* deps, int where);
+
+/* pprpa_grad_sum: gradient of sum_{r < nw} w[r] omega_r over the first nw roots of the last
+ * pprpa_solve (either channel, removal roots carrying their sign z^T W z = -1), i.e.
+ * sum_r w[r] (d omega_r / d L^P_pq, d omega_r / d eps_p) of pprpa_grad in one call (the
+ * backward step of a function of several roots, Sec. "Analytic Gradient").  w: host
+ * float64[nw], finite, 1 <= nw <= roots of the last solve.  dL[naux][n][n], deps[n]: host or
+ * device per `where`, either may be NULL.  FP64 on the device, the roots batched through
+ * one reduction per slice of the auxiliary index.  PPRPA_ERR_STATE without a solve. */
+int pprpa_grad_sum(pprpa_ctx* ctx, int nw, const double* w, double* dL, double* deps, int where);
 
 /* pprpa_grad_vector: the same Hellmann-Feynman contraction for an explicit pair vector
  * z[N] of multiplicity `mult` (Sec. "Analytic Gradient": d(z^T M z)/d theta = z^T (dM/d theta) z),

@@ -40,6 +40,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
 * two_e_density_ab, nto_ab (alpha-beta subspace): pinned by each spin's trace rule,
   by the alpha and beta energy gradients of grad_omega_ab (the diagonals), by
   reconstructing X and Y from their NTOs and by the weight sum rule.
+* matrix_rows / explicit_matrix_ri, shifted_lambda_min, roots_near (stability at
+  workload sizes): pinned by build_matrix (rows), dense symmetric eigenvalues of
+  M - mu W, and the dense spectrum of solve_full (roots and their norm signs).
 * eigenvector phase: fixed by convention (largest-magnitude component
   positive); parity unpinned beyond that convention.
 """
@@ -76,3 +79,4 @@ from .brute import (  # noqa: F401
     mp2_pair_energy,
 )
 from .davidson_ref import ri_sigma, ri_sigma_rows, davidson  # noqa: F401
+from .stability import matrix_rows, explicit_matrix_ri, shifted_lambda_min, roots_near  # noqa: F401

@@ -54,6 +54,8 @@ class Info(ctypes.Structure):
         ("t_sigma_ms", ctypes.c_double),
         ("t_total_ms", ctypes.c_double),
         ("sigma_flops", ctypes.c_double),
+        ("nconv", ctypes.c_int),
+        ("n_real", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -88,6 +90,7 @@ SIGNATURES = {
     "pprpa_grad": (_I, [_P, _I, _P, _P, _I]),
     "pprpa_grad_vector": (_I, [_P, _I, _P, _P, _P, _I]),
     "pprpa_grad_ec": (_I, [_P, _P, _P, _I]),
+    "pprpa_grad_sum": (_I, [_P, _I, _P, _P, _P, _I]),
     "pprpa_grad_ao": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _I]),
     "pprpa_analyze": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "pprpa_set_beta": (_I, [_P, _I, _I, _I, _P, _P, _I]),
@@ -99,6 +102,7 @@ SIGNATURES = {
     "pprpa_sigma_noalloc": (_I, [_I, _I, _I, _I, _P, _P, _I, _P, _P, _P]),
     "pprpa_sigma_batch": (_I, [_I, _P, _P, _P, _P, _P, _I, _I]),
     "pprpa_autotune": (_I, [_P, _I, _I, _I, _P]),
+    "pprpa_solve_batch": (_I, [_I, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -190,6 +194,44 @@ def sigma_batch(contexts, mults, zs, outs, precision=PREC_BF16, graph=True):
     op = (_P * n)(*[o.data_ptr() for o in outs])
     _check(load().pprpa_sigma_batch(n, ctxs, mu, ks, zp, op, int(precision), 1 if graph else 0))
     return outs
+
+
+def solve_batch(contexts, mults, nroots, precision=PREC_BF16, conv_tol=1e-5, max_iter=200,
+                channel=CHANNEL_PP, max_subspace=0):
+    """pprpa_solve_batch over several contexts (one molecule each, one device).
+
+    mults / nroots: one entry per molecule (or a single value for all).  Returns a list of
+    dicts like Context.solve (omega, X, Y, info, rc); raises only for a call-level argument
+    error, a molecule's own failure shows in its rc."""
+    n = len(contexts)
+    mults = list(mults) if hasattr(mults, "__len__") else [mults] * n
+    nroots = list(nroots) if hasattr(nroots, "__len__") else [nroots] * n
+    opts = (Options * n)()
+    om, Xs, Ys = [], [], []
+    for m, c in enumerate(contexts):
+        _, _, nvv, noo = c.dims(mults[m])
+        opts[m] = Options(int(mults[m]), int(channel), METHOD_DAVIDSON, int(precision), int(nroots[m]),
+                          float(conv_tol), int(max_iter), int(max_subspace), 0)
+        om.append(np.empty(nroots[m]))
+        Xs.append(np.empty((nroots[m], nvv)))
+        Ys.append(np.empty((nroots[m], max(noo, 1))))
+    infos = (Info * n)()
+    rcs = (_I * n)()
+    ctxs = (_P * n)(*[c._h for c in contexts])
+    po = (_P * n)(*[a.ctypes.data for a in om])
+    px = (_P * n)(*[a.ctypes.data for a in Xs])
+    py = (_P * n)(*[a.ctypes.data for a in Ys])
+    rc = load().pprpa_solve_batch(n, ctxs, opts, po, px, py, infos, rcs)
+    if rc == ERR_ARG and all(r == 0 for r in rcs):
+        _check(rc)
+    out = []
+    for m, c in enumerate(contexts):
+        if rcs[m] in (OK, ERR_NOCONV):
+            c._last_mult = mults[m]
+        noo = c.dims(mults[m])[3]
+        out.append({"omega": om[m], "X": Xs[m], "Y": Ys[m][:, :noo], "info": infos[m].as_dict(),
+                    "rc": int(rcs[m])})
+    return out
 
 
 def sigma_noalloc(mult, nocc_act, nvir_act, L, eps, z, out, stream=None):
@@ -371,8 +413,26 @@ class Context:
         _check(self.lib.pprpa_autotune(self._h, int(mult), int(k), int(precision), t))
         return list(t)
 
+    def grad_sum(self, w, dL=None, deps=None):
+        """Gradient of sum_r w[r] omega_r over the first len(w) roots of the last solve."""
+        n, naux, _, _ = self.dims(1)
+        wh = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+        if dL is None:
+            dL = np.empty((naux, n, n))
+        if deps is None:
+            deps = np.empty(n) if isinstance(dL, np.ndarray) else dL.new_empty(n)
+        _need(dL, (naux, n, n), "grad_sum dL")
+        _need(deps, (n,), "grad_sum deps")
+        p1, w1 = _ptr(dL, True)
+        p2, w2 = _ptr(deps, True)
+        if w1 != w2:
+            raise ValueError("dL and deps must live on the same side")
+        _check(self.lib.pprpa_grad_sum(self._h, int(wh.shape[0]), wh.ctypes.data, p1, p2, w1))
+        return dL, deps
+
     def grad_ec(self, dL=None, deps=None):
-        """dE_c/dL^P_pq and dE_c/d eps_p after a FULL solve with every addition root."""
+        """dE_c/dL^P_pq and dE_c/d eps_p after a solve that returned every root of its
+        channel (every addition root, or every removal root)."""
         n, naux, _, _ = self.dims(1)
         if dL is None:
             dL = np.empty((naux, n, n))

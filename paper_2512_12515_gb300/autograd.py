@@ -1,10 +1,10 @@
 """torch.autograd wrapper: (L, eps) -> lowest two-electron addition energies.
 
 Forward runs pprpa_solve on the device; backward contracts the incoming
-gradient with the Hellmann-Feynman derivatives from pprpa_grad
-(Sec. "Analytic Gradient": d omega = z^T (dM) z for z^T W z = 1), computed
-in FP64 by the library.  Both directions stay in the CUDA library; this
-class only moves tensors across the C ABI.
+gradient with the Hellmann-Feynman derivatives of the roots in one
+pprpa_grad_sum call (Sec. "Analytic Gradient": d omega = z^T (dM) z for
+z^T W z = 1), computed in FP64 by the library.  Both directions stay in the
+CUDA library; this class only moves tensors across the C ABI.
 """
 from __future__ import annotations
 
@@ -20,7 +20,9 @@ class PPRPARoots(torch.autograd.Function):
     L: (naux, n, n) float64 CUDA tensor of active-space fitted integrals
     (occupied orbitals first), eps: (n,) float64 orbital energies (any
     device), nocc: number of occupied orbitals among the n.
-    Returns omega (nroots,) on L's device.
+    Returns omega (nroots,) on L's device.  The library context holding the
+    solve's eigenvectors lives as long as the autograd graph, so backward
+    may run more than once (retain_graph=True).
     """
 
     @staticmethod
@@ -36,28 +38,17 @@ class PPRPARoots(torch.autograd.Function):
         c.set_mo(L.detach().contiguous())
         res = c.solve(mult=mult, nroots=nroots, method=method, precision=precision,
                       conv_tol=conv_tol)
-        ctx.pprpa = c
-        ctx.nroots = nroots
+        ctx.pprpa = c  # closed when the graph (and this ctx) is freed
         ctx.shape = L.shape
         ctx.eps_device = eps.device
         return torch.as_tensor(res["omega"], dtype=torch.float64, device=L.device)
 
     @staticmethod
     def backward(ctx, g):
-        c = ctx.pprpa
         naux, n, _ = ctx.shape
-        dL = torch.zeros(ctx.shape, dtype=torch.float64, device=g.device)
-        de = torch.zeros(n, dtype=torch.float64, device=g.device)
-        tmpL = torch.empty_like(dL)
-        tmpe = torch.empty_like(de)
-        gh = g.detach().to("cpu").numpy()
-        for r in range(ctx.nroots):
-            if gh[r] == 0.0:
-                continue
-            c.grad(r, tmpL, tmpe)
-            dL.add_(tmpL, alpha=float(gh[r]))
-            de.add_(tmpe, alpha=float(gh[r]))
-        c.close()
+        dL = torch.empty(ctx.shape, dtype=torch.float64, device=g.device)
+        de = torch.empty(n, dtype=torch.float64, device=g.device)
+        ctx.pprpa.grad_sum(g.detach().to("cpu", torch.float64).numpy(), dL, de)
         return dL, de.to(ctx.eps_device), None, None, None, None, None, None
 
 

@@ -211,6 +211,7 @@ void pprpa_destroy(pprpa_ctx* c) {
         cudaEventDestroy(r.b);
     }
     destroy_batch_plan(c->batch_plan);
+    destroy_batch_plan(c->batch_plan3);
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -535,12 +536,19 @@ int pprpa_sigma(pprpa_ctx* c, int mult, int precision, int k, const double* z, d
 }  // extern "C"
 
 namespace pprpa {
-// d omega / d L^P and d omega / d eps for one W-normalised pair vector z (device, N).
-static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, double* dL,
-                          double* deps, int where) {
+// Weighted Hellmann-Feynman gradient (Sec. "Analytic Gradient") of nr pair vectors Z (device,
+// nr x N, row r = z_r):
+//   G = sum_r f_r z_r^T (dM / d theta) z_r  [- d Tr A (trace_blk 0) or - d Tr C (trace_blk 1)]
+// with respect to every entry of L^P (dL[naux][n][n]) and to eps (deps[n]); f on the host.
+// Per root, z^T (dM / d L^P) z = 1/2 (Zt L^P Zt^T + Zt^T L^P Zt) = t Zt L^P Zt, t = +1
+// singlet (Zt symmetric), -1 triplet (Zt antisymmetric).  The roots go through batched FP64
+// GEMMs, T[P][r] = L^P Zt_r for a slice of P and a chunk of roots, then
+// dL^P (+)= sum_r (t f_r Zt_r) T[P][r] as one GEMM reducing over the roots.
+static int grad_weighted(pprpa_ctx* c, int mult, const double* Z, int nr, const double* f,
+                         int trace_blk, double* dL, double* deps, int where) {
     PairTable* t;
     PP_TRY(ensure_pairs(c, mult, &t));
-    const int n = c->n(), naux = c->naux;
+    const int n = c->n(), naux = c->naux, N = t->N;
     const int64_t n2 = (int64_t)n * n;
     cudaStream_t st = c->stream;
     const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -548,38 +556,60 @@ static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, dou
         double* d;
         PP_TRY(ws_get(c, "grad_eps", sizeof(double) * n, (void**)&d));
         PP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
-        PP_TRY(launch_grad_eps(z, t->N, t->nvv, t->d_pp, t->d_pq, n, s, d, st));
+        for (int r = 0; r < nr; ++r)
+            if (f[r] != 0.0)
+                PP_TRY(launch_grad_eps(Z + (size_t)r * N, N, t->nvv, t->d_pp, t->d_pq, n, f[r], d, st));
+        if (trace_blk >= 0) PP_TRY(launch_trace_block_grad(c->d_L, 0, n, c->no, mult, trace_blk, nullptr, d, st));
         PP_CUDA(cudaMemcpyAsync(deps, d, sizeof(double) * n, kind, st));
     }
     if (dL) {
-        // d omega / d L^P = s/2 (Zt L^P Zt^T + Zt^T L^P Zt) = s * t * Zt L^P Zt, t = +1 singlet
-        // (Zt symmetric), -1 triplet (Zt antisymmetric).
-        double *Zt, *T, *out;
-        PP_TRY(ws_get(c, "grad_Zt", sizeof(double) * n2, (void**)&Zt));
-        PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2, st));
-        PP_TRY(launch_unpack_f64(z, 1, t->N, t->d_pp, t->d_pq, n, mult, Zt, st));
-        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * n2)));
-        PP_TRY(ws_get(c, "grad_T", sizeof(double) * n2 * pc, (void**)&T));
+        // roots per chunk: their packed pair matrices (plain and weighted) within 1 GiB
+        const int rc = (int)std::max<int64_t>(1, std::min<int64_t>(nr, (1LL << 30) / (16 * n2)));
+        // auxiliary slices per pass: T within 1 GiB and the batched launch within its grid
+        int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * n2 * rc)));
+        pc = std::min(pc, std::max(1, 65535 / rc));
+        double *Zt, *Zw, *T, *out, *fd;
+        PP_TRY(ws_get(c, "grad_Zt", sizeof(double) * n2 * rc, (void**)&Zt));
+        PP_TRY(ws_get(c, "grad_Zw", sizeof(double) * n2 * rc, (void**)&Zw));
+        PP_TRY(ws_get(c, "grad_T", sizeof(double) * n2 * rc * pc, (void**)&T));
+        PP_TRY(ws_get(c, "grad_f", sizeof(double) * nr, (void**)&fd));
+        std::vector<double> tf(f, f + nr);
+        for (double& v : tf) v *= mult == 1 ? 1.0 : -1.0;
+        PP_CUDA(cudaMemcpyAsync(fd, tf.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
         if (where == PPRPA_DEVICE) out = dL;
         else PP_TRY(ws_get(c, "grad_dL", sizeof(double) * n2 * pc, (void**)&out));
+        auto unpack_chunk = [&](int r0, int kr) -> int {
+            PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2 * kr, st));
+            PP_TRY(launch_unpack_f64(Z + (size_t)r0 * N, kr, N, t->d_pp, t->d_pq, n, mult, Zt, st));
+            PP_CUDA(cudaMemcpyAsync(Zw, Zt, sizeof(double) * n2 * kr, cudaMemcpyDeviceToDevice, st));
+            return launch_scale_rows(Zw, kr, n2, fd + r0, st);
+        };
+        if (nr <= rc) PP_TRY(unpack_chunk(0, nr));
         for (int P0 = 0; P0 < naux; P0 += pc) {
             const int np = std::min(pc, naux - P0);
-            Dgemm g1;  // T^P = L^P Zt
-            g1.M = n; g1.N = n; g1.K = n;
-            g1.A = c->d_L + (size_t)P0 * n2; g1.lda = n; g1.sA1 = n2;
-            g1.B = Zt; g1.ldb = n;
-            g1.C = T; g1.ldc = n; g1.sC1 = n2;
-            g1.nb1 = np;
-            PP_TRY(dgemm(g1, st));
-            Dgemm g2;  // dL^P = (s t) Zt T^P
-            g2.M = n; g2.N = n; g2.K = n;
-            g2.A = Zt; g2.lda = n;
-            g2.B = T; g2.ldb = n; g2.sB1 = n2;
             double* dst = where == PPRPA_DEVICE ? out + (size_t)P0 * n2 : out;
-            g2.C = dst; g2.ldc = n; g2.sC1 = n2;
-            g2.nb1 = np;
-            g2.alpha = s * (mult == 1 ? 1.0 : -1.0);
-            PP_TRY(dgemm(g2, st));
+            for (int r0 = 0; r0 < nr; r0 += rc) {
+                const int kr = std::min(rc, nr - r0);
+                if (nr > rc) PP_TRY(unpack_chunk(r0, kr));
+                Dgemm g1;  // T[p][r] = L^P Zt_r
+                g1.M = n; g1.N = n; g1.K = n;
+                g1.A = c->d_L + (size_t)P0 * n2; g1.lda = n; g1.sA1 = n2;
+                g1.B = Zt; g1.ldb = n; g1.sB2 = n2;
+                g1.C = T; g1.ldc = n; g1.sC1 = n2 * kr; g1.sC2 = n2;
+                g1.nb1 = np; g1.nb2 = kr;
+                PP_TRY(dgemm(g1, st));
+                Dgemm g2;  // dL^P (+)= sum_r (t f_r Zt_r) T[p][r]
+                g2.M = n; g2.N = n; g2.K = n;
+                g2.A = Zw; g2.lda = n; g2.sAr = n2;
+                g2.B = T; g2.ldb = n; g2.sB1 = n2 * kr; g2.sBr = n2;
+                g2.C = dst; g2.ldc = n; g2.sC1 = n2;
+                g2.nb1 = np; g2.nr = kr;
+                g2.beta = r0 == 0 ? 0.0 : 1.0;
+                PP_TRY(dgemm(g2, st));
+            }
+            if (trace_blk >= 0)
+                PP_TRY(launch_trace_block_grad(c->d_L + (size_t)P0 * n2, np, n, c->no, mult, trace_blk, dst,
+                                               nullptr, st));
             if (where == PPRPA_HOST) {
                 PP_CUDA(cudaMemcpyAsync(dL + (size_t)P0 * n2, out, sizeof(double) * n2 * np,
                                         cudaMemcpyDeviceToHost, st));
@@ -588,6 +618,20 @@ static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, dou
         }
     }
     PP_CUDA(cudaStreamSynchronize(st));
+    return PPRPA_OK;
+}
+
+// Checks that the last solve can be differentiated; returns its pair table.
+static int last_solve_pairs(pprpa_ctx* c, const char* who, PairTable** out) {
+    if (c && c->last_nroots && c->last_mult == PPRPA_AB)
+        return set_error(PPRPA_ERR_UNSUPPORTED,
+                         std::string(who) + ": roots of the alpha-beta subspace take pprpa_grad_ab");
+    PP_TRY(check_ctx(c));
+    PP_TRY(need_L(c));
+    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, std::string(who) + ": no solve to differentiate");
+    PP_TRY(ensure_pairs(c, c->last_mult, out));
+    if ((*out)->N != c->last_N)
+        return set_error(PPRPA_ERR_STATE, std::string(who) + ": the pair space changed since the solve");
     return PPRPA_OK;
 }
 }  // namespace pprpa
@@ -595,89 +639,38 @@ static int grad_of_vector(pprpa_ctx* c, int mult, const double* z, double s, dou
 extern "C" {
 
 int pprpa_grad(pprpa_ctx* c, int root, double* dL, double* deps, int where) {
-    if (c && c->last_nroots && c->last_mult == PPRPA_AB)
-        return set_error(PPRPA_ERR_UNSUPPORTED, "grad: roots of the alpha-beta subspace take pprpa_grad_ab");
-    PP_TRY(check_ctx(c));
-    PP_TRY(need_L(c));
-    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad: no solve to differentiate");
-    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
     PairTable* t;
-    PP_TRY(ensure_pairs(c, c->last_mult, &t));
-    if (t->N != c->last_N) return set_error(PPRPA_ERR_STATE, "grad: the pair space changed since the solve");
+    PP_TRY(last_solve_pairs(c, "grad", &t));
+    if (root < 0 || root >= c->last_nroots) return set_error(PPRPA_ERR_ARG, "grad: root index out of range");
     // addition roots have z^T W z = +1, removal roots (hh channel) -1
     const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
-    return grad_of_vector(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, s, dL, deps, where);
+    return grad_weighted(c, c->last_mult, c->d_lastZ + (size_t)root * t->N, 1, &s, -1, dL, deps, where);
+}
+
+int pprpa_grad_sum(pprpa_ctx* c, int nw, const double* w, double* dL, double* deps, int where) {
+    PairTable* t;
+    PP_TRY(last_solve_pairs(c, "grad_sum", &t));
+    if (nw < 1 || nw > c->last_nroots || !w) return set_error(PPRPA_ERR_ARG, "grad_sum: need 1 <= nw <= roots of the last solve");
+    const double s = c->last_channel == PPRPA_CHANNEL_HH ? -1.0 : 1.0;
+    std::vector<double> f(w, w + nw);
+    for (double& v : f) {
+        if (!std::isfinite(v)) return set_error(PPRPA_ERR_ARG, "grad_sum: non-finite weight");
+        v *= s;
+    }
+    return grad_weighted(c, c->last_mult, c->d_lastZ, nw, f.data(), -1, dL, deps, where);
 }
 
 int pprpa_grad_ec(pprpa_ctx* c, double* dL, double* deps, int where) {
-    if (c && c->last_nroots && c->last_mult == PPRPA_AB)
-        return set_error(PPRPA_ERR_UNSUPPORTED, "gradients of the alpha-beta subspace are not built");
-    PP_TRY(check_ctx(c));
-    PP_TRY(need_L(c));
     PairTable* t;
-    if (c->last_nroots == 0 || !c->d_lastZ) return set_error(PPRPA_ERR_STATE, "grad_ec: no solve to differentiate");
-    PP_TRY(ensure_pairs(c, c->last_mult, &t));
-    if (t->N != c->last_N) return set_error(PPRPA_ERR_STATE, "grad_ec: the pair space changed since the solve");
+    PP_TRY(last_solve_pairs(c, "grad_ec", &t));
     if (!c->last_all_roots)
-        return set_error(PPRPA_ERR_STATE, "grad_ec: needs every addition root (a FULL solve with nroots = nvv)");
-    const int mult = c->last_mult, n = c->n(), naux = c->naux, nr = c->last_nroots;
-    const int64_t n2 = (int64_t)n * n;
-    cudaStream_t st = c->stream;
-    const cudaMemcpyKind kind = where == PPRPA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    // d E_c = sum over addition roots of z^T (dM) z  -  d Tr A
-    if (deps) {
-        double* d;
-        PP_TRY(ws_get(c, "gec_eps", sizeof(double) * n, (void**)&d));
-        PP_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
-        for (int r = 0; r < nr; ++r)
-            PP_TRY(launch_grad_eps(c->d_lastZ + (size_t)r * t->N, t->N, t->nvv, t->d_pp, t->d_pq, n, 1.0, d, st));
-        PP_TRY(launch_trace_a_grad(c->d_L, 0, n, c->no, mult, nullptr, d, st));
-        PP_CUDA(cudaMemcpyAsync(deps, d, sizeof(double) * n, kind, st));
-    }
-    if (dL) {
-        if ((double)nr * n2 * 8 > (double)(2LL << 30))
-            return set_error(PPRPA_ERR_ARG, "grad_ec: too many roots for the packed pair matrices");
-        double *Zt, *T, *out;
-        PP_TRY(ws_get(c, "gec_Zt", sizeof(double) * n2 * nr, (void**)&Zt));
-        PP_CUDA(cudaMemsetAsync(Zt, 0, sizeof(double) * n2 * nr, st));
-        PP_TRY(launch_unpack_f64(c->d_lastZ, nr, t->N, t->d_pp, t->d_pq, n, mult, Zt, st));
-        const int pc = (int)std::max<int64_t>(1, std::min<int64_t>(naux, (1LL << 30) / (8 * n2)));
-        PP_TRY(ws_get(c, "gec_T", sizeof(double) * n2 * pc, (void**)&T));
-        if (where == PPRPA_DEVICE) out = dL;
-        else PP_TRY(ws_get(c, "gec_dL", sizeof(double) * n2 * pc, (void**)&out));
-        const double tsign = mult == 1 ? 1.0 : -1.0;
-        for (int P0 = 0; P0 < naux; P0 += pc) {
-            const int np = std::min(pc, naux - P0);
-            double* dst = where == PPRPA_DEVICE ? out + (size_t)P0 * n2 : out;
-            for (int r = 0; r < nr; ++r) {
-                const double* Zr = Zt + (size_t)r * n2;
-                Dgemm g1;  // T^P = L^P Zt_r
-                g1.M = n; g1.N = n; g1.K = n;
-                g1.A = c->d_L + (size_t)P0 * n2; g1.lda = n; g1.sA1 = n2;
-                g1.B = Zr; g1.ldb = n;
-                g1.C = T; g1.ldc = n; g1.sC1 = n2;
-                g1.nb1 = np;
-                PP_TRY(dgemm(g1, st));
-                Dgemm g2;  // dL^P (+)= t Zt_r T^P
-                g2.M = n; g2.N = n; g2.K = n;
-                g2.A = Zr; g2.lda = n;
-                g2.B = T; g2.ldb = n; g2.sB1 = n2;
-                g2.C = dst; g2.ldc = n; g2.sC1 = n2;
-                g2.nb1 = np;
-                g2.alpha = tsign;
-                g2.beta = r == 0 ? 0.0 : 1.0;
-                PP_TRY(dgemm(g2, st));
-            }
-            PP_TRY(launch_trace_a_grad(c->d_L + (size_t)P0 * n2, np, n, c->no, mult, dst, nullptr, st));
-            if (where == PPRPA_HOST) {
-                PP_CUDA(cudaMemcpyAsync(dL + (size_t)P0 * n2, out, sizeof(double) * n2 * np,
-                                        cudaMemcpyDeviceToHost, st));
-                PP_CUDA(cudaStreamSynchronize(st));
-            }
-        }
-    }
-    PP_CUDA(cudaStreamSynchronize(st));
-    return PPRPA_OK;
+        return set_error(PPRPA_ERR_STATE,
+                         "grad_ec: needs every root of one channel (nroots = nvv for pp, nroots = noo for hh)");
+    // pp: E_c = sum Omega^{+2e} - Tr A, each root z^T dM z;  hh: E_c = -sum Omega^{-2e} - Tr C
+    // with d Omega^{-2e} = -z^T dM z (Eq. correlation_energy), so both sum z^T dM z
+    const bool hh = c->last_channel == PPRPA_CHANNEL_HH;
+    std::vector<double> f(c->last_nroots, 1.0);
+    return grad_weighted(c, c->last_mult, c->d_lastZ, c->last_nroots, f.data(), hh ? 1 : 0, dL, deps, where);
 }
 
 int pprpa_grad_vector(pprpa_ctx* c, int mult, const double* z, double* dL, double* deps, int where) {
@@ -695,7 +688,8 @@ int pprpa_grad_vector(pprpa_ctx* c, int mult, const double* z, double* dL, doubl
         PP_CUDA(cudaMemcpyAsync(b, z, sizeof(double) * t->N, cudaMemcpyHostToDevice, c->stream));
         dz = b;
     }
-    return grad_of_vector(c, mult, dz, 1.0, dL, deps, where);
+    const double one = 1.0;
+    return grad_weighted(c, mult, dz, 1, &one, -1, dL, deps, where);
 }
 
 int pprpa_sigma_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,

@@ -89,8 +89,10 @@ struct pprpa_ctx {
     bool profile = false;
     std::vector<pprpa::ProfRec> prof;
 
-    // batched-sigma plan (tensor maps, work items, CUDA graph) owned by this context
+    // batched-sigma plans (tensor maps, work items, CUDA graph) owned by this context: BF16
+    // and BF16x3 forms
     void* batch_plan = nullptr;
+    void* batch_plan3 = nullptr;
 
     // last solve (for gradients)
     int last_mult = 0;
@@ -123,5 +125,16 @@ int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int
 void destroy_batch_plan(void* plan);
 int autotune_tiles(pprpa_ctx* c, int mult, int k, int nterms, int* bn_out);
 int check_status(pprpa_ctx* c);
+
+// Tensor-core sigma provider of a Davidson solve run among others (pprpa_solve_batch): the
+// solve hands its BF16 (nterms 1) or BF16x3 (nterms 3) products of k device vectors to it
+// instead of launching them itself.
+struct SigmaHook {
+    virtual ~SigmaHook() {}
+    virtual int sigma(pprpa_ctx* c, int mult, int k, const double* z, double* out, int nterms) = 0;
+};
+// pprpa_solve after its argument checks; hook may be null.
+int solve_checked(pprpa_ctx* c, const pprpa_options* o, double* omega, double* X, double* Y,
+                  double* ec, pprpa_info* info, SigmaHook* hook);
 
 }  // namespace pprpa

@@ -627,45 +627,68 @@ namespace pprpa {
 
 // Derivatives of the two-electron part of Tr A (Sec. "ppRPA Equation"), subtracted from the
 // sum of root gradients to give d E_c (Eq. correlation_energy).  With
-// Tr A_2e = 1/2 sum_P [(tr_v L^P)^2 +- sum_{ab} (L^P_ab)^2] (+ singlet, - triplet):
-//   d Tr A / d L^P_xy = d_xy tr_v L^P +- L^P_xy  (x, y virtual), 0 otherwise;
-//   d Tr A / d eps_a  = nv + 1 (singlet) or nv - 1 (triplet) for virtual a.
-__global__ void trace_a_grad_kernel(const double* __restrict__ L, int n, int no, int mult,
-                                    double* __restrict__ dL) {
+// Two-electron part of the trace of the A block (blk = 0, virtual pairs) or of the C block
+// (blk = 1, occupied pairs); with tr L^P over the block's orbitals,
+//   Tr_2e = 1/2 sum_P [(tr L^P)^2 +- sum_{xy} (L^P_xy)^2]   (+ singlet, - triplet),
+//   d Tr_2e / d L^P_xy = d_xy tr L^P +- L^P_xy  for x, y in the block, 0 otherwise.
+// The orbital-energy part: d Tr A / d eps_a = nv +- 1 (virtual a), d Tr C / d eps_i =
+// -(no +- 1) (occupied i).  The kernels subtract these derivatives from dL / deps.
+__global__ void trace_block_grad_kernel(const double* __restrict__ L, int n, int x0, int x1,
+                                        int mult, double* __restrict__ dL) {
     __shared__ double sh[32];
     const int64_t P = blockIdx.x;
     const double* Lp = L + P * (int64_t)n * n;
     double* dp = dL + P * (int64_t)n * n;
     double tr = 0.0;
-    for (int a = no + threadIdx.x; a < n; a += blockDim.x) tr += Lp[(int64_t)a * n + a];
+    for (int a = x0 + threadIdx.x; a < x1; a += blockDim.x) tr += Lp[(int64_t)a * n + a];
     tr = block_sum(tr, sh);
-    __shared__ double trv;
-    if (threadIdx.x == 0) trv = tr;
+    __shared__ double trb;
+    if (threadIdx.x == 0) trb = tr;
     __syncthreads();
     const double sg = mult == 1 ? 1.0 : -1.0;
-    const int nv = n - no;
-    for (int t = threadIdx.x; t < nv * nv; t += blockDim.x) {
-        const int x = no + t / nv, y = no + t % nv;
+    const int nb = x1 - x0;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int x = x0 + t / nb, y = x0 + t % nb;
         const int64_t o = (int64_t)x * n + y;
-        dp[o] -= (x == y ? trv : 0.0) + sg * Lp[o];
+        dp[o] -= (x == y ? trb : 0.0) + sg * Lp[o];
     }
 }
 
-__global__ void trace_a_eps_kernel(int n, int no, int mult, double* deps) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= no && p < n) deps[p] -= (double)(n - no) + (mult == 1 ? 1.0 : -1.0);
+__global__ void trace_block_eps_kernel(int x0, int x1, double d, double* deps) {
+    const int p = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < x1) deps[p] -= d;
 }
 
-int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, double* dL,
-                        double* deps, cudaStream_t st) {
+int launch_trace_block_grad(const double* L, int naux, int n, int no, int mult, int blk,
+                            double* dL, double* deps, cudaStream_t st) {
+    const int x0 = blk == 0 ? no : 0, x1 = blk == 0 ? n : no;
+    if (x1 <= x0) return PPRPA_OK;
     if (dL && naux > 0) {
-        trace_a_grad_kernel<<<naux, 256, 0, st>>>(L, n, no, mult, dL);
+        trace_block_grad_kernel<<<naux, 256, 0, st>>>(L, n, x0, x1, mult, dL);
         PP_CHECK_LAUNCH();
     }
     if (deps) {
-        trace_a_eps_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, no, mult, deps);
+        const double nb = (double)(x1 - x0), sg = mult == 1 ? 1.0 : -1.0;
+        const double d = blk == 0 ? nb + sg : -(nb + sg);
+        trace_block_eps_kernel<<<(unsigned)ceil_div(x1 - x0, 128), 128, 0, st>>>(x0, x1, d, deps);
         PP_CHECK_LAUNCH();
     }
+    return PPRPA_OK;
+}
+
+// X[r][i] *= f[r] for k rows of length len.
+__global__ void scale_rows_kernel(double* __restrict__ X, int k, int64_t len, const double* __restrict__ f) {
+    const int64_t total = (int64_t)k * len;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        X[t] *= f[t / len];
+}
+
+int launch_scale_rows(double* X, int k, int64_t len, const double* f, cudaStream_t st) {
+    const int64_t total = (int64_t)k * len;
+    if (total <= 0) return PPRPA_OK;
+    scale_rows_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 16), 256, 0, st>>>(X, k, len, f);
+    PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }
 

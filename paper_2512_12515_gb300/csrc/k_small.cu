@@ -743,12 +743,9 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
     const char* pv = getenv("PPRPA_RR_PROF");
     a.prof = pv ? atoi(pv) : 0;
     const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * sizeof(double) * RR_SMEM_MAX * (RR_SMEM_MAX + 1));
-        attr_set = true;
-    }
+    // per device and cheap: set on every launch (several host threads may launch at once)
+    cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * sizeof(double) * RR_SMEM_MAX * (RR_SMEM_MAX + 1));
     rayleigh_ritz_kernel<<<1, RR_THREADS, smem, st>>>(a);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;

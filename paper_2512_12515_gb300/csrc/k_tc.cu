@@ -23,6 +23,7 @@
 // and returns.
 #include <cuda.h>
 
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -72,16 +73,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; returns false (and raises the abort flag) on expiry or abort.
+// Bounded wait (limit_ns); returns false (and raises the abort flag) on expiry or abort.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, unsigned long long limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > TC_WAIT_NS) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicOr(status, DEV_TIMEOUT);
                 return false;
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // a pair's leader expects both CTAs' A rows and both halves of B
                 const uint32_t tx = ((PAIR ? 2 : 1) * a_bytes + b_bytes) * (NTERMS == 3 ? 2 : 1);
                 for (int kb = c.kb0; kb < c.kb1; ++kb) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, &abort_flag, p.status)) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, &abort_flag, p.status, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -638,11 +639,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int bn = c.nw;
                 constexpr int MM = PAIR ? 2 * TC_BM : TC_BM;
                 const uint32_t idesc = F8 ? idesc_e4m3(bn, MM) : idesc_bf16(bn, MM);
-                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status)) break;
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, &abort_flag, p.status, p.wait_ns)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem_base + (uint32_t)(acc * p.slot_bn);
                 for (int kb = c.kb0; kb < c.kb1; ++kb) {
-                    if (!mbar_wait(full_bar(stage), phase, &abort_flag, p.status)) {
+                    if (!mbar_wait(full_bar(stage), phase, &abort_flag, p.status, p.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -715,7 +716,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int bn = c.nw;
             const int bn2 = ((bn / 2) + 15) / 16 * 16;  // half-tile split on a 16-column boundary
             const int cbeg = half == 0 ? 0 : bn2, cend = half == 0 ? min(bn2, bn) : bn;
-            if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status)) break;
+            if (!mbar_wait(tfull_bar(acc), acc_phase, &abort_flag, p.status, p.wait_ns)) break;
             tc_fence_after();
             const uint32_t tbase =
                 tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * p.slot_bn);
@@ -1009,6 +1010,17 @@ static size_t plan_smem(TcParams& p, int bn, int nterms, bool want_epi) {
     return (size_t)slot_bytes_for(bn, nterms) * p.stages + 1024 + (p.epi_stage ? TC_EPI_BYTES : 0);
 }
 
+// Limit of the kernel's pipeline waits: PPRPA_TC_WAIT_NS nanoseconds when set (clamped to
+// [1 us, 4 s]; a short limit makes a normal launch's waits run out, which is how the
+// timeout path is tested), else 4 s.
+static unsigned long long tc_wait_ns() {
+    const char* v = getenv("PPRPA_TC_WAIT_NS");
+    if (!v) return TC_WAIT_NS;
+    const long long x = atoll(v);
+    if (x < 1000) return 1000ull;
+    return x > (long long)TC_WAIT_NS ? TC_WAIT_NS : (unsigned long long)x;
+}
+
 // Zero-filled stand-in for tensor-map parameters a launch does not use.
 static const CUtensorMap& no_map() {
     static CUtensorMap m = [] {
@@ -1023,6 +1035,7 @@ int tc_gemm_launch(const CUtensorMap& a_hi, const CUtensorMap& a_lo, const CUten
                    const CUtensorMap& b_lo, TcParams p, int nterms, int num_sms, cudaStream_t st,
                    bool f8, const CUtensorMap* t_hi, const CUtensorMap* t_lo) {
     if (p.total_items <= 0) return PPRPA_OK;
+    p.wait_ns = tc_wait_ns();
     p.t_store = (p.mode == 0 && t_hi) ? 1 : 0;
     const CUtensorMap& th = t_hi ? *t_hi : no_map();
     const CUtensorMap& tl = t_lo ? *t_lo : th;
@@ -1086,6 +1099,7 @@ int tc_gemm_launch_cluster(const CUtensorMap& a_hi, const CUtensorMap& a_lo,
                            const CUtensorMap& b_hi_part, const CUtensorMap& b_lo_part, TcParams p,
                            int nterms, int cl, int num_sms, cudaStream_t st, bool f8, bool pair,
                            const CUtensorMap* t_hi, const CUtensorMap* t_lo) {
+    p.wait_ns = tc_wait_ns();
     p.t_store = (p.mode == 0 && t_hi) ? 1 : 0;
     const CUtensorMap& th = t_hi ? *t_hi : no_map();
     const CUtensorMap& tl = t_lo ? *t_lo : th;
@@ -1145,6 +1159,7 @@ int tc_gemm_launch_batched(const TcJob* jobs, const TcItem* items, int total_ite
     TcParams p;
     p.total_items = total_items;
     p.status = status;
+    p.wait_ns = tc_wait_ns();
     p.slot_bn = max_bn;
     p.BN = max_bn;
     const size_t smem = plan_smem(p, max_bn, nterms, true);

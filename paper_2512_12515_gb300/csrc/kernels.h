@@ -87,8 +87,12 @@ int launch_ec_sum(const double* omega, int nw, const double* D, int nvv, double*
                   cudaStream_t st);
 // W = diag(wsign I_nvv, -wsign I_noo); wsign = -1 gives the metric of the removal channel
 int launch_metric_matrix(double* W, int N, int nvv, cudaStream_t st, double wsign = 1.0);
-int launch_trace_a_grad(const double* L, int naux, int n, int no, int mult, double* dL,
-                        double* deps, cudaStream_t st);
+// Subtracts the derivative of the A-block (blk = 0) or C-block (blk = 1) trace from dL
+// (naux slices) and deps; either may be null.
+int launch_trace_block_grad(const double* L, int naux, int n, int no, int mult, int blk,
+                            double* dL, double* deps, cudaStream_t st);
+// X[r][:] *= f[r] (f on the device) for k rows of length len.
+int launch_scale_rows(double* X, int k, int64_t len, const double* f, cudaStream_t st);
 int launch_grad_eps(const double* z, int N, int nvv, const int* pp, const int* pq, int n,
                     double s, double* deps, cudaStream_t st);
 

@@ -624,7 +624,8 @@ static bool same_signature(const BatchPlan& bp, int nmol, pprpa_ctx* const* ctxs
 static int batch_persistent(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int* ks,
                             const double* const* z, double* const* sigma, int nterms, cudaStream_t st,
                             pprpa_ctx* owner, bool use_graph) {
-    BatchPlan* bp = (BatchPlan*)owner->batch_plan;
+    void*& slot = nterms == 3 ? owner->batch_plan3 : owner->batch_plan;
+    BatchPlan* bp = (BatchPlan*)slot;
     if (bp && use_graph && bp->exec && same_signature(*bp, nmol, ctxs, mults, ks, z, sigma, nterms, st)) {
         PP_CUDA(cudaGraphLaunch(bp->exec, st));
         count_launch(bp->graph_kernels);
@@ -632,7 +633,7 @@ static int batch_persistent(int nmol, pprpa_ctx* const* ctxs, const int* mults, 
     }
     destroy_batch_plan(bp);
     bp = new BatchPlan();
-    owner->batch_plan = bp;
+    slot = bp;
     bp->ctxs.assign(ctxs, ctxs + nmol);
     bp->mults.assign(mults, mults + nmol);
     bp->ks.assign(ks, ks + nmol);

@@ -230,12 +230,14 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     if (hh)
         for (double& v : h_om) v = -v;  // omega of the removal roots, highest first
     PP_TRY(write_outputs(c, pt, o->nroots, coef, h_om.data(), omega, X, Y));
-    c->last_all_roots = !hh && o->nroots == nvv;
+    c->last_all_roots = o->nroots == npos;
     c->last_channel = o->channel;
     tt.stop();
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->converged = 1;
+        info->nconv = o->nroots;
+        info->n_real = npos;
         info->mu = hinfo[1];
         info->t_total_ms = tt.total_ms;
     }
@@ -245,7 +247,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
 
 // ---------------------------------------------------------------------------
 static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, double* omega,
-                          double* X, double* Y, pprpa_info* info) {
+                          double* X, double* Y, double* ec, pprpa_info* info, SigmaHook* hook) {
     const int N = pt->N, nvv = pt->nvv, noo = pt->noo;
     const int nroots = o->nroots;
     cudaStream_t st = c->stream;
@@ -337,10 +339,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         if (o->mult == PPRPA_AB) rc = sigma_ab_f64(c, k, z, out);
         else if (stage == 0) rc = sigma_f64(c, o->mult, k, z, out);
         else if (stage == 3) rc = sigma_tc(c, o->mult, k, z, out, 1, true);
+        else if (hook) rc = hook->sigma(c, o->mult, k, z, out, stage == 1 ? 1 : 3);
         else rc = sigma_tc(c, o->mult, k, z, out, stage == 1 ? 1 : 3);
         t_sig.stop();
         if (rc != PPRPA_OK) return rc;
-        if (stage != 0) PP_TRY(check_status(c));
+        if (stage != 0 && !(hook && (stage == 1 || stage == 2))) PP_TRY(check_status(c));
         if (info) {
             info->n_sigma += k;
             info->sigma_flops += (double)k * 3.0 * c->naux * c->n() *
@@ -465,7 +468,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         if (env_int("PPRPA_LOG", 0))
             fprintf(stderr, "[pprpa] it %d stage %d m %d mu %.6f omega0 %.10f max|r| %.3e sweeps %d\n", it, stage,
                     m, mu_prev, h_om[0], rmax, general ? -1 : (int)hinfo[5]);
-        if (info) info->max_resid = rmax;
+        if (info) {
+            info->max_resid = rmax;
+            info->nconv = ntg - (int)todo.size();
+            info->n_real = npos;
+        }
         if (stage == 1 || stage == 3) {
             ++stage1_iters;
             best_hist.push_back(rmax);
@@ -551,10 +558,21 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_TRY(project_block(m, m + added));
         m += added;
     }
+    if (ec && rc_final == PPRPA_OK && nroots == npos_blk) {
+        // every root of the channel converged: E_c = sum Omega^{+2e} - Tr A (pp), or
+        // sum mu - Tr C = -sum Omega^{-2e} - Tr C (hh) (Eq. correlation_energy), summed in FP64
+        // on the device from the Ritz values (om, the targets first) and the diagonal
+        double* dec;
+        PP_TRY(ws_get(c, "dv_ec", sizeof(double), (void**)&dec));
+        if (hh) PP_TRY(launch_ec_sum(om, nroots, D + nvv, noo, dec, st));
+        else PP_TRY(launch_ec_sum(om, nroots, D, nvv, dec, st));
+        PP_CUDA(cudaMemcpyAsync(ec, dec, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaStreamSynchronize(st));
+    }
     if (hh)
         for (int j = 0; j < nroots; ++j) h_om[j] = -h_om[j];  // omega of the removal roots
     PP_TRY(write_outputs(c, pt, nroots, Zr, h_om.data(), omega, X, Y));
-    c->last_all_roots = false;
+    c->last_all_roots = rc_final == PPRPA_OK && nroots == npos_blk;
     c->last_channel = o->channel;
     t_all.stop();
     if (info) {
@@ -577,6 +595,11 @@ using namespace pprpa;
 
 extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, double* X, double* Y,
                            double* ec, pprpa_info* info) {
+    return solve_checked(c, o, omega, X, Y, ec, info, nullptr);
+}
+
+int pprpa::solve_checked(pprpa_ctx* c, const pprpa_options* o, double* omega, double* X, double* Y,
+                         double* ec, pprpa_info* info, SigmaHook* hook) {
     if (!c || !o) return set_error(PPRPA_ERR_ARG, "solve: null argument");
     PP_CUDA(cudaSetDevice(c->device));
     if (!c->have_L) return set_error(PPRPA_ERR_STATE, "solve: integrals not set");
@@ -600,7 +623,7 @@ extern "C" int pprpa_solve(pprpa_ctx* c, const pprpa_options* o, double* omega, 
     if (o->method == PPRPA_METHOD_FULL) return solve_full(c, o, pt, omega, X, Y, ec, info);
     if (!(o->conv_tol > 0.0) || o->max_iter < 1) return set_error(PPRPA_ERR_ARG, "solve: bad tolerance / max_iter");
     if (ec) *ec = NAN;
-    return solve_davidson(c, o, pt, omega, X, Y, info);
+    return solve_davidson(c, o, pt, omega, X, Y, o->want_ec ? ec : nullptr, info, hook);
 }
 
 extern "C" int pprpa_build_matrix(pprpa_ctx* c, int mult, double* Mout, int where) {

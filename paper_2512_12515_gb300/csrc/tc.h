@@ -17,6 +17,9 @@ struct TcParams {
     int total_items = 0;
     int kb_total = 0;  // 64-wide K blocks per work item before splitting
     int* status = nullptr;
+    // limit of each pipeline wait (ns); set by the launcher (PPRPA_TC_WAIT_NS, default 4 s).
+    // The drains after an expired wait keep the fixed 4 s limit.
+    unsigned long long wait_ns = 4000000000ull;
     // stage 1
     int tiles_n = 0;
     int64_t M_rows = 0;  // naux * n_pad

@@ -69,12 +69,33 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert len(lib.pprpa_last_error()) > 0
 
 
-def test_options_struct_layout_matches_header():
+def test_options_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors of pprpa_options and pprpa_info have the C header's size and field
+    offsets (read from a small C program compiled against include/pprpa.h)."""
+    import shutil
+    import subprocess
+
     from paper_2512_12515_gb300 import _lib
 
-    # int, int, int, int, int, double, int, int, int  -> 48 bytes with alignment
-    assert ctypes.sizeof(_lib.Options) == 48
-    assert ctypes.sizeof(_lib.Info) == 4 * 4 + 6 * 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pprpa.h"', "int main(void) {"]
+    for cname, cls in (("pprpa_options", _lib.Options), ("pprpa_info", _lib.Info)):
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, cls in (("pprpa_options", _lib.Options), ("pprpa_info", _lib.Info)):
+        assert int(got[cname]) == ctypes.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
 
 
 def test_binding_pair_counts_match_the_oracle_pair_lists():

@@ -76,7 +76,9 @@ def test_sigma_sampled_rows_full_size(pp, name, mult):
     err48 = np.abs(out["split"] - ref).max()
     print(f"{name} mult {mult}: scale {scale:.3e} err fp64 {err64:.3e} bf16 {err16:.3e} split {err48:.3e}")
     assert err64 <= 1e-10 * max(1.0, scale)
-    assert err16 <= 2e-2 * scale
+    # BF16: unit roundoff u = 2^-8, about u of the two-electron scale in a CPU emulation of
+    # the same arithmetic; bound 2u (the reasoning beside check_bf16 in test_gpu_parity.py)
+    assert err16 <= 2.0 * 2.0 ** -8 * scale
     # BF16x3 drops the lo*lo product (2^-16 ~ 1.5e-5 relative) and accumulates at most
     # two auxiliary slices per tensor-memory accumulator before the FP32 partial sums
     assert err48 <= 3e-5 * scale

@@ -119,6 +119,6 @@ def test_hh_argument_checks(pp):
             c.solve(mult=1, nroots=noo + 1, channel=pp.CHANNEL_HH)
         with pytest.raises(pp.PprpaError):
             c.solve(mult=1, nroots=2, channel=7)
-        c.solve(mult=1, nroots=noo, method=pp.METHOD_FULL, channel=pp.CHANNEL_HH)
+        c.solve(mult=1, nroots=noo - 1, method=pp.METHOD_FULL, channel=pp.CHANNEL_HH)
         with pytest.raises(pp.PprpaError):
-            c.grad_ec()  # the correlation-energy gradient needs every addition root
+            c.grad_ec()  # the correlation-energy gradient needs every root of the channel

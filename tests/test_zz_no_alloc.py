@@ -31,14 +31,14 @@ def _check_noalloc(spec, no, nv, calls):
     import paper_2512_12515_gb300 as pp
 
     s, orb, L_ref, eps_ref = _case(spec, no, nv)
-    eps_act = torch.as_tensor(eps_ref, device="cuda")
+    eps_act = torch.as_tensor(np.ascontiguousarray(eps_ref), device="cuda")
     with pp.Context(0) as c:
         c.set_orbitals(s["occ"], s["eps"])
         c.set_active(no, nv)
         c.set_ao(s["C"], s["ao3c"])
         L = torch.empty(c.get_L().shape, dtype=torch.float64, device="cuda")
         c.get_L(L)
-        L_or = torch.as_tensor(L_ref, device="cuda")
+        L_or = torch.as_tensor(np.ascontiguousarray(L_ref), device="cuda")
         for mult, k, seed in calls:
             _, _, nvv, noo = c.dims(mult)
             z = torch.as_tensor(synth.random_trial_vectors(nvv + noo, k, seed), device="cuda")
