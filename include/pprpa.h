@@ -47,7 +47,8 @@ extern "C" {
 #define PPRPA_ERR_CUDA (-2)     /* a CUDA runtime call failed */
 #define PPRPA_ERR_OOM (-3)      /* device allocation failed */
 #define PPRPA_ERR_NOCONV (-4)   /* Davidson hit max_iter; outputs hold the last iterate */
-#define PPRPA_ERR_UNSTABLE (-5) /* no shift makes M - mu W positive definite */
+#define PPRPA_ERR_UNSTABLE (-5) /* no shift makes M - mu W positive definite, and (Davidson) the
+                                   lowest roots are interleaved with complex pairs */
 #define PPRPA_ERR_TIMEOUT (-6)  /* a device-side bounded wait expired */
 #define PPRPA_ERR_STATE (-7)    /* required data not set yet (e.g. no integrals) */
 #define PPRPA_ERR_UNSUPPORTED (-8) /* the GPU lacks sm_103a features */
@@ -84,6 +85,9 @@ typedef struct pprpa_options {
                           below 8192 pairs while the shifted pencil is definite */
     int want_ec;       /* also return the correlation energy: FULL, or Davidson asked for every
                           root of its channel (nroots = nvv for pp, noo for hh) */
+    int require_definite; /* Davidson: 1 = return PPRPA_ERR_UNSTABLE as soon as the subspace
+                          pencil has no definite shift (the stability test of a screen), instead
+                          of continuing with the general subspace solver; 0 = default */
 } pprpa_options;
 
 typedef struct pprpa_info {
@@ -93,7 +97,8 @@ typedef struct pprpa_info {
     int converged;        /* 1 if every root met conv_tol */
     double max_resid;     /* largest residual norm of the returned roots */
     double mu;            /* shift used by the last Rayleigh-Ritz step */
-    double max_imag;      /* FULL: not computed (0); reserved */
+    double max_imag;      /* Davidson: largest |Im| of complex Ritz values below the highest
+                             target at the last iteration (0 if none); FULL: 0 */
     double t_sigma_ms;    /* device time in sigma (CUDA events) */
     double t_total_ms;    /* device time of the whole solve */
     double sigma_flops;   /* algorithmic sigma flops 3*naux*n*(nv^2+no^2) per vector, summed */
@@ -269,7 +274,14 @@ int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int naux, const do
  * info may be NULL.
  * Host output pointers.  Returns PPRPA_ERR_NOCONV (outputs filled with the
  * last iterate) or PPRPA_ERR_UNSTABLE when no positive-definite shift
- * exists.  The converged eigenvectors stay on the device for pprpa_grad. */
+ * exists and the roots cannot be separated: FULL when the root count by norm fails;
+ * Davidson when its subspace pencil has no definite shift, complex Ritz pairs lie below the
+ * highest target in at least half of the last PPRPA_UNSTABLE_WINDOW (default 40) iterations
+ * and the largest residual has not dropped tenfold over them (outputs hold the last iterate,
+ * info->max_imag the largest imaginary part below the targets), or at once when
+ * opts->require_definite is set.  Lowest real roots isolated below any
+ * complex pairs still converge through the general (non-symmetric) subspace solver.
+ * The converged eigenvectors stay on the device for pprpa_grad. */
 int pprpa_solve(pprpa_ctx* ctx, const pprpa_options* opts, double* omega, double* X,
                 double* Y, double* ec, pprpa_info* info);
 

@@ -79,4 +79,6 @@ from .brute import (  # noqa: F401
     mp2_pair_energy,
 )
 from .davidson_ref import ri_sigma, ri_sigma_rows, davidson  # noqa: F401
-from .stability import matrix_rows, explicit_matrix_ri, shifted_lambda_min, roots_near  # noqa: F401
+from .stability import (  # noqa: F401
+    matrix_rows, explicit_matrix_ri, shifted_lambda_min, roots_near, block_shift_window,
+    classified_spectrum)

@@ -102,3 +102,76 @@ def roots_near(M, nvv, noo, sigma, k=20):
         np.einsum("ik,ik->k", vecs.conj(), vecs))
     order = np.argsort(vals.real)
     return vals[order], metric[order]
+
+
+def block_shift_window(eps_act, nocc_act, L_act, mult, steps=40, seed=0):
+    """Necessary condition for a definite shift, from the diagonal blocks alone.
+
+    M - mu W positive definite needs its diagonal blocks A - mu I and C + mu I positive
+    definite, i.e. -lambda_min(C) < mu < lambda_min(A).  lambda_min(C) is taken from the
+    explicit occupied-pair block (``matrix_rows``); lambda_min(A) is bounded from above by
+    the lowest Ritz value of ``steps`` Lanczos steps on A, applied through the
+    density-fitted sigma with a zero occupied part (``ri_sigma``, virtual-pair rows).  If
+    that upper bound lies below -lambda_min(C), no shift is definite and the pencil is
+    proven indefinite.  Returns a dict with ``theta_A`` (>= lambda_min(A)),
+    ``lambda_min_C``, ``window`` = theta_A + lambda_min(C) and ``proven_indefinite``.
+    """
+    from .davidson_ref import ri_sigma
+
+    eps = np.asarray(eps_act, dtype=np.float64)
+    n = eps.shape[0]
+    _, _, nvv, noo = _pairs_all(n, nocc_act, mult)
+    N = nvv + noo
+    if noo:
+        Crows = matrix_rows(eps_act, nocc_act, L_act, mult, np.arange(nvv, N))
+        lam_c = float(np.linalg.eigvalsh(Crows[:, nvv:])[0])
+        del Crows
+    else:
+        lam_c = np.inf
+
+    def a_mul(x):
+        z = np.zeros(N)
+        z[:nvv] = x
+        return ri_sigma(eps_act, nocc_act, L_act, mult, z[None, :])[0, :nvv]
+
+    # plain Lanczos with full reorthogonalisation; the lowest Ritz value bounds lambda_min(A)
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal(nvv)
+    q /= np.linalg.norm(q)
+    Q = [q]
+    alpha, beta = [], []
+    for j in range(min(steps, nvv)):
+        w = a_mul(Q[-1])
+        alpha.append(float(Q[-1] @ w))
+        for v in Q:
+            w -= (v @ w) * v
+        b = float(np.linalg.norm(w))
+        if j + 1 == min(steps, nvv) or b < 1e-12:
+            break
+        beta.append(b)
+        Q.append(w / b)
+    T = np.diag(alpha) + np.diag(beta[:len(alpha) - 1], 1) + np.diag(beta[:len(alpha) - 1], -1)
+    theta = float(np.linalg.eigvalsh(T)[0])
+    window = theta + lam_c
+    return {"theta_A": theta, "lambda_min_C": lam_c, "window": window,
+            "proven_indefinite": bool(window < 0.0), "lanczos_steps": len(alpha)}
+
+
+def classified_spectrum(M, nvv, noo, imag_tol=1e-9):
+    """Every root of M z = omega W z (dense), sorted into the three kinds of Eq. xy_norm's
+    reading: real addition roots (z^T W z > 0), real removal roots (< 0), and complex
+    values (|Im| > imag_tol times the spectral scale; they come in conjugate pairs and their
+    eigenvectors have z^H W z = 0).  Returns ``(addition ascending, removal ascending,
+    complex (sorted by real part))``."""
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    vals, vecs = sla.eig(w[:, None] * M)
+    scale = max(1.0, float(np.max(np.abs(vals)))) if vals.size else 1.0
+    cplx = np.abs(vals.imag) > imag_tol * scale
+    real = ~cplx
+    v = vecs[:, real].real
+    metric = np.einsum("ik,i,ik->k", v, w, v)
+    r = vals[real].real
+    add = np.sort(r[metric > 0])
+    rem = np.sort(r[metric < 0])
+    c = vals[cplx]
+    return add, rem, c[np.argsort(c.real)]

@@ -39,6 +39,7 @@ class Options(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("max_subspace", ctypes.c_int),
         ("want_ec", ctypes.c_int),
+        ("require_definite", ctypes.c_int),
     ]
 
 
@@ -197,7 +198,7 @@ def sigma_batch(contexts, mults, zs, outs, precision=PREC_BF16, graph=True):
 
 
 def solve_batch(contexts, mults, nroots, precision=PREC_BF16, conv_tol=1e-5, max_iter=200,
-                channel=CHANNEL_PP, max_subspace=0):
+                channel=CHANNEL_PP, max_subspace=0, require_definite=False):
     """pprpa_solve_batch over several contexts (one molecule each, one device).
 
     mults / nroots: one entry per molecule (or a single value for all).  Returns a list of
@@ -211,7 +212,7 @@ def solve_batch(contexts, mults, nroots, precision=PREC_BF16, conv_tol=1e-5, max
     for m, c in enumerate(contexts):
         _, _, nvv, noo = c.dims(mults[m])
         opts[m] = Options(int(mults[m]), int(channel), METHOD_DAVIDSON, int(precision), int(nroots[m]),
-                          float(conv_tol), int(max_iter), int(max_subspace), 0)
+                          float(conv_tol), int(max_iter), int(max_subspace), 0, int(require_definite))
         om.append(np.empty(nroots[m]))
         Xs.append(np.empty((nroots[m], nvv)))
         Ys.append(np.empty((nroots[m], max(noo, 1))))
@@ -386,12 +387,12 @@ class Context:
     # ---- solve / gradient ----
     def solve(self, mult=SINGLET, nroots=10, method=METHOD_DAVIDSON, precision=PREC_FP64,
               conv_tol=1e-6, max_iter=200, max_subspace=0, want_ec=False, raise_noconv=True,
-              channel=CHANNEL_PP):
+              channel=CHANNEL_PP, require_definite=False):
         """pp channel: the lowest N+2 roots, ascending, X^T X - Y^T Y = +1.
         hh channel: the highest N-2 roots, descending, X^T X - Y^T Y = -1."""
         _, _, nvv, noo = self.dims(mult)
         o = Options(mult, channel, method, precision, nroots, conv_tol, max_iter, max_subspace,
-                    int(want_ec))
+                    int(want_ec), int(require_definite))
         omega = np.empty(nroots)
         X = np.empty((nroots, nvv))
         Y = np.empty((nroots, max(noo, 1)))
@@ -400,9 +401,14 @@ class Context:
         rc = self.lib.pprpa_solve(self._h, ctypes.byref(o), omega.ctypes.data, X.ctypes.data,
                                   Y.ctypes.data, ec.ctypes.data if want_ec else None,
                                   ctypes.byref(info))
-        if rc in (OK, ERR_NOCONV):  # the library now holds this solve's vectors
-            self._last_mult = mult
-        if rc != OK and not (rc == ERR_NOCONV and not raise_noconv):
+        # a Davidson solve that stopped without converging (max_iter, or lowest roots
+        # interleaved with complex pairs: UNSTABLE after some iterations) returns its last
+        # iterate; raise_noconv=False hands it back instead of raising
+        stopped = rc == ERR_NOCONV or (rc == ERR_UNSTABLE and method == METHOD_DAVIDSON
+                                       and info.iters > 0)
+        if rc == OK or stopped:
+            self._last_mult = mult  # the library now holds this solve's vectors
+        if rc != OK and not (stopped and not raise_noconv):
             _check(rc)
         return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
                 "info": info.as_dict(), "rc": rc}

@@ -18,6 +18,17 @@ int set_error(int code, const std::string& msg) {
 
 void count_launch(long long n) { g_launches += n; }
 
+int ctx_sync(pprpa_ctx* c) {
+    if (!c->blocking_sync) {
+        PP_CUDA(cudaStreamSynchronize(c->stream));
+        return PPRPA_OK;
+    }
+    if (!c->sync_ev) PP_CUDA(cudaEventCreateWithFlags(&c->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+    PP_CUDA(cudaEventRecord(c->sync_ev, c->stream));
+    PP_CUDA(cudaEventSynchronize(c->sync_ev));
+    return PPRPA_OK;
+}
+
 static int check_ctx(pprpa_ctx* c) {
     if (!c) return set_error(PPRPA_ERR_ARG, "null context");
     cudaError_t e = cudaSetDevice(c->device);
@@ -212,6 +223,7 @@ void pprpa_destroy(pprpa_ctx* c) {
     }
     destroy_batch_plan(c->batch_plan);
     destroy_batch_plan(c->batch_plan3);
+    if (c->sync_ev) cudaEventDestroy(c->sync_ev);
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -103,6 +103,12 @@ struct pprpa_ctx {
     double* d_lastZ = nullptr;
 
     int n() const { return no + nv; }
+
+    // host waits on this context's stream: spin (cudaStreamSynchronize, lowest latency) or,
+    // when many host threads each drive a context (pprpa_solve_batch), block on an event
+    // created with cudaEventBlockingSync so that waiting threads do not occupy host cores
+    bool blocking_sync = false;
+    cudaEvent_t sync_ev = nullptr;
 };
 
 namespace pprpa {
@@ -125,6 +131,8 @@ int sigma_tc_batch(int nmol, pprpa_ctx* const* ctxs, const int* mults, const int
 void destroy_batch_plan(void* plan);
 int autotune_tiles(pprpa_ctx* c, int mult, int k, int nterms, int* bn_out);
 int check_status(pprpa_ctx* c);
+// Waits for the context's stream (see pprpa_ctx::blocking_sync).
+int ctx_sync(pprpa_ctx* c);
 
 // Tensor-core sigma provider of a Davidson solve run among others (pprpa_solve_batch): the
 // solve hands its BF16 (nterms 1) or BF16x3 (nterms 3) products of k device vectors to it

@@ -155,16 +155,32 @@ int dgemm(const Dgemm& gin, cudaStream_t st) {
         dgemm_scale_c_kernel<<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 8), 256, 0, st>>>(g);
         PP_CHECK_LAUNCH();
     }
-    const int64_t zb = (int64_t)g.nb1 * g.nb2 * g.splitk * g.rsplit;
-    if (zb > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: too many batches");
     if (g.K <= 0 || g.nr <= 0) {
         // C = beta * C
         if (g.splitk > 1) return PPRPA_OK;
     }
-    dim3 grid((unsigned)ceil_div(g.N, DG_BN), (unsigned)ceil_div(g.M, DG_BM), (unsigned)zb);
-    if (grid.y > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: M too large");
-    dgemm_kernel<<<grid, 256, 0, st>>>(g);
-    PP_CHECK_LAUNCH();
+    if (ceil_div(g.M, DG_BM) > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: M too large");
+    // the grid's z dimension (at most 65535) covers batches x K slices x reduction slices:
+    // launch the batches in as many pieces as that needs
+    const int64_t per_b = (int64_t)g.splitk * g.rsplit;
+    if (per_b > 65535) return set_error(PPRPA_ERR_ARG, "dgemm: too many K / reduction slices");
+    const int c2 = (int)std::min<int64_t>(g.nb2, 65535 / per_b);
+    for (int b2 = 0; b2 < g.nb2; b2 += c2) {
+        const int n2c = std::min(c2, g.nb2 - b2);
+        const int c1 = (int)std::max<int64_t>(1, std::min<int64_t>(g.nb1, 65535 / (per_b * n2c)));
+        for (int b1 = 0; b1 < g.nb1; b1 += c1) {
+            Dgemm p = g;
+            p.nb1 = std::min(c1, g.nb1 - b1);
+            p.nb2 = n2c;
+            p.A = g.A + b1 * g.sA1 + b2 * g.sA2;
+            p.B = g.B + b1 * g.sB1 + b2 * g.sB2;
+            p.C = g.C + b1 * g.sC1 + b2 * g.sC2;
+            const int64_t zb = (int64_t)p.nb1 * p.nb2 * per_b;
+            dim3 grid((unsigned)ceil_div(g.N, DG_BN), (unsigned)ceil_div(g.M, DG_BM), (unsigned)zb);
+            dgemm_kernel<<<grid, 256, 0, st>>>(p);
+            PP_CHECK_LAUNCH();
+        }
+    }
     return PPRPA_OK;
 }
 

@@ -78,9 +78,6 @@ extern "C" int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int nau
         return set_error(PPRPA_ERR_ARG, "sigma_noalloc: bad sizes");
     if (k == 0) return PPRPA_OK;
     if (!L || !eps || !z || !sigma) return set_error(PPRPA_ERR_ARG, "sigma_noalloc: null pointer");
-    // one FP64 GEMM launch covers (auxiliary slices of a pass) x k products in its grid's
-    // z dimension, at most 65535
-    if (k > 65535) return set_error(PPRPA_ERR_ARG, "sigma_noalloc: k > 65535 vectors per call");
     const int no = nocc_act, nv = nvir_act, n = no + nv;
     const int tri = mult == 1 ? 0 : 1;
     const int64_t nvv = (int64_t)nv * (nv + 1) / 2 - (int64_t)tri * nv;
@@ -104,10 +101,9 @@ extern "C" int pprpa_sigma_noalloc(int mult, int nocc_act, int nvir_act, int nau
     double* Zt = (double*)(base + 2 * b_pairs);
     double* O = (double*)(base + 2 * b_pairs + b_mat);
     double* T = (double*)(base + fixed);
-    // auxiliary slices per pass: as many products as the scratch holds, and few enough that
-    // the batched T = L^P Zt launch (pc * k products) stays within the grid limit
-    int pc = (int)std::min<int64_t>(naux, (int64_t)((kNoAllocScratchBytes - fixed) / b_mat));
-    pc = std::min(pc, std::max(1, 65535 / k));
+    // auxiliary slices per pass: as many products as the scratch holds (the batched GEMM
+    // launches split themselves where pc * k products exceed one grid)
+    const int pc = (int)std::min<int64_t>(naux, (int64_t)((kNoAllocScratchBytes - fixed) / b_mat));
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     noalloc_pairs_kernel<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(no, nv, mult, (int)nvv, pp, pq);

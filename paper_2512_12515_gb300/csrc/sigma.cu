@@ -37,7 +37,7 @@ int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out) {
 int check_status(pprpa_ctx* c) {
     int st = 0;
     PP_CUDA(cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    PP_CUDA(cudaStreamSynchronize(c->stream));
+    PP_TRY(ctx_sync(c));
     if (st & DEV_TIMEOUT) {
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
         return set_error(PPRPA_ERR_TIMEOUT, "device-side wait expired in the tensor-core GEMM");

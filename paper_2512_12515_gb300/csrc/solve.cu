@@ -30,9 +30,9 @@ struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
     double total_ms = 0.0;
     cudaStream_t st;
-    explicit Timer(cudaStream_t s) : st(s) {
+    explicit Timer(cudaStream_t s, bool blocking = false) : st(s) {
         cudaEventCreate(&a);
-        cudaEventCreate(&b);
+        cudaEventCreateWithFlags(&b, blocking ? cudaEventBlockingSync : cudaEventDefault);
     }
     ~Timer() {
         if (a) cudaEventDestroy(a);
@@ -93,7 +93,7 @@ int write_outputs(pprpa_ctx* c, PairTable* pt, int nroots, const double* d_Z, co
     const int N = pt->N;
     std::vector<double> Z((size_t)nroots * N);
     PP_CUDA(cudaMemcpyAsync(Z.data(), d_Z, sizeof(double) * Z.size(), cudaMemcpyDeviceToHost, c->stream));
-    PP_CUDA(cudaStreamSynchronize(c->stream));
+    PP_TRY(ctx_sync(c));
     for (int j = 0; j < nroots; ++j) {
         fix_phase(Z.data() + (size_t)j * N, N);
         if (omega) omega[j] = h_omega[j];
@@ -106,7 +106,7 @@ int write_outputs(pprpa_ctx* c, PairTable* pt, int nroots, const double* d_Z, co
     c->d_lastZ = nullptr;
     PP_CUDA(cudaMalloc(&c->d_lastZ, sizeof(double) * Z.size()));
     PP_CUDA(cudaMemcpyAsync(c->d_lastZ, Z.data(), sizeof(double) * Z.size(), cudaMemcpyHostToDevice, c->stream));
-    PP_CUDA(cudaStreamSynchronize(c->stream));
+    PP_TRY(ctx_sync(c));
     c->last_nroots = nroots;
     c->last_N = N;
     return PPRPA_OK;
@@ -159,7 +159,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     const int N = pt->N, nvv = pt->nvv, n = c->n();
     cudaStream_t st = c->stream;
     if (N > 1024) return set_error(PPRPA_ERR_ARG, "full diagonalisation is limited to N <= 1024 pairs; use Davidson");
-    Timer tt(st);
+    Timer tt(st, c->blocking_sync);
     tt.start();
     const int64_t n2 = (int64_t)n * n;
     double *eri, *M, *W, *work, *om, *coef, *rinfo, *D, *dwork, *mus, *dec;
@@ -187,7 +187,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     else PP_TRY(launch_diag(c->d_L, c->naux, n, c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-    PP_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(ctx_sync(c));
     // gap edges of the solved pencil from the diagonal: its positive-norm block (vv, or oo
     // for hh) starts near min D there, its negative-norm block ends near max(-D)
     double hi = 1e300, lo = -1e300;
@@ -212,7 +212,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
     PP_TRY(launch_rayleigh_ritz(a, st));
     double hinfo[8];
     PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
-    PP_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(ctx_sync(c));
     if ((int)hinfo[0] == DEV_NOTPD)
         return set_error(PPRPA_ERR_UNSTABLE, "full: no shift makes M - mu W positive definite");
     if ((int)hinfo[2] != npos)
@@ -226,7 +226,7 @@ static int solve_full(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, doubl
         else PP_TRY(launch_ec_sum(om, nvv, D, nvv, dec, st));
         PP_CUDA(cudaMemcpyAsync(ec, dec, sizeof(double), cudaMemcpyDeviceToHost, st));
     }
-    PP_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(ctx_sync(c));
     if (hh)
         for (double& v : h_om) v = -v;  // omega of the removal roots, highest first
     PP_TRY(write_outputs(c, pt, o->nroots, coef, h_om.data(), omega, X, Y));
@@ -272,7 +272,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     // outweighs the few extra sigma products; the general path keeps the full cap
     const int m_soft = (o->max_subspace > 0 || N >= 8192) ? m_max : std::min(m_max, std::max(72, nkeep + nroots));
     const int max_new = nroots;
-    Timer t_all(st), t_sig(st);
+    Timer t_all(st, c->blocking_sync), t_sig(st, c->blocking_sync);
     t_all.start();
 
     double *V, *Sg, *G, *S, *D, *dwork, *R, *Zr, *SZ, *Dn, *Dn2, *H, *rwork, *om, *coef, *rinfo,
@@ -312,7 +312,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     else PP_TRY(launch_diag(c->d_L, c->naux, c->n(), c->d_eps, pt->d_pp, pt->d_pq, nvv, N, o->mult, D, dwork, st));
     std::vector<double> hD(N);
     PP_CUDA(cudaMemcpyAsync(hD.data(), D, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-    PP_CUDA(cudaStreamSynchronize(st));
+    PP_TRY(ctx_sync(c));
     std::vector<int> order(npos_blk);
     std::iota(order.begin(), order.end(), pos0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hD[a] < hD[b]; });
@@ -396,6 +396,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     std::vector<double> h_om(m_max), h_nrm(nroots), best_hist;
     int rc_final = PPRPA_ERR_NOCONV;
     int it = 0, stage1_iters = 0;
+    // iterations of persistent complex pairs below the targets without a tenfold residual drop
+    // after which the solve reports the problem as unstable (PPRPA_UNSTABLE_WINDOW)
+    const int unstable_win = std::max(1, env_int("PPRPA_UNSTABLE_WINDOW", 40));
+    std::vector<int> cplx_hist;
+    std::vector<double> gen_hist;
     double hinfo[8] = {0};
     for (it = 1; it <= o->max_iter; ++it) {
         // ---- Rayleigh-Ritz: shifted symmetric reduction while the pencil is definite,
@@ -417,8 +422,12 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             a.work = rwork; a.omega = om; a.coef = coef; a.info = rinfo;
             PP_TRY(launch_rayleigh_ritz(a, st));
             PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
-            PP_CUDA(cudaStreamSynchronize(st));
+            PP_TRY(ctx_sync(c));
             if ((int)hinfo[0] == DEV_NOTPD) {
+                if (o->require_definite) {
+                    if (info) info->iters = it;
+                    return set_error(PPRPA_ERR_UNSTABLE, "Davidson: the subspace pencil has no definite shift");
+                }
                 if (m > 128) return set_error(PPRPA_ERR_UNSTABLE, "Davidson: no definite shift and subspace > 128");
                 general = true;
                 if (env_int("PPRPA_LOG", 0)) fprintf(stderr, "[pprpa] no definite shift: general Rayleigh-Ritz\n");
@@ -437,7 +446,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             g.work = rwork; g.omega = om; g.coef = coef; g.info = rinfo;
             PP_TRY(launch_rr_general(g, st));
             PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
-            PP_CUDA(cudaStreamSynchronize(st));
+            PP_TRY(ctx_sync(c));
             if ((int)hinfo[0] == DEV_NOTPD)
                 return set_error(PPRPA_ERR_UNSTABLE, "Davidson: subspace eigenvalue iteration failed");
             npos = (int)hinfo[2];
@@ -446,7 +455,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             return set_error(PPRPA_ERR_UNSTABLE, "Davidson: the subspace holds no real addition root");
         const int ntg = std::min(npos, nroots);  // targets this iteration
         PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * std::min(npos, nk_req), cudaMemcpyDeviceToHost, st));
-        PP_CUDA(cudaStreamSynchronize(st));
+        PP_TRY(ctx_sync(c));
         const int nk_avail = std::min(npos, nk_req);
         // complex Ritz values below the highest target: complex roots among the lowest
         if (general) max_imag_below = (hinfo[6] < h_om[ntg - 1]) ? hinfo[7] : 0.0;
@@ -456,7 +465,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * ntg, st));
         PP_TRY(launch_residual(SZ, Zr, om, ntg, N, nvv, R, nrm, st, ws));
         PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * ntg, cudaMemcpyDeviceToHost, st));
-        PP_CUDA(cudaStreamSynchronize(st));
+        PP_TRY(ctx_sync(c));
         double rmax = 0.0;
         std::vector<int> todo;
         for (int j = 0; j < ntg; ++j) {
@@ -472,6 +481,26 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             info->max_resid = rmax;
             info->nconv = ntg - (int)todo.size();
             info->n_real = npos;
+            info->max_imag = max_imag_below;
+        }
+        if (general) {
+            // complex Ritz pairs below the highest target in at least half of the last
+            // unstable_win iterations while the residual has not dropped tenfold over them: the
+            // lowest roots are interleaved with complex pairs (no definite shift), where a
+            // Davidson iteration on the real Ritz values does not settle
+            gen_hist.push_back(rmax);
+            cplx_hist.push_back(max_imag_below > 0.0 ? 1 : 0);
+            const int nh = (int)gen_hist.size();
+            if (nh >= unstable_win) {
+                int with_cplx = 0;
+                for (int t = nh - unstable_win; t < nh; ++t) with_cplx += cplx_hist[t];
+                const double then = gen_hist[nh - unstable_win];
+                const double best = *std::min_element(gen_hist.end() - unstable_win, gen_hist.end());
+                if (2 * with_cplx >= unstable_win && best > 0.1 * then) {
+                    rc_final = PPRPA_ERR_UNSTABLE;
+                    break;
+                }
+            }
         }
         if (stage == 1 || stage == 3) {
             ++stage1_iters;
@@ -524,7 +553,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
         PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
         PP_CUDA(cudaMemcpyAsync(n_after.data(), nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
-        PP_CUDA(cudaStreamSynchronize(st));
+        PP_TRY(ctx_sync(c));
         std::vector<int> live;
         for (int t = 0; t < kn; ++t)
             if (n_after[t] > 1e-20 * std::max(n_before[t], 1e-300)) live.push_back(t);
@@ -543,7 +572,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             PP_CUDA(cudaMemcpyAsync(Dn2, Dn, sizeof(double) * (size_t)kl * N, cudaMemcpyDeviceToDevice, st));
             std::vector<int> kp(kl);
             PP_CUDA(cudaMemcpyAsync(kp.data(), keep, sizeof(int) * kl, cudaMemcpyDeviceToHost, st));
-            PP_CUDA(cudaStreamSynchronize(st));
+            PP_TRY(ctx_sync(c));
             for (int t = 0; t < kl; ++t) hkeep[t] &= kp[t];
         }
         int added = 0;
@@ -567,7 +596,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         if (hh) PP_TRY(launch_ec_sum(om, nroots, D + nvv, noo, dec, st));
         else PP_TRY(launch_ec_sum(om, nroots, D, nvv, dec, st));
         PP_CUDA(cudaMemcpyAsync(ec, dec, sizeof(double), cudaMemcpyDeviceToHost, st));
-        PP_CUDA(cudaStreamSynchronize(st));
+        PP_TRY(ctx_sync(c));
     }
     if (hh)
         for (int j = 0; j < nroots; ++j) h_om[j] = -h_om[j];  // omega of the removal roots
@@ -580,11 +609,14 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         info->iters_stage1 = stage1_iters;
         info->converged = rc_final == PPRPA_OK;
         info->mu = general ? 0.0 : mu_prev;
-        info->max_imag = max_imag_below;
         info->t_sigma_ms = t_sig.total_ms;
         info->t_total_ms = t_all.total_ms;
     }
     c->last_mult = o->mult;
+    if (rc_final == PPRPA_ERR_UNSTABLE)
+        return set_error(PPRPA_ERR_UNSTABLE,
+                         "Davidson: complex Ritz pairs among the lowest roots persist and the residual "
+                         "stagnates (no definite shift); outputs hold the last iterate");
     if (rc_final != PPRPA_OK) return set_error(PPRPA_ERR_NOCONV, "Davidson: max_iter reached");
     return PPRPA_OK;
 }
@@ -645,6 +677,6 @@ extern "C" int pprpa_build_matrix(pprpa_ctx* c, int mult, double* Mout, int wher
     }
     if (where != PPRPA_DEVICE)
         PP_CUDA(cudaMemcpyAsync(Mout, M, mbytes, cudaMemcpyDeviceToHost, c->stream));
-    PP_CUDA(cudaStreamSynchronize(c->stream));
+    PP_TRY(ctx_sync(c));
     return PPRPA_OK;
 }

@@ -11,7 +11,9 @@
 // for the small molecules, replayed from a CUDA graph while the batch keeps its shape, and
 // clustered launches for the large ones) on the batch's stream, and releases them.  A solve
 // that finishes leaves the rendezvous, so the others never wait for it.
+#include <algorithm>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -32,22 +34,32 @@ struct Request {
 
 class BatchSigma : public SigmaHook {
   public:
-    BatchSigma(int nmol, pprpa_ctx* const* ctxs, pprpa_ctx* owner)
-        : ctxs_(ctxs, ctxs + nmol), owner_(owner), req_(nmol), active_(nmol) {}
+    BatchSigma(int nmol, pprpa_ctx* const* ctxs, pprpa_ctx* owner, int kcap)
+        : ctxs_(ctxs, ctxs + nmol), owner_(owner), req_(nmol), active_(nmol), kcap_(kcap) {}
 
+    // A block larger than kcap vectors (the guess, a collapse) goes over several rounds, so
+    // that every molecule's intermediate T of a round holds at most kcap vectors.
     int sigma(pprpa_ctx* c, int mult, int k, const double* z, double* out, int nterms) override {
-        const int m = index_of(c);
-        if (m < 0) return set_error(PPRPA_ERR_ARG, "solve_batch: unknown context");
         PairTable* pt;
         PP_TRY(ensure_pairs(c, mult, &pt));
-        const size_t bytes = sizeof(double) * (size_t)k * pt->N;
-        // staging buffers grow to the largest block a solve hands over (its guess, or a
-        // collapse), so their addresses, and the batch's graph, stay fixed between rounds
+        for (int j0 = 0; j0 < k; j0 += kcap_) {
+            const int kj = std::min(kcap_, k - j0);
+            PP_TRY(round_trip(c, mult, kj, z + (size_t)j0 * pt->N, out + (size_t)j0 * pt->N, nterms, pt->N));
+        }
+        return PPRPA_OK;
+    }
+
+    int round_trip(pprpa_ctx* c, int mult, int k, const double* z, double* out, int nterms, int N) {
+        const int m = index_of(c);
+        if (m < 0) return set_error(PPRPA_ERR_ARG, "solve_batch: unknown context");
+        const size_t bytes = sizeof(double) * (size_t)k * N;
+        // staging buffers of kcap vectors: their addresses, and the batch's graph, stay fixed
+        // between rounds
         double *zs, *ss;
-        PP_TRY(ws_get(c, "bsolve_z", bytes, (void**)&zs));
-        PP_TRY(ws_get(c, "bsolve_s", bytes, (void**)&ss));
+        PP_TRY(ws_get(c, "bsolve_z", sizeof(double) * (size_t)kcap_ * N, (void**)&zs));
+        PP_TRY(ws_get(c, "bsolve_s", sizeof(double) * (size_t)kcap_ * N, (void**)&ss));
         PP_CUDA(cudaMemcpyAsync(zs, z, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        PP_CUDA(cudaStreamSynchronize(c->stream));
+        PP_TRY(ctx_sync(c));
         int rc;
         {
             std::unique_lock<std::mutex> lk(mu_);
@@ -107,11 +119,8 @@ class BatchSigma : public SigmaHook {
             if (cs.empty()) continue;
             int rc = sigma_tc_batch((int)cs.size(), cs.data(), mults.data(), ks.data(), zs.data(), ss.data(),
                                     nterms, owner_->stream, owner_, true);
-            if (rc == PPRPA_OK) {
-                const cudaError_t e = cudaStreamSynchronize(owner_->stream);
-                rc = e == cudaSuccess ? check_status(owner_)
-                                      : set_error(PPRPA_ERR_CUDA, std::string("solve_batch: ") + cudaGetErrorString(e));
-            }
+            if (rc == PPRPA_OK) rc = ctx_sync(owner_);
+            if (rc == PPRPA_OK) rc = check_status(owner_);
             for (int m : who) req_[m].rc = rc;
         }
         for (Request& r : req_) r.on = false;
@@ -124,6 +133,7 @@ class BatchSigma : public SigmaHook {
     pprpa_ctx* owner_;
     std::vector<Request> req_;
     int active_;
+    int kcap_;
     int posted_ = 0;
     unsigned long long round_ = 0;
     std::mutex mu_;
@@ -153,17 +163,25 @@ extern "C" int pprpa_solve_batch(int nmol, pprpa_ctx* const* ctxs, const pprpa_o
     // the batch's own context: its stream runs the batched sigma, and it owns the batch plans
     pprpa_ctx* owner = nullptr;
     PP_TRY(pprpa_create(&owner, ctxs[0]->device, nullptr));
+    owner->blocking_sync = true;
     std::vector<std::thread> threads;
     std::vector<std::string> errs(nmol);
     {
-        BatchSigma hub(nmol, ctxs, owner);
+        // vectors per molecule and round (PPRPA_BATCH_KCAP, default 8): bounds the sum over
+        // molecules of the first-stage intermediates
+        const char* kv = getenv("PPRPA_BATCH_KCAP");
+        const int kcap = std::max(1, kv ? atoi(kv) : 8);
+        BatchSigma hub(nmol, ctxs, owner, kcap);
         threads.reserve(nmol);
         for (int m = 0; m < nmol; ++m) {
             threads.emplace_back([&, m] {
                 cudaSetDevice(ctxs[m]->device);
+                const bool keep = ctxs[m]->blocking_sync;
+                ctxs[m]->blocking_sync = true;  // many threads wait at once: block, do not spin
                 rcs[m] = solve_checked(ctxs[m], &opts[m], omega[m], X ? X[m] : nullptr, Y ? Y[m] : nullptr,
                                        nullptr, infos ? &infos[m] : nullptr, &hub);
                 if (rcs[m] != PPRPA_OK) errs[m] = pprpa_last_error();
+                ctxs[m]->blocking_sync = keep;
                 hub.leave();
             });
         }

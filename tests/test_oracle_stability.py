@@ -65,3 +65,53 @@ def test_roots_near_a_point_are_the_dense_roots():
     for v, m in zip(got, metric):
         if abs(v.imag) > 1e-6:
             assert abs(m) <= 1e-8
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_block_shift_window_bounds_the_dense_blocks(mult):
+    eps, L = _case(4, 13, 21, 54, mult)
+    M, nvv, noo = oracle.build_matrix(eps, 4, L, mult)
+    lam_a = np.linalg.eigvalsh(M[:nvv, :nvv])[0]
+    lam_c = np.linalg.eigvalsh(M[nvv:, nvv:])[0]
+    r = oracle.block_shift_window(eps, 4, L, mult, steps=nvv)
+    assert abs(r["lambda_min_C"] - lam_c) <= 1e-12
+    # a full Lanczos run reaches lambda_min(A); fewer steps bound it from above
+    assert abs(r["theta_A"] - lam_a) <= 1e-9
+    r5 = oracle.block_shift_window(eps, 4, L, mult, steps=5)
+    assert r5["theta_A"] >= lam_a - 1e-12
+    # proven indefinite means no shift makes M - mu W positive definite (dense check on a grid)
+    w = np.concatenate([np.ones(nvv), -np.ones(noo)])
+    if r["proven_indefinite"]:
+        for mu in np.linspace(-3, 3, 121):
+            assert np.linalg.eigvalsh(M - mu * np.diag(w))[0] <= 1e-12
+
+
+def test_block_shift_window_proves_an_unstable_case():
+    eps, L = _case(6, 30, 12, 53, 3)
+    r = oracle.block_shift_window(eps, 6, L, 3, steps=60)
+    assert r["proven_indefinite"]
+
+
+@pytest.mark.parametrize("mult", [1, 3])
+def test_classified_spectrum_of_a_stable_problem_is_solve_full(mult):
+    eps, L = _case(4, 13, 21, 55, mult)
+    M, nvv, noo = oracle.build_matrix(eps, 4, L, mult)
+    sol = oracle.solve_full(M, nvv, noo)
+    if sol["unstable"]:
+        pytest.skip("this draw is unstable")
+    add, rem, c = oracle.classified_spectrum(M, nvv, noo)
+    assert len(c) == 0 and len(add) == nvv and len(rem) == noo
+    assert np.abs(add - sol["omega_pp"]).max() <= 1e-10
+    assert np.abs(rem - sol["omega_hh"]).max() <= 1e-10
+
+
+def test_classified_spectrum_counts_conjugate_pairs():
+    eps, L = _case(6, 30, 12, 53, 3)
+    M, nvv, noo = oracle.build_matrix(eps, 6, L, 3)
+    add, rem, c = oracle.classified_spectrum(M, nvv, noo)
+    assert len(c) > 0 and len(c) % 2 == 0
+    assert len(add) + len(rem) + len(c) == nvv + noo
+    # conjugate pairs: the imaginary parts cancel in pairs
+    assert abs(np.sum(c.imag)) <= 1e-8 * np.abs(c.imag).max()
+    # every complex pair removes one addition and one removal root from the count
+    assert len(add) == nvv - len(c) // 2 and len(rem) == noo - len(c) // 2

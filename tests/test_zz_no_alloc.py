@@ -75,8 +75,8 @@ def test_sigma_noalloc_matches_pprpa_sigma_twice():
 
 def test_sigma_noalloc_few_orbitals_long_aux():
     """Few active orbitals, many vectors and a long auxiliary index: the scratch holds
-    thousands of auxiliary slices per pass, more than one batched GEMM launch can cover,
-    so the pass length is capped by the launch grid."""
+    thousands of auxiliary slices per pass, more products than one batched GEMM launch grid
+    covers, so the launches split themselves (pprpa_sigma's FP64 form likewise)."""
     import torch
 
     if not torch.cuda.is_available():
