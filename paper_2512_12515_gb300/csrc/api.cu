@@ -62,6 +62,7 @@ int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out) {
             }
         t.N = (int)t.pp.size();
         t.noo = t.N - t.nvv;
+        ++c->mem_epoch;
         if (t.d_pp) cudaFree(t.d_pp);
         if (t.d_pq) cudaFree(t.d_pq);
         t.d_pp = t.d_pq = nullptr;
@@ -79,6 +80,7 @@ int ensure_pairs(pprpa_ctx* c, int mult, PairTable** out) {
 }
 
 static void reset_integrals(pprpa_ctx* c) {
+    ++c->mem_epoch;
     if (c->d_L) cudaFree(c->d_L);
     if (c->d_Lhi) cudaFree(c->d_Lhi);
     if (c->d_Llo) cudaFree(c->d_Llo);
@@ -100,6 +102,7 @@ static void reset_integrals(pprpa_ctx* c) {
 // Slot energies, weights and MO indices on the device.
 static int upload_eps(pprpa_ctx* c) {
     const int n = c->n();
+    ++c->mem_epoch;
     if (c->d_eps) cudaFree(c->d_eps);
     if (c->d_slot_w) cudaFree(c->d_slot_w);
     if (c->d_slot_orb) cudaFree(c->d_slot_orb);

@@ -104,6 +104,11 @@ struct pprpa_ctx {
 
     int n() const { return no + nv; }
 
+    // bumped whenever device memory of the context is freed or moved (workspaces, integrals,
+    // pair tables, energies): batched-sigma plans captured with its pointers compare it
+    // before replaying
+    unsigned long long mem_epoch = 0;
+
     // host waits on this context's stream: spin (cudaStreamSynchronize, lowest latency) or,
     // when many host threads each drive a context (pprpa_solve_batch), block on an event
     // created with cudaEventBlockingSync so that waiting threads do not occupy host cores

@@ -17,6 +17,7 @@ static int env_int(const char* name, int dflt);
 int ws_get(pprpa_ctx* c, const std::string& name, size_t bytes, void** out) {
     DevBuf& b = c->ws[name];
     if (b.bytes < bytes) {
+        ++c->mem_epoch;
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
         b.bytes = 0;
@@ -105,6 +106,7 @@ int ensure_bf16(pprpa_ctx* c) {
     c->pm = make_padmap(c->no, c->nv);
     const int64_t np = c->pm.n_pad;
     const size_t bytes = sizeof(__nv_bfloat16) * (size_t)c->naux * np * np;
+    ++c->mem_epoch;
     if (c->d_Lhi) cudaFree(c->d_Lhi);
     if (c->d_Llo) cudaFree(c->d_Llo);
     c->d_Lhi = c->d_Llo = nullptr;
@@ -121,6 +123,7 @@ int ensure_fp8(pprpa_ctx* c) {
     const PadMap pm = c->pm;
     c->c_off8 = (int)round_up(c->no, 16);
     c->ncol8 = (int)round_up(c->c_off8 + c->nv, 16);
+    ++c->mem_epoch;
     if (c->d_L8) cudaFree(c->d_L8);
     if (c->d_L8scale) cudaFree(c->d_L8scale);
     c->d_L8 = nullptr;
@@ -236,6 +239,9 @@ struct TcJobHost {
 static int tc_alloc(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms, TcPrepared& pr,
                     cudaStream_t st, bool f8 = false) {
     PP_TRY(ensure_pairs(c, mult, &pr.pt));
+    // the BF16 / E4M3 copies of L are made on the context's stream; a batched launch on
+    // another stream must not start before they are complete
+    const bool fresh = !c->bf16_ready || (f8 && !c->fp8_ready);
     PP_TRY(ensure_bf16(c));
     pr.f8 = f8;
     if (f8) {
@@ -246,6 +252,7 @@ static int tc_alloc(pprpa_ctx* c, int mult, int k, const double* d_z, int nterms
         PP_TRY(ws_get(c, "tc_ys8", (size_t)k * round_up(std::max(c->no, 1), 8) * pr.ld8y + 16, &pr.ys8));
         PP_TRY(ws_get(c, "tc_zscale", sizeof(float) * k, (void**)&pr.zscale));
     }
+    if (fresh && st != c->stream) PP_TRY(ctx_sync(c));
     pr.pm = c->pm;
     pr.k = k;
     pr.mult = mult;
@@ -570,6 +577,7 @@ struct BatchPlan {
     std::vector<int> mults, ks;
     std::vector<const double*> z;
     std::vector<double*> sigma;
+    std::vector<unsigned long long> epochs;  // each context's mem_epoch when the plan was built
     int nterms = 1;
     cudaStream_t st = nullptr;
     std::vector<TcPrepared> prs;
@@ -615,7 +623,7 @@ static bool same_signature(const BatchPlan& bp, int nmol, pprpa_ctx* const* ctxs
     if ((int)bp.ctxs.size() != nmol || bp.nterms != nterms || bp.st != st) return false;
     for (int m = 0; m < nmol; ++m)
         if (bp.ctxs[m] != ctxs[m] || bp.mults[m] != mults[m] || bp.ks[m] != ks[m] || bp.z[m] != z[m] ||
-            bp.sigma[m] != sigma[m])
+            bp.sigma[m] != sigma[m] || bp.epochs[m] != ctxs[m]->mem_epoch)
             return false;
     return true;
 }
@@ -686,10 +694,14 @@ static int batch_persistent(int nmol, pprpa_ctx* const* ctxs, const int* mults, 
     }
     bp->n1 = (int)i1.size();
     bp->n2 = (int)i2.size();
-    PP_TRY(ws_get(owner, "batch_j1", sizeof(TcJob) * std::max<size_t>(1, j1.size()), (void**)&bp->dj1));
-    PP_TRY(ws_get(owner, "batch_j2", sizeof(TcJob) * std::max<size_t>(1, j2.size()), (void**)&bp->dj2));
-    PP_TRY(ws_get(owner, "batch_i1", sizeof(TcItem) * std::max<size_t>(1, i1.size()), (void**)&bp->di1));
-    PP_TRY(ws_get(owner, "batch_i2", sizeof(TcItem) * std::max<size_t>(1, i2.size()), (void**)&bp->di2));
+    // each plan slot (BF16, BF16x3) keeps its job and item arrays in buffers of its own: a
+    // graph of one slot is replayed after the other slot's plan has been rebuilt, so they
+    // must not share (or reallocate) each other's arrays
+    const std::string sfx = nterms == 3 ? "_x3" : "";
+    PP_TRY(ws_get(owner, "batch_j1" + sfx, sizeof(TcJob) * std::max<size_t>(1, j1.size()), (void**)&bp->dj1));
+    PP_TRY(ws_get(owner, "batch_j2" + sfx, sizeof(TcJob) * std::max<size_t>(1, j2.size()), (void**)&bp->dj2));
+    PP_TRY(ws_get(owner, "batch_i1" + sfx, sizeof(TcItem) * std::max<size_t>(1, i1.size()), (void**)&bp->di1));
+    PP_TRY(ws_get(owner, "batch_i2" + sfx, sizeof(TcItem) * std::max<size_t>(1, i2.size()), (void**)&bp->di2));
     if (!j1.empty()) {
         PP_CUDA(cudaMemcpyAsync(bp->dj1, j1.data(), sizeof(TcJob) * j1.size(), cudaMemcpyHostToDevice, st));
         PP_CUDA(cudaMemcpyAsync(bp->di1, i1.data(), sizeof(TcItem) * i1.size(), cudaMemcpyHostToDevice, st));
@@ -699,6 +711,9 @@ static int batch_persistent(int nmol, pprpa_ctx* const* ctxs, const int* mults, 
         PP_CUDA(cudaMemcpyAsync(bp->di2, i2.data(), sizeof(TcItem) * i2.size(), cudaMemcpyHostToDevice, st));
     }
     PP_CUDA(cudaStreamSynchronize(st));  // host vectors must outlive the copies
+    // the pointers captured below are those of the contexts as they are now
+    bp->epochs.resize(nmol);
+    for (int m = 0; m < nmol; ++m) bp->epochs[m] = ctxs[m]->mem_epoch;
     if (!use_graph) return batch_exec(*bp, owner);
     const long long captured0 = pprpa_kernel_launches();
     PP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
