@@ -317,10 +317,24 @@ def config_solve(pp, c, spec, forms, torch=None, nroots=10):
     return rec
 
 
-def batch_molecule(pp, torch, m, redraw=0):
+def draw_molecules(keys):
+    """Synthetic inputs of several batch molecules, drawn on host threads in parallel (each
+    from its own stream [12515, 3, m(, r)], so the result does not depend on the order)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(key):
+        spec, rng, mult = synth.batch_molecule_spec(*key)
+        return spec, mult, synth.make_system(spec, rng=rng)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, keys))
+
+
+def batch_molecule(pp, torch, m, redraw=0, drawn=None):
     """Molecule m of the batch workload (re-draw `redraw`) on its own context and stream."""
-    spec, rng, mult = synth.batch_molecule_spec(m, redraw)
-    s = synth.make_system(spec, rng=rng)
+    if drawn is None:
+        drawn = draw_molecules([(m, redraw)])[0]
+    spec, mult, s = drawn
     st = torch.cuda.Stream()
     c = pp.Context(0, stream=st.cuda_stream)
     c.set_orbitals(s["occ"], s["eps"])
@@ -336,13 +350,15 @@ def batch_bench(pp, torch, nmol, nvec, steps, warmup, fp64_subset=8, max_redraw=
     (large molecules on their own clustered launches, the rest in one persistent launch per
     stage replayed from a CUDA graph); TFLOP/s of the algorithmic sigma work.
     solve: the stability screen re-draws every molecule whose batched solve meets a subspace
-    pencil without a definite shift (require_definite: PPRPA_ERR_UNSTABLE) with the stream
-    [12515, 3, m, r], r = 1, 2, ...; the screened batch is then solved in one
+    pencil without a definite shift within 15 iterations (require_definite:
+    PPRPA_ERR_UNSTABLE) with the stream [12515, 3, m, r], r = 1, 2, ...; the screened batch is then solved in one
     pprpa_solve_batch call, BF16 sigma then BF16x3 to 1e-5 (timed, root-solves/s), and its
     first `fp64_subset` molecules once more in FP64 and in the mixed form for the
     time-to-solution ratio and |d omega| between the two."""
     t0 = time.perf_counter()
-    mols = [batch_molecule(pp, torch, m) for m in range(nmol)]
+    drawn = draw_molecules([(m, 0) for m in range(nmol)])
+    mols = [batch_molecule(pp, torch, m, 0, d) for m, d in enumerate(drawn)]
+    del drawn
     setup_s = time.perf_counter() - t0
     ctxs = [d["ctx"] for d in mols]
     mults = [d["mult"] for d in mols]
@@ -378,22 +394,27 @@ def batch_bench(pp, torch, nmol, nvec, steps, warmup, fp64_subset=8, max_redraw=
     todo = list(range(nmol))
     screen_rounds = []
     while todo:
+        # a pencil without a definite shift shows it within the first iterations: 15 of them,
+        # stopping at the first subspace without one (PPRPA_ERR_UNSTABLE)
         res = pp._lib.solve_batch([mols[i]["ctx"] for i in todo], [mols[i]["mult"] for i in todo], 8,
-                                  precision=pp.PREC_BF16, conv_tol=1e-5, max_iter=150,
+                                  precision=pp.PREC_BF16, conv_tol=1e-5, max_iter=15,
                                   require_definite=True)
         nxt = []
         for i, r in zip(todo, res):
-            if r["rc"] != 0:
+            if r["rc"] not in (0, pp._lib.ERR_NOCONV):
                 nxt.append(i)
         screen_rounds.append({"solved": len(todo), "rejected": len(nxt)})
         todo = []
         for i in nxt:
             mols[i]["ctx"].close()
             if mols[i]["redraw"] < max_redraw:
-                mols[i] = batch_molecule(pp, torch, i, mols[i]["redraw"] + 1)
                 todo.append(i)
             else:
                 mols[i] = None
+        drawn = draw_molecules([(i, mols[i]["redraw"] + 1) for i in todo])
+        for i, d in zip(todo, drawn):
+            mols[i] = batch_molecule(pp, torch, i, mols[i]["redraw"] + 1, d)
+        del drawn
     acc = [d for d in mols if d is not None]
     screen_s = time.perf_counter() - t0
 
@@ -401,7 +422,7 @@ def batch_bench(pp, torch, nmol, nvec, steps, warmup, fp64_subset=8, max_redraw=
         torch.cuda.synchronize()
         t = time.perf_counter()
         res = pp._lib.solve_batch([d["ctx"] for d in group], [d["mult"] for d in group], 8,
-                                  precision=prec, conv_tol=tol, max_iter=300)
+                                  precision=prec, conv_tol=tol, max_iter=300, require_definite=True)
         return res, time.perf_counter() - t
 
     res_m, t_m = solve_all(acc, pp.PREC_BF16, 1e-5)
