@@ -302,8 +302,130 @@ __device__ void block_gemm(double* C, int ldc, const double* A, int lda, bool tr
 //     (quadratic convergence: one or two sweeps) and U = G U'.
 // G and T are m x m FP64 scratch (leading dimension m) outside H and U.  Returns
 // 100 * FP32 sweeps + FP64 sweeps.
+// Sum over the CTA of three per-thread values (red: >= 2 * 32 * 3 / 2 + 3 doubles).
+__device__ void block_sum3(double& a, double& b, double& c, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        red[tid >> 5] = a;
+        red[32 + (tid >> 5)] = b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < nt / 32; ++w) { x += red[w]; y += red[32 + w]; }
+        red[64] = x;
+        red[65] = y;
+    }
+    __syncthreads();
+    const double sa = red[64], sb = red[65];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = c;
+    __syncthreads();
+    if (tid == 0) {
+        double z = 0.0;
+        for (int w = 0; w < nt / 32; ++w) z += red[w];
+        red[66] = z;
+    }
+    __syncthreads();
+    a = sa;
+    b = sb;
+    c = red[66];
+    __syncthreads();
+}
+
+// One step of the iterative refinement of a symmetric eigendecomposition by Ogita and Aishima
+// ("Iterative refinement for symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math.
+// 35, 2018), in FP64: for approximate eigenvectors G (columns, m x m, leading dimension m) of
+// the symmetric H (ld),
+//   R = I - G^T G,  S = G^T H G,  lam_i = S_ii / (1 - R_ii),
+//   E_ii = R_ii / 2,  E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  (i != j),
+//   G <- G (I + E),
+// which squares the error of eigenpairs whose eigenvalues are separated by more than
+// delta = 2 (||S - diag(lam)|| + ||H|| ||R||) (Frobenius norms as bounds).  Returns false, with
+// G unchanged, when some pair is closer than delta (the refinement cannot separate it) or the
+// start is too far off; otherwise lam holds the refined eigenvalues, G the refined vectors and
+// *corr the Frobenius norm of E.  T (m x m, ld m) and W (m x ld) are scratch; H is untouched.
+__device__ bool oa_refine(const double* H, int ld, double* G, double* T, double* W, int m, double* lam,
+                          double* red, double* corr, int* flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    block_gemm(T, m, H, ld, false, G, m, m);  // T = H G
+    __syncthreads();
+    // W = S = G^T (H G) and T = R = I - G^T G afterwards, upper triangles mirrored
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], T[k * m + j], acc);
+        W[i * ld + j] = acc;
+        W[j * ld + i] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], G[k * m + j], acc);
+        const double r = (i == j ? 1.0 : 0.0) - acc;
+        T[i * m + j] = r;
+        T[j * m + i] = r;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) lam[i] = W[i * ld + i] / (1.0 - T[i * m + i]);
+    __syncthreads();
+    double ns = 0.0, nh = 0.0, nr = 0.0;
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        const double sij = W[i * ld + j] - (i == j ? lam[i] : 0.0);
+        ns += sij * sij;
+        nh += H[i * ld + j] * H[i * ld + j];
+        nr += T[t] * T[t];
+    }
+    block_sum3(ns, nh, nr, red);
+    const double delta = 2.0 * (sqrt(ns) + sqrt(nh) * sqrt(nr));
+    if (tid == 0) *flag = (sqrt(nr) > 1e-3 || sqrt(ns) > 1e-3 * sqrt(nh)) ? 1 : 0;
+    __syncthreads();
+    for (int t = tid; t < m * m && !*flag; t += nt) {
+        const int i = t / m, j = t % m;
+        if (i < j && fabs(lam[i] - lam[j]) <= delta) *flag = 1;
+    }
+    __syncthreads();
+    if (*flag) return false;
+    // E in place of S in W
+    double ne = 0.0;
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        const double e = (i == j) ? 0.5 * T[t] : (W[i * ld + j] + lam[j] * T[i * m + j]) / (lam[j] - lam[i]);
+        W[i * ld + j] = e;
+        ne += e * e;
+    }
+    double z0 = 0.0, z1 = 0.0;
+    block_sum3(ne, z0, z1, red);
+    // T = G (I + E), then G = T
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        double acc = G[t];
+        for (int k = 0; k < m; ++k) acc = fma(G[i * m + k], W[k * ld + j], acc);
+        T[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < m * m; t += nt) G[t] = T[t];
+    __syncthreads();
+    *corr = sqrt(ne);
+    return true;
+}
+
 __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, double* T, double* rot,
-                               int* pairs, double* red, double tol32) {
+                               int* pairs, double* red, double tol32, bool refine_oa) {
     const int tid = threadIdx.x, nt = blockDim.x;
     float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
     float* U32 = H32 + (size_t)m * ld;
@@ -318,6 +440,32 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
         G[t] = (double)U32[i * ld + j];
     }
     __syncthreads();
+    if (refine_oa) {
+        // FP64 refinement by matrix products (about 3 m^3 FP64 FMAs a step instead of the
+        // ~10 m^3 of the orthonormalisation and Jacobi sweeps below); falls back to them when
+        // eigenvalues are too close for it
+        __shared__ int oa_flag;
+        double* lam = rot;  // the rotation buffer is free until a fallback Jacobi needs it
+        // a step squares the error; from the FP32 floor (~1e-7) one step reaches FP64 rounding,
+        // and a correction below 1e-6 leaves an error near its square
+        double corr = 1.0;
+        bool ok = true;
+        int steps = 0;
+        while (steps < 2 && ok && corr > 1e-6) {
+            ok = oa_refine(H, ld, G, T, U, m, lam, red, &corr, &oa_flag);
+            ++steps;
+        }
+        if (ok && corr <= 1e-6) {
+            for (int t = tid; t < m * m; t += nt) {
+                const int i = t / m, j = t % m;
+                U[i * ld + j] = G[t];
+                H[i * ld + j] = (i == j) ? lam[i] : 0.0;
+            }
+            __syncthreads();
+            return 100 * s32 + 50 + steps;
+        }
+        // refined only in part: G is still a good start for the path below
+    }
     for (int ns = 0; ns < 2; ++ns) {
         block_gemm(T, m, G, m, true, G, m, m);  // T = G^T G
         __syncthreads();
@@ -647,9 +795,9 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     }
     __syncthreads();
     if (tid == 0) clk[2] = clock64();
-    const int sweeps = (a.eig == 3 && in_smem)
+    const int sweeps = ((a.eig == 3 || a.eig == 4) && in_smem)
                            ? block_mixed_eig(H, U, m, lh, a.work + (size_t)m * m, a.work + 2 * (size_t)m * m, rot,
-                                             pairs, red, a.tol32)
+                                             pairs, red, a.tol32, a.eig == 4)
                        : (a.eig == 0 || a.eig == 3) ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
                        : a.eig == 1                 ? block_jacobi(H, U, m, lh, rot, pairs, red)
                                     : block_tridiag_eig(H, U, m, lh,
@@ -719,12 +867,14 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     }
 }
 
-// Eigensolver of the one-CTA kernels (PPRPA_EIG): 3 mixed FP32 / FP64 Jacobi where H and U fit
-// in shared memory, else 0 (default); 0 FP64 Jacobi with the fused symmetric update; 1 FP64
-// Jacobi with separate row and column passes; 2 Householder + implicit QR.
+// Eigensolver of the one-CTA kernels (PPRPA_EIG): 4 (default) FP32 Jacobi refined in FP64 by
+// Ogita-Aishima steps where H and U fit in shared memory, with the path of 3 as its fallback;
+// 3 mixed FP32 / FP64 Jacobi (Newton-Schulz orthonormalisation, FP64 Jacobi sweeps); 0 FP64
+// Jacobi with the fused symmetric update (also the default beyond shared memory); 1 FP64 Jacobi
+// with separate row and column passes; 2 Householder + implicit QR.
 static int eig_method() {
     const char* v = getenv("PPRPA_EIG");
-    return v ? atoi(v) : 3;
+    return v ? atoi(v) : 4;
 }
 
 // Odd leading dimension of the shared-memory matrices unless PPRPA_RR_PAD=0.
@@ -832,7 +982,7 @@ __global__ void __launch_bounds__(1024, 1) sym_eig_kernel(double* H, double* U, 
                                                           double* work, int* iwork, int eig) {
     const int b = blockIdx.x;
     double* w = work + (int64_t)b * 8192;
-    if (eig == 0 || eig == 3) block_jacobi_sym(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
+    if (eig == 0 || eig == 3 || eig == 4) block_jacobi_sym(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
     else if (eig == 1) block_jacobi(H + b * stride, U + b * stride, m, m, w, iwork + (int64_t)b * 1024, w + 1024);
     else block_tridiag_eig(H + b * stride, U + b * stride, m, m, w);
 }
