@@ -301,7 +301,8 @@ __device__ void block_gemm(double* C, int ldc, const double* A, int lda, bool tr
 //  3. H' = G^T H G in FP64 is diagonal up to FP32-level terms; FP64 Jacobi sweeps finish it
 //     (quadratic convergence: one or two sweeps) and U = G U'.
 // G and T are m x m FP64 scratch (leading dimension m) outside H and U.  Returns
-// 100 * FP32 sweeps + FP64 sweeps.
+// 100 * FP32 sweeps + FP64 sweeps (+ 10 * the reason a refinement fell back to them), or
+// 100 * FP32 sweeps + 50 + refinement steps.
 // Sum over the CTA of three per-thread values (red: >= 2 * 32 * 3 / 2 + 3 doubles).
 __device__ void block_sum3(double& a, double& b, double& c, double* red) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -346,11 +347,11 @@ __device__ void block_sum3(double& a, double& b, double& c, double* red) {
 //   R = I - G^T G,  S = G^T H G,  lam_i = S_ii / (1 - R_ii),
 //   E_ii = R_ii / 2,  E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  (i != j),
 //   G <- G (I + E),
-// which squares the error of eigenpairs whose eigenvalues are separated by more than
-// delta = 2 (||S - diag(lam)|| + ||H|| ||R||) (Frobenius norms as bounds).  Returns false, with
-// G unchanged, when some pair is closer than delta (the refinement cannot separate it) or the
-// start is too far off; otherwise lam holds the refined eigenvalues, G the refined vectors and
-// *corr the Frobenius norm of E.  T (m x m, ld m) and W (m x ld) are scratch; H is untouched.
+// which squares the error of eigenpairs whose eigenvalues are well separated relative to their
+// coupling.  Returns false, with G unchanged, when some pair is coupled by more than 1 % of
+// its gap (the refinement cannot separate it) or the start is too far off; otherwise lam holds the refined eigenvalues, G the refined vectors and
+// *corr the Frobenius norm of E; *flag says why it returned false (1 close eigenvalues, 2 a start
+// too far off).  T (m x m, ld m) and W (m x ld) are scratch; H is untouched.
 __device__ bool oa_refine(const double* H, int ld, double* G, double* T, double* W, int m, double* lam,
                           double* red, double* corr, int* flag) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -391,12 +392,19 @@ __device__ bool oa_refine(const double* H, int ld, double* G, double* T, double*
         nr += T[t] * T[t];
     }
     block_sum3(ns, nh, nr, red);
-    const double delta = 2.0 * (sqrt(ns) + sqrt(nh) * sqrt(nr));
-    if (tid == 0) *flag = (sqrt(nr) > 1e-3 || sqrt(ns) > 1e-3 * sqrt(nh)) ? 1 : 0;
+    if (tid == 0) *flag = (sqrt(nr) > 1e-3 || sqrt(ns) > 1e-3 * sqrt(nh)) ? 2 : 0;
     __syncthreads();
+    // pairs the first-order step cannot separate: a coupling |S_ij + lam_j R_ij| above 1 % of
+    // the gap (the step's error is the square of that ratio), or eigenvalues equal to rounding.
+    // This per-pair form of the method's separation condition keeps well-resolved pairs of
+    // close eigenvalues, which the norm bound delta would reject together with the rest.
+    const double tiny = 1e-13 * sqrt(nh);
     for (int t = tid; t < m * m && !*flag; t += nt) {
         const int i = t / m, j = t % m;
-        if (i < j && fabs(lam[i] - lam[j]) <= delta) *flag = 1;
+        if (i >= j) continue;
+        const double gap = fabs(lam[j] - lam[i]);
+        const double cpl = fmax(fabs(W[i * ld + j] + lam[j] * T[i * m + j]), fabs(W[i * ld + j] + lam[i] * T[i * m + j]));
+        if (gap <= tiny || cpl > 0.01 * gap) *flag = 1;
     }
     __syncthreads();
     if (*flag) return false;
@@ -440,6 +448,7 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
         G[t] = (double)U32[i * ld + j];
     }
     __syncthreads();
+    int fallback = 0;  // why the refinement fell back: 1 close eigenvalues, 2 poor start, 3 slow
     if (refine_oa) {
         // FP64 refinement by matrix products (about 3 m^3 FP64 FMAs a step instead of the
         // ~10 m^3 of the orthonormalisation and Jacobi sweeps below); falls back to them when
@@ -465,6 +474,7 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
             return 100 * s32 + 50 + steps;
         }
         // refined only in part: G is still a good start for the path below
+        fallback = ok ? 3 : oa_flag;
     }
     for (int ns = 0; ns < 2; ++ns) {
         block_gemm(T, m, G, m, true, G, m, m);  // T = G^T G
@@ -497,7 +507,7 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
     __syncthreads();
     for (int t = tid; t < m * m; t += nt) U[(t / m) * ld + t % m] = T[t];
     __syncthreads();
-    return 100 * s32 + s64;
+    return 100 * s32 + 10 * fallback + s64;
 }
 
 // Symmetric eigendecomposition by Householder reduction to tridiagonal form followed by the
@@ -889,7 +899,10 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
     if (a.m <= 0 || a.m > 1024) return set_error(PPRPA_ERR_ARG, "rayleigh_ritz: size must be 1..1024");
     a.pad = rr_pad();
     const char* tv = getenv("PPRPA_RR_TOL32");
-    a.tol32 = tv ? atof(tv) : 1e-10;
+    // the FP64 refinement by Ogita-Aishima steps separates only eigenvalues farther apart than
+    // about twice the off-diagonal left by the FP32 stage: run that stage to its rounding floor
+    // (it stops on stalling) before refining, or to 1e-5 of the norm before FP64 Jacobi
+    a.tol32 = tv ? atof(tv) : (a.eig == 4 ? 1e-14 : 1e-10);
     const char* pv = getenv("PPRPA_RR_PROF");
     a.prof = pv ? atoi(pv) : 0;
     const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
