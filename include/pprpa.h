@@ -104,7 +104,8 @@ typedef struct pprpa_info {
     double sigma_flops;   /* algorithmic sigma flops 3*naux*n*(nv^2+no^2) per vector, summed */
     int nconv;            /* returned roots whose residual met conv_tol (the lowest ones need
                              not be among them when the solve did not converge) */
-    int n_real;           /* Davidson: real positive-norm Ritz values in the last subspace */
+    int n_real;           /* Davidson: real positive-norm Ritz values in the last subspace; 0 when
+                             the solve returned no iterate (stopped by require_definite) */
 } pprpa_info;
 
 /* ---- context ------------------------------------------------------------

@@ -402,16 +402,19 @@ class Context:
                                   Y.ctypes.data, ec.ctypes.data if want_ec else None,
                                   ctypes.byref(info))
         # a Davidson solve that stopped without converging (max_iter, or lowest roots
-        # interleaved with complex pairs: UNSTABLE after some iterations) returns its last
-        # iterate; raise_noconv=False hands it back instead of raising
-        stopped = rc == ERR_NOCONV or (rc == ERR_UNSTABLE and method == METHOD_DAVIDSON
-                                       and info.iters > 0)
+        # interleaved with complex pairs: UNSTABLE after some iterations with n_real Ritz
+        # values) returns its last iterate; one that stopped at its first indefinite subspace
+        # (require_definite) returns none.  raise_noconv=False hands either back instead of
+        # raising; "iterate" says whether omega / X / Y hold a last iterate.
+        davidson = method == METHOD_DAVIDSON
+        stopped = rc == ERR_NOCONV or (rc == ERR_UNSTABLE and davidson and info.iters > 0
+                                       and info.n_real > 0)
         if rc == OK or stopped:
             self._last_mult = mult  # the library now holds this solve's vectors
-        if rc != OK and not (stopped and not raise_noconv):
+        if rc != OK and not (davidson and rc in (ERR_NOCONV, ERR_UNSTABLE) and not raise_noconv):
             _check(rc)
         return {"omega": omega, "X": X, "Y": Y[:, :noo], "ec": float(ec[0]),
-                "info": info.as_dict(), "rc": rc}
+                "info": info.as_dict(), "rc": rc, "iterate": rc == OK or stopped}
 
     def autotune(self, mult, k, precision=PREC_BF16):
         """Tune the tensor-core tile widths on this problem; returns the four widths."""

@@ -425,7 +425,10 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             PP_TRY(ctx_sync(c));
             if ((int)hinfo[0] == DEV_NOTPD) {
                 if (o->require_definite) {
-                    if (info) info->iters = it;
+                    if (info) {
+                        info->iters = it;
+                        info->n_real = 0;  // no iterate is returned
+                    }
                     return set_error(PPRPA_ERR_UNSTABLE, "Davidson: the subspace pencil has no definite shift");
                 }
                 if (m > 128) return set_error(PPRPA_ERR_UNSTABLE, "Davidson: no definite shift and subspace > 128");
