@@ -7,6 +7,8 @@
 // The sign of kappa is the sign of the norm c^T S c (two-electron addition
 // roots have kappa > 0), and the lowest addition roots have the largest
 // kappa.  H is diagonalised with the parallel cyclic Jacobi method.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace pprpa {
@@ -18,6 +20,65 @@ constexpr int RR_THREADS = 1024;
 constexpr int RR_SMEM_MAX = 112;
 
 __host__ __device__ inline int rr_ld(int m, int pad) { return pad ? (m | 1) : m; }
+
+// Sums over the CTA of per-thread values, returned to every thread.  The partial sums of the
+// warps are added by a shuffle tree on warp 0: a serial chain of dependent FP64 additions on
+// one thread costs thousands of cycles on this GPU.  red: >= 99 doubles (partials at 0..95,
+// results at 96..98).
+__device__ void block_sum3(double& a, double& b, double& c, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[w] = a;
+        red[32 + w] = b;
+        red[64 + w] = c;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < nw ? red[lane] : 0.0, y = lane < nw ? red[32 + lane] : 0.0, z = lane < nw ? red[64 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) {
+            red[96] = x;
+            red[97] = y;
+            red[98] = z;
+        }
+    }
+    __syncthreads();
+    a = red[96];
+    b = red[97];
+    c = red[98];
+}
+
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+    double c = 0.0;
+    block_sum3(a, b, c, red);
+}
+
+// Maximum over the CTA of a per-thread value (same tree; red as above).
+__device__ double block_max(double v, double* red) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = lane < nw ? red[lane] : -1e300;
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) red[96] = x;
+    }
+    __syncthreads();
+    return red[96];
+}
+
 
 // In-place Cholesky of the lower triangle of K (m x m, ld).  Returns false on a
 // pivot <= rel_tol * scale.  All threads of the block must call it.
@@ -70,20 +131,8 @@ __device__ int block_jacobi(double* H, double* U, int m, int ld, double* rot, in
             tot += h * h;
             if (i != j) off += h * h;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        }
-        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = off; red[2 * (tid >> 5) + 1] = tot; }
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < nt / 32; ++w) { a += red[2 * w]; b += red[2 * w + 1]; }
-            red[64] = a;
-            red[65] = b;
-        }
-        __syncthreads();
-        if (!(red[64] > 1e-30 * red[65]) || me < 2) break;
+        block_sum2(off, tot, red);
+        if (!(off > 1e-30 * tot) || me < 2) break;
         for (int s = 0; s < me - 1; ++s) {
             // pair i: fixed player me-1 vs s, others (s+i, s-i) mod (me-1)
             for (int i = tid; i < half; i += nt) {
@@ -176,23 +225,11 @@ __device__ int jacobi_sym_t(T* H, T* U, int m, int ld, T* rot, int* pairs, doubl
             if (i != j) off += h * h;
         }
         double offd = off, totd = tot;
-        for (int o = 16; o > 0; o >>= 1) {
-            offd += __shfl_xor_sync(0xffffffffu, offd, o);
-            totd += __shfl_xor_sync(0xffffffffu, totd, o);
-        }
-        if ((tid & 31) == 0) { red[2 * (tid >> 5)] = offd; red[2 * (tid >> 5) + 1] = totd; }
-        __syncthreads();
-        if (tid == 0) {
-            double x = 0.0, y = 0.0;
-            for (int w = 0; w < nt / 32; ++w) { x += red[2 * w]; y += red[2 * w + 1]; }
-            red[64] = x;
-            red[65] = y;
-        }
-        __syncthreads();
-        if (!(red[64] > tol2 * red[65]) || me < 2) break;
+        block_sum2(offd, totd, red);
+        if (!(offd > tol2 * totd) || me < 2) break;
         // rounding floor of a low precision: quadratic convergence has stopped
-        if (stop_on_stall && sweep >= 2 && red[64] > 0.25 * prev_off) break;
-        prev_off = red[64];
+        if (stop_on_stall && sweep >= 2 && offd > 0.25 * prev_off) break;
+        prev_off = offd;
         for (int s = 0; s < me - 1; ++s) {
             for (int i = tid; i < half; i += nt) {
                 int p, q;
@@ -303,43 +340,6 @@ __device__ void block_gemm(double* C, int ldc, const double* A, int lda, bool tr
 // G and T are m x m FP64 scratch (leading dimension m) outside H and U.  Returns
 // 100 * FP32 sweeps + FP64 sweeps (+ 10 * the reason a refinement fell back to them), or
 // 100 * FP32 sweeps + 50 + refinement steps.
-// Sum over the CTA of three per-thread values (red: >= 2 * 32 * 3 / 2 + 3 doubles).
-__device__ void block_sum3(double& a, double& b, double& c, double* red) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    __syncthreads();
-    if ((tid & 31) == 0) {
-        red[tid >> 5] = a;
-        red[32 + (tid >> 5)] = b;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double x = 0.0, y = 0.0;
-        for (int w = 0; w < nt / 32; ++w) { x += red[w]; y += red[32 + w]; }
-        red[64] = x;
-        red[65] = y;
-    }
-    __syncthreads();
-    const double sa = red[64], sb = red[65];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = c;
-    __syncthreads();
-    if (tid == 0) {
-        double z = 0.0;
-        for (int w = 0; w < nt / 32; ++w) z += red[w];
-        red[66] = z;
-    }
-    __syncthreads();
-    a = sa;
-    b = sb;
-    c = red[66];
-    __syncthreads();
-}
-
 // One step of the iterative refinement of a symmetric eigendecomposition by Ogita and Aishima
 // ("Iterative refinement for symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math.
 // 35, 2018), in FP64: for approximate eigenvectors G (columns, m x m, leading dimension m) of
@@ -433,7 +433,7 @@ __device__ bool oa_refine(const double* H, int ld, double* G, double* T, double*
 }
 
 __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, double* T, double* rot,
-                               int* pairs, double* red, double tol32, bool refine_oa) {
+                               int* pairs, double* red, double tol32, bool refine_oa, long long* pclk = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
     float* U32 = H32 + (size_t)m * ld;
@@ -443,6 +443,7 @@ __device__ int block_mixed_eig(double* H, double* U, int m, int ld, double* G, d
     }
     const int s32 = jacobi_sym_t<float>(H32, U32, m, ld, reinterpret_cast<float*>(rot), pairs, red, tol32,
                                         1e-9f, 1e-30f, 16, true);
+    if (pclk && tid == 0) *pclk = clock64();
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
         G[t] = (double)U32[i * ld + j];
@@ -701,7 +702,7 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     extern __shared__ double sm[];
     __shared__ double rot[2 * 512 + 2];
     __shared__ int pairs[2 * 512 + 2];
-    __shared__ double red[2 * 32 + 4];
+    __shared__ double red[104];
     __shared__ int flag;
     __shared__ int npos_sh;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -718,22 +719,15 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
     int* rank = (int*)(a.work + 4 * (size_t)m * m);
 
     __shared__ long long clk[6];  // phase clocks of thread 0 (PPRPA_RR_PROF)
+    __shared__ long long clk6;    // end of the FP32 stage of the mixed eigensolver
     if (tid == 0) clk[0] = clock64();
     if (tid == 0) a.info[0] = DEV_NOTPD;
     // scale for the pivot test
     double sc = 0.0;
     for (int i = tid; i < m; i += nt)
         sc = fmax(sc, fabs(a.G[i * ld + i] + (a.Go ? a.Go[i * ld + i] : 0.0)) + fabs(a.S[i * ld + i]));
-    for (int o = 16; o > 0; o >>= 1) sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, o));
-    if ((tid & 31) == 0) red[tid >> 5] = sc;
-    __syncthreads();
-    if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < nt / 32; ++w) s = fmax(s, red[w]);
-        red[64] = s;
-    }
-    __syncthreads();
-    const double scale = red[64] > 0.0 ? red[64] : 1.0;
+    sc = block_max(sc, red);
+    const double scale = sc > 0.0 ? sc : 1.0;
 
     int used = -1;
     double mu = 0.0;
@@ -804,10 +798,10 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         }
     }
     __syncthreads();
-    if (tid == 0) clk[2] = clock64();
+    if (tid == 0) clk6 = clk[2] = clock64();
     const int sweeps = ((a.eig == 3 || a.eig == 4) && in_smem)
                            ? block_mixed_eig(H, U, m, lh, a.work + (size_t)m * m, a.work + 2 * (size_t)m * m, rot,
-                                             pairs, red, a.tol32, a.eig == 4)
+                                             pairs, red, a.tol32, a.eig == 4, &clk6)
                        : (a.eig == 0 || a.eig == 3) ? block_jacobi_sym(H, U, m, lh, rot, pairs, red)
                        : a.eig == 1                 ? block_jacobi(H, U, m, lh, rot, pairs, red)
                                     : block_tridiag_eig(H, U, m, lh,
@@ -871,10 +865,636 @@ __global__ void __launch_bounds__(RR_THREADS, 1) rayleigh_ritz_kernel(RRArgs a) 
         a.info[5] = sweeps;
         if (a.prof) {
             clk[5] = clock64();
-            printf("[rr] m %d sweeps %d cycles: factor %lld solves %lld eig %lld rank %lld ritz %lld\n", m, sweeps,
-                   clk[1] - clk[0], clk[2] - clk[1], clk[3] - clk[2], clk[4] - clk[3], clk[5] - clk[4]);
+            printf("[rr] m %d sweeps %d cycles: factor %lld solves %lld eig %lld (fp32 %lld) rank %lld ritz %lld\n", m,
+                   sweeps, clk[1] - clk[0], clk[2] - clk[1], clk[3] - clk[2], clk6 - clk[2], clk[4] - clk[3],
+                   clk[5] - clk[4]);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz on a cluster of CTAs (m <= RRC_MAX, eigensolver 4).
+//
+// GB300 runs FP64 at about two FMAs per clock per SM, so the O(m^3) FP64 products of the
+// one-CTA kernel above (the triangular solves of the reduction, the Ogita-Aishima
+// refinement) are bound by a single SM's FP64 pipe.  Here RRC_SIZE CTAs of one thread-block
+// cluster each hold a full copy of the state in shared memory and run the same control flow
+// on it.  The serial steps (the shifted Cholesky, the FP32 Jacobi rotations of H, the
+// reductions and tests) run on every CTA alike and give bit-identical results, since every
+// CTA executes the same instructions on the same data; each FP64 product and each
+// triangular solve is split over the CTAs (rows, or columns), and every CTA stores its slice
+// into the copies of all CTAs through distributed shared memory, a cluster barrier then
+// publishing it.  A buffer that other CTAs write is never read across such a barrier: every
+// broadcast phase starts after a barrier that follows the last local read of its target.
+// In the FP32 Jacobi each CTA applies the rotations to its own slice of the rows of U.
+constexpr int RRC_SIZE = 8;   // CTAs per cluster (the portable maximum)
+constexpr int RRC_MAX = 72;   // largest subspace of the clustered form (its five m x m buffers fit)
+
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+
+// v stored at the address p (a shared-memory buffer) in every CTA of the cluster
+__device__ __forceinline__ void cl_bcast(double* p, double v) {
+    cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+    for (int r = 0; r < RRC_SIZE; ++r) *cl.map_shared_rank(p, r) = v;
+}
+
+// packed lower triangle: element (i, j), j <= i
+__device__ __forceinline__ int lp(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// In-place Cholesky of the packed lower triangle K (m x m); false on a pivot <= rel_tol * scale.
+// Right-looking: the trailing update gives a warp to each row and a lane to each column.
+__device__ bool chol_packed(double* K, int m, double rel_tol, double scale, int* flag, double* rpiv) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    for (int j = 0; j < m; ++j) {
+        __syncthreads();
+        if (tid == 0) {
+            const double d = K[lp(j, j)];
+            if (!(d > rel_tol * scale)) *flag = 1;
+            else {
+                const double r = sqrt(d);
+                K[lp(j, j)] = r;
+                *rpiv = 1.0 / r;
+            }
+        }
+        __syncthreads();
+        if (*flag) return false;
+        const double ri = *rpiv;
+        for (int i = j + 1 + tid; i < m; i += nt) K[lp(i, j)] *= ri;
+        __syncthreads();
+        for (int i = j + 1 + w; i < m; i += nw) {
+            const double kij = K[lp(i, j)];
+            for (int l = j + 1 + lane; l <= i; l += 32) K[lp(i, l)] = fma(-kij, K[lp(l, j)], K[lp(i, l)]);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Triangular solves of a warp with the unit lower factor Ls = L D^-1 (packed, diagonal
+// unused): L x = b is Ls y = b with x = D^-1 y, and L^T c = u is Ls^T c = D^-1 u.  Column-
+// oriented substitution: element i is final once the elements before it have updated it; the
+// lane holding it broadcasts it and it updates the ones after it.  Three elements per lane
+// (m <= 96); a block of 32 elements with none left to update skips the step.
+// warp_lsolve_unit: Ls y = b, element r = m - 1 - (lane + 32 k) in x_k (the partial block
+// holds the first rows and drops out first).
+__device__ __forceinline__ void warp_lsolve_unit(const double* Ls, int m, double& x0, double& x1, double& x2) {
+    const int lane = threadIdx.x & 31;
+    const int r0 = m - 1 - lane, r1 = r0 - 32, r2 = r0 - 64;
+    for (int i = 0; i < m - 1; ++i) {
+        const int idx = m - 1 - i, k = idx >> 5, src = idx & 31;
+        const double yi = __shfl_sync(0xffffffffu, k == 0 ? x0 : (k == 1 ? x1 : x2), src);
+        if (r0 > i) x0 = fma(-Ls[lp(r0, i)], yi, x0);
+        if (m - 33 > i && r1 > i) x1 = fma(-Ls[lp(r1, i)], yi, x1);
+        if (m - 65 > i && r2 > i) x2 = fma(-Ls[lp(r2, i)], yi, x2);
+    }
+}
+
+// warp_usolve_unit: Ls^T c = v, element r = lane + 32 k in x_k.
+__device__ __forceinline__ void warp_usolve_unit(const double* Ls, int m, double& x0, double& x1, double& x2) {
+    const int lane = threadIdx.x & 31;
+    const int r0 = lane, r1 = lane + 32, r2 = lane + 64;
+    for (int i = m - 1; i > 0; --i) {
+        const int k = i >> 5, src = i & 31;
+        const double ci = __shfl_sync(0xffffffffu, k == 0 ? x0 : (k == 1 ? x1 : x2), src);
+        if (r0 < i) x0 = fma(-Ls[lp(i, r0)], ci, x0);
+        if (i > 32 && r1 < i) x1 = fma(-Ls[lp(i, r1)], ci, x1);
+        if (i > 64 && r2 < i) x2 = fma(-Ls[lp(i, r2)], ci, x2);
+    }
+}
+
+// FP32 parallel cyclic Jacobi with the pairing, rotations, fused 2 x 2 block update and
+// stopping rules of jacobi_sym_t, for the clustered kernel: U receives the rotations on its
+// rows [u0, u1) only (rows of U evolve independently), one thread per (pair, row).  btab lists
+// the blocks (a, b), a <= b, of a round (a << 8 | b); pq holds the pair (p | q << 16) and rot
+// its (c, s).  H is stored in full: the mirrored stores of a block hit distinct banks, where
+// an upper-triangle-only form mixes two address patterns within a warp and conflicts.
+__device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u0, int u1, float2* rot, int* pq,
+                           const unsigned short* btab, double* red, double tol2, int max_sweeps) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nu = u1 - u0;
+    for (int t = tid; t < nu * m; t += nt) {
+        const int i = u0 + t / m, j = t % m;
+        U[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+    }
+    const int me = (m + 1) & ~1;
+    const int half = me / 2;
+    const int nblk = half * (half + 1) / 2;
+    int sweep = 0;
+    double prev_off = 0.0;
+    for (; sweep < max_sweeps; ++sweep) {
+        __syncthreads();
+        float off = 0.0f, tot = 0.0f;
+        for (int t = tid; t < m * m; t += nt) {
+            const int i = t / m, j = t % m;
+            const float h = H[i * ld + j];
+            tot += h * h;
+            if (i != j) off += h * h;
+        }
+        double offd = off, totd = tot;
+        block_sum2(offd, totd, red);
+        if (!(offd > tol2 * totd) || me < 2) break;
+        if (sweep >= 2 && offd > 0.25 * prev_off) break;  // FP32 rounding floor reached
+        prev_off = offd;
+        for (int s = 0; s < me - 1; ++s) {
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                if (i == 0) { p = me - 1; q = s; }
+                else {
+                    p = s + i;
+                    if (p >= me - 1) p -= me - 1;
+                    q = s - i;
+                    if (q < 0) q += me - 1;
+                }
+                if (p > q) { const int x = p; p = q; q = x; }
+                float c = 1.0f, sn = 0.0f;
+                if (q < m) {
+                    const float apq = H[p * ld + q], app = H[p * ld + p], aqq = H[q * ld + q];
+                    if (fabsf(apq) > 1e-30f && apq * apq > 1e-18f * fabsf(app * aqq)) {
+                        // the hardware reciprocal square root and division (a few ulp): a
+                        // rotation stays orthogonal to that order whatever its angle, and the
+                        // FP64 refinement takes the FP32 result from there
+                        const float d = aqq - app, a2 = 2.0f * apq;
+                        const float h2 = fmaf(d, d, a2 * a2);
+                        const float tt = __fdividef(d >= 0.0f ? a2 : -a2, fabsf(d) + h2 * rsqrtf(h2));
+                        c = rsqrtf(fmaf(tt, tt, 1.0f));
+                        sn = tt * c;
+                    }
+                }
+                pq[i] = p | (q << 16);
+                rot[i] = make_float2(c, sn);
+            }
+            __syncthreads();
+            // the 2 x 2 blocks of H, then (threads nblk.. of the same pass) U <- U J on rows
+            // [u0, u1), one (pair, row) each: H and U are disjoint
+            for (int t = tid; t < nblk + half * nu; t += nt) {
+                if (t >= nblk) {
+                    const int tu = t - nblk;
+                    const int i = tu / nu, row = u0 + tu - (tu / nu) * nu;
+                    const int pqi = pq[i];
+                    const int p = pqi & 0xffff, q = pqi >> 16;
+                    if (q >= m) continue;
+                    const float2 r = rot[i];
+                    const float up = U[row * ld + p], uq = U[row * ld + q];
+                    U[row * ld + p] = r.x * up - r.y * uq;
+                    U[row * ld + q] = r.y * up + r.x * uq;
+                    continue;
+                }
+                const int v = btab[t];
+                const int aa = v >> 8, b = v & 255;
+                const int pqa = pq[aa], pqb = pq[b];
+                const int pa = pqa & 0xffff, qa = pqa >> 16, pb = pqb & 0xffff, qb = pqb >> 16;
+                const bool va = qa < m, vb = qb < m;  // q = m marks the dummy player (odd m)
+                const float2 ra = rot[aa], rb = rot[b];
+                const float h00 = H[pa * ld + pb];
+                const float h01 = vb ? H[pa * ld + qb] : 0.0f;
+                const float h10 = va ? H[qa * ld + pb] : 0.0f;
+                const float h11 = (va && vb) ? H[qa * ld + qb] : 0.0f;
+                const float r00 = ra.x * h00 - ra.y * h10, r01 = ra.x * h01 - ra.y * h11;
+                const float r10 = ra.y * h00 + ra.x * h10, r11 = ra.y * h01 + ra.x * h11;
+                const float o00 = rb.x * r00 - rb.y * r01, o01 = rb.y * r00 + rb.x * r01;
+                const float o10 = rb.x * r10 - rb.y * r11, o11 = rb.y * r10 + rb.x * r11;
+                if (aa == b) {
+                    const float od = 0.5f * (o01 + o10);
+                    H[pa * ld + pa] = o00;
+                    if (va) {
+                        H[pa * ld + qa] = od;
+                        H[qa * ld + pa] = od;
+                        H[qa * ld + qa] = o11;
+                    }
+                } else {
+                    H[pa * ld + pb] = o00;
+                    H[pb * ld + pa] = o00;
+                    if (vb) { H[pa * ld + qb] = o01; H[qb * ld + pa] = o01; }
+                    if (va) { H[qa * ld + pb] = o10; H[pb * ld + qa] = o10; }
+                    if (va && vb) { H[qa * ld + qb] = o11; H[qb * ld + qa] = o11; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    return sweep;
+}
+
+// One Ogita-Aishima step (same arithmetic as oa_refine above) with every O(m^3) product and
+// every O(m^2) step split over the cluster: T = H G and G (I + E) by rows, S = G^T T and
+// R = I - G^T G by upper-triangle entries, the separation test and E by entries; each slice
+// is stored into every CTA, and each CTA stores its partial sums (of S, R and E squared) and
+// its test result into slot `rank` of every CTA, which all add in the same order.  G (m x m)
+// and T swap roles on success (*G then holds the refined vectors); W (m x ld) is scratch and
+// holds E off its diagonal at the end, dE (m) the diagonal; nh = ||H||_F^2; flags has
+// RRC_SIZE + 1 entries, the last one the reason of a failed step.  Entered and left just
+// after a cluster barrier.
+__device__ __noinline__ bool oa_refine_cl(const double* H, int ld, double*& G, double*& T, double* W, int m, double* lam,
+                             double nh, double* red, double (*part)[RRC_SIZE], int* flags, double* dE,
+                             double* scal, double* corr, long long* pc) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int i0 = rank * m / RRC_SIZE, i1 = (rank + 1) * m / RRC_SIZE;
+    const int ntri = m * (m + 1) / 2;
+    const int t0 = (int)((long long)rank * ntri / RRC_SIZE), t1 = (int)((long long)(rank + 1) * ntri / RRC_SIZE);
+    const int e0 = rank * m * m / RRC_SIZE, e1 = (rank + 1) * m * m / RRC_SIZE;
+    // T = H G, rows [i0, i1)
+    for (int t = tid; t < (i1 - i0) * m; t += nt) {
+        const int i = i0 + t / m, j = t % m;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(H[i * ld + k], G[k * m + j], acc);
+        cl_bcast(&T[i * m + j], acc);
+    }
+    if (tid == 0) pc[5] = clock64();
+    __syncthreads();
+    if (tid == 0) pc[6] = clock64();
+    cl_sync();
+    if (tid == 0) pc[0] = clock64();
+    // W = S = G^T T, upper-triangle entries [t0, t1), mirrored; partial sum of the squares of
+    // its off-diagonal entries
+    double so = 0.0, z = 0.0, z2 = 0.0;
+    for (int t = t0 + tid; t < t1; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], T[k * m + j], acc);
+        cl_bcast(&W[i * ld + j], acc);
+        if (i != j) {
+            cl_bcast(&W[j * ld + i], acc);
+            so = fma(2.0 * acc, acc, so);
+        }
+    }
+    if (tid == 0) pc[7] = clock64();
+    block_sum3(so, z, z2, red);
+    if (tid == 0) pc[8] = clock64();
+    if (tid == 0) cl_bcast(&part[0][rank], so);
+    cl_sync();
+    if (tid == 0) pc[1] = clock64();
+    // T = R = I - G^T G, same split (every CTA has finished reading T above)
+    double sr = 0.0;
+    z = z2 = 0.0;
+    for (int t = t0 + tid; t < t1; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], G[k * m + j], acc);
+        const double r = (i == j ? 1.0 : 0.0) - acc;
+        cl_bcast(&T[i * m + j], r);
+        if (i != j) cl_bcast(&T[j * m + i], r);
+        sr = fma(i != j ? 2.0 * r : r, r, sr);
+    }
+    block_sum3(sr, z, z2, red);
+    if (tid == 0) cl_bcast(&part[1][rank], sr);
+    cl_sync();
+    if (tid == 0) pc[2] = clock64();
+    // lam and the diagonal of E (0.5 R_ii) kept aside: the E stores below leave the diagonal
+    // of W (S_ii) alone, and T (R) is not written before the next barrier
+    for (int i = tid; i < m; i += nt) {
+        lam[i] = W[i * ld + i] / (1.0 - T[i * m + i]);
+        dE[i] = 0.5 * T[i * m + i];
+    }
+    __syncthreads();
+    // scalars once, by warp 0 (FP64 work repeated on every thread costs the FP64 pipe):
+    // ||S - diag(lam)||^2 = off-diagonal part + diagonal terms, ||R||^2, the test on a poor
+    // start, and the rounding-level gap
+    if (tid < 32) {
+        double d2 = 0.0;
+        for (int i = tid; i < m; i += 32) {
+            const double d = W[i * ld + i] - lam[i];
+            d2 = fma(d, d, d2);
+        }
+        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        if (tid == 0) {
+            double ns = d2, nr = 0.0;
+            for (int r = 0; r < RRC_SIZE; ++r) { ns += part[0][r]; nr += part[1][r]; }
+            scal[0] = (sqrt(nr) > 1e-3 || sqrt(ns) > 1e-3 * sqrt(nh)) ? 2.0 : 0.0;
+            scal[1] = 1e-13 * sqrt(nh);
+        }
+    }
+    __syncthreads();
+    const int poor = (int)scal[0];
+    const double tiny = scal[1];
+    // separation test and E on the off-diagonal entries [e0, e1): a pair coupled by more than
+    // 1 % of its gap, or eigenvalues equal to rounding, cannot be separated by the step
+    int bad = 0;
+    double ne = 0.0;
+    z = z2 = 0.0;
+    for (int t = e0 + tid; t < e1; t += nt) {
+        const int i = t / m, j = t % m;
+        double e = dE[i];
+        if (i != j) {
+            const double g = lam[j] - lam[i];
+            const double sij = W[i * ld + j];
+            const double cpl = fmax(fabs(sij + lam[j] * T[i * m + j]), fabs(sij + lam[i] * T[i * m + j]));
+            if (fabs(g) <= tiny || cpl > 0.01 * fabs(g)) bad = 1;
+            // 1 / gap: FP32 reciprocal and one Newton step (relative error ~1e-14; E is a
+            // correction of FP32 size, so its own relative accuracy need not be FP64's)
+            double rg = (double)__frcp_rn((float)g);
+            rg = rg * fma(-g, rg, 2.0);
+            e = (sij + lam[j] * T[i * m + j]) * rg;
+            if (!bad) cl_bcast(&W[i * ld + j], e);  // the owner of (i, j) alone reads S_ij
+        }
+        ne = fma(e, e, ne);
+    }
+    bad = __syncthreads_or(bad);
+    block_sum3(ne, z, z2, red);
+    if (tid == 0) {
+        cl_bcast(&part[2][rank], ne);
+        for (int r = 0; r < RRC_SIZE; ++r) *cl.map_shared_rank(&flags[rank], r) = poor ? poor : bad;
+    }
+    cl_sync();
+    if (tid == 0) pc[3] = clock64();
+    if (tid == 0) {
+        int f = 0;
+        double x = 0.0;
+        for (int r = 0; r < RRC_SIZE; ++r) {
+            f = max(f, flags[r]);
+            x += part[2][r];
+        }
+        flags[RRC_SIZE] = f;  // why a step fails: 1 close eigenvalues, 2 a start too far off
+        scal[0] = sqrt(x);
+    }
+    __syncthreads();
+    if (flags[RRC_SIZE]) return false;  // the same on every CTA: no barrier is skipped by one CTA alone
+    const double ne_sqrt = scal[0];
+    // T = G (I + E), rows [i0, i1) (the diagonal of E from dE: W_jj still holds S_jj)
+    for (int t = tid; t < (i1 - i0) * m; t += nt) {
+        const int i = i0 + t / m, j = t % m;
+        const double gij = G[i * m + j];
+        double acc = fma(gij, dE[j] - W[j * ld + j], gij);
+        for (int k = 0; k < m; ++k) acc = fma(G[i * m + k], W[k * ld + j], acc);
+        cl_bcast(&T[i * m + j], acc);
+    }
+    cl_sync();
+    if (tid == 0) pc[4] = clock64();
+    double* x = G;
+    G = T;
+    T = x;
+    *corr = ne_sqrt;
+    return true;
+}
+
+// Clustered form of block_mixed_eig (same contract and return code).  G and T are m x m
+// shared-memory buffers at the same offsets in every CTA.
+__device__ int mixed_eig_cl(double* H, double* U, int m, int ld, double* G, double* T, double* rot, int* pq,
+                            unsigned short* btab, double* red, double tol32, long long* pclk) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int u0 = rank * m / RRC_SIZE, u1 = (rank + 1) * m / RRC_SIZE;
+    float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
+    float* U32 = H32 + (size_t)m * ld;
+    const int half = ((m + 1) & ~1) / 2;
+    for (int t = tid; t < half * (half + 1) / 2; t += nt) {
+        int b = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (b * (b + 1) / 2 > t) --b;
+        while ((b + 1) * (b + 2) / 2 <= t) ++b;
+        btab[t] = (unsigned short)(((t - b * (b + 1) / 2) << 8) | b);
+    }
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        H32[i * ld + j] = (float)H[i * ld + j];
+    }
+    const int s32 = jacobi32_cl(H32, U32, m, ld, u0, u1, reinterpret_cast<float2*>(rot), pq, btab, red, tol32, 16);
+    if (tid == 0) pclk[0] = clock64();
+    // G = the FP32 eigenvectors: this CTA's rows, stored into every CTA
+    for (int t = tid; t < (u1 - u0) * m; t += nt) {
+        const int i = u0 + t / m, j = t % m;
+        cl_bcast(&G[i * m + j], (double)U32[i * ld + j]);
+    }
+    cl_sync();
+    if (tid == 0) pclk[1] = clock64();
+    double* lam = rot;  // free once the FP32 stage is done
+    __shared__ double part[3][RRC_SIZE];
+    __shared__ int flags[RRC_SIZE + 1];
+    __shared__ double dE[RRC_MAX];
+    __shared__ double scal[2];
+    double nh = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int t = tid; t < m * m; t += nt) {
+        const double h = H[(t / m) * ld + t % m];
+        nh = fma(h, h, nh);
+    }
+    block_sum3(nh, z0, z1, red);
+    double corr = 1.0;
+    bool ok = true;
+    int steps = 0;
+    while (steps < 2 && ok && corr > 1e-6) {
+        ok = oa_refine_cl(H, ld, G, T, U, m, lam, nh, red, part, flags, dE, scal, &corr, pclk + 4 + 10 * steps);
+        ++steps;
+        if (tid == 0) pclk[1 + steps] = clock64();
+    }
+    if (ok && corr <= 1e-6) {
+        for (int t = tid; t < m * m; t += nt) {
+            const int i = t / m, j = t % m;
+            U[i * ld + j] = G[t];
+            H[i * ld + j] = (i == j) ? lam[i] : 0.0;
+        }
+        __syncthreads();
+        return 100 * s32 + 50 + steps;
+    }
+    // fallback (close eigenvalues): the one-CTA path on every CTA alike, from the current G
+    const int fallback = ok ? 3 : flags[RRC_SIZE];
+    for (int ns = 0; ns < 2; ++ns) {
+        block_gemm(T, m, G, m, true, G, m, m);
+        __syncthreads();
+        for (int t = tid; t < m * m; t += nt) T[t] = (t / m == t % m ? 1.5 : 0.0) - 0.5 * T[t];
+        __syncthreads();
+        block_gemm(U, ld, G, m, false, T, m, m);
+        __syncthreads();
+        for (int t = tid; t < m * m; t += nt) G[t] = U[(t / m) * ld + t % m];
+        __syncthreads();
+    }
+    block_gemm(T, m, H, ld, false, G, m, m);
+    __syncthreads();
+    for (int t = tid; t < m * (m + 1) / 2; t += nt) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (j * (j + 1) / 2 > t) --j;
+        while ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        double acc = 0.0;
+        for (int k = 0; k < m; ++k) acc = fma(G[k * m + i], T[k * m + j], acc);
+        H[i * ld + j] = acc;
+        H[j * ld + i] = acc;
+    }
+    __syncthreads();
+    const int s64 = block_jacobi_sym(H, U, m, ld, rot, pq, red, 1e-26);
+    block_gemm(T, m, G, m, false, U, ld, m);
+    __syncthreads();
+    for (int t = tid; t < m * m; t += nt) U[(t / m) * ld + t % m] = T[t];
+    __syncthreads();
+    return 100 * s32 + 10 * fallback + s64;
+}
+
+__global__ void __cluster_dims__(RRC_SIZE, 1, 1) __launch_bounds__(RR_THREADS, 1) rr_cluster_kernel(RRArgs a) {
+    extern __shared__ double sm[];
+    __shared__ double rot[2 * 64 + 2];
+    __shared__ int pq[2 * 64 + 2];
+    __shared__ double red[104];
+    __shared__ unsigned short btab[(RRC_MAX / 2) * (RRC_MAX / 2 + 1) / 2 + 8];
+    __shared__ int inv[RRC_MAX];
+    __shared__ int flag, npos_sh;
+    __shared__ double rpiv;
+    __shared__ long long clk[32];  // phase clocks of thread 0 of CTA 0 (PPRPA_RR_PROF)
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int m = a.m, ld = a.ld;
+    const int lh = rr_ld(m, a.pad);
+    double* H = sm;
+    double* U = H + (size_t)m * lh;
+    double* G = U + (size_t)m * lh;
+    double* T = G + (size_t)m * m;
+    double* Kc = T + (size_t)m * m;  // packed lower triangle of the Cholesky factor
+    double* rd = Kc + (size_t)m * (m + 1) / 2;
+    cl_sync();  // every CTA of the cluster runs before any store into its shared memory
+    if (tid == 0) clk[0] = clock64();
+    if (rank == 0 && tid == 0) a.info[0] = DEV_NOTPD;
+    double sc = 0.0;
+    for (int i = tid; i < m; i += nt)
+        sc = fmax(sc, fabs(a.G[i * ld + i] + (a.Go ? a.Go[i * ld + i] : 0.0)) + fabs(a.S[i * ld + i]));
+    sc = block_max(sc, red);
+    const double scale = sc > 0.0 ? sc : 1.0;
+    int used = -1;
+    double mu = 0.0;
+    for (int c = 0; c < a.nmu && used < 0; ++c) {
+        mu = a.mus[c];
+        // K = sym(G) - mu S, lower triangle (S: upper triangle valid)
+        for (int t = tid; t < m * m; t += nt) {
+            const int i = t / m, j = t % m;
+            if (j > i) continue;
+            double g = 0.5 * (a.G[i * ld + j] + a.G[j * ld + i]);
+            if (a.Go) g += 0.5 * (a.Go[i * ld + j] + a.Go[j * ld + i]);
+            Kc[lp(i, j)] = g - mu * a.S[j * ld + i];
+        }
+        if (tid == 0) flag = 0;
+        __syncthreads();
+        if (chol_packed(Kc, m, 1e-13, scale, &flag, &rpiv)) used = c;
+        __syncthreads();
+    }
+    if (used < 0) {
+        if (rank == 0 && tid == 0) { a.info[0] = DEV_NOTPD; a.info[1] = mu; }
+        cl_sync();
+        return;
+    }
+    if (tid == 0) clk[1] = clock64();
+    for (int i = tid; i < m; i += nt) rd[i] = 1.0 / Kc[lp(i, i)];
+    __syncthreads();
+    // Lc = Ls D: columns scaled to a unit diagonal
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        if (j < i) Kc[lp(i, j)] *= rd[j];
+    }
+    __syncthreads();
+    // X = Lc^-1 S into G: a warp per column, the columns dealt over the cluster
+    for (int col = rank + RRC_SIZE * w; col < m; col += RRC_SIZE * nw) {
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = m - 1 - lane - 32 * k;
+            x[k] = r >= 0 ? (r <= col ? a.S[r * ld + col] : a.S[col * ld + r]) : 0.0;
+        }
+        warp_lsolve_unit(Kc, m, x[0], x[1], x[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = m - 1 - lane - 32 * k;
+            if (r >= 0) cl_bcast(&G[r * m + col], x[k] * rd[r]);
+        }
+    }
+    cl_sync();
+    // H = Lc^-1 X^T
+    for (int col = rank + RRC_SIZE * w; col < m; col += RRC_SIZE * nw) {
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = m - 1 - lane - 32 * k;
+            x[k] = r >= 0 ? G[col * m + r] : 0.0;
+        }
+        warp_lsolve_unit(Kc, m, x[0], x[1], x[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = m - 1 - lane - 32 * k;
+            if (r >= 0) cl_bcast(&H[r * lh + col], x[k] * rd[r]);
+        }
+    }
+    cl_sync();
+    for (int t = tid; t < m * m; t += nt) {
+        const int i = t / m, j = t % m;
+        if (i < j) {
+            const double v = 0.5 * (H[i * lh + j] + H[j * lh + i]);
+            H[i * lh + j] = v;
+            H[j * lh + i] = v;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) clk[2] = clock64();
+    if (tid == 0) clk[6] = clk[7] = clk[8] = clk[9] = clk[2];
+    const int sweeps = mixed_eig_cl(H, U, m, lh, G, T, rot, pq, btab, red, a.tol32, clk + 6);
+    if (tid == 0) clk[3] = clock64();
+    // rank the positive kappas (descending) -> targets
+    if (tid == 0) npos_sh = 0;
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) {
+        const double ki = H[i * lh + i];
+        if (ki > 0.0) {
+            int r = 0;
+            for (int j = 0; j < m; ++j) {
+                const double kj = H[j * lh + j];
+                if (kj > 0.0 && (kj > ki || (kj == ki && j < i))) ++r;
+            }
+            inv[r] = i;
+            atomicAdd(&npos_sh, 1);
+        }
+    }
+    __syncthreads();
+    const int npos = npos_sh;
+    const int nk = min(a.nkeep, npos);
+    if (tid == 0) clk[4] = clock64();
+    // Ritz coefficients c = Lc^-T u / sqrt(kappa): a warp per kept root, dealt over the cluster
+    for (int slot = rank + RRC_SIZE * w; slot < nk; slot += RRC_SIZE * nw) {
+        const int i = inv[slot];
+        const double kap = H[i * lh + i];
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = lane + 32 * k;
+            x[k] = r < m ? U[r * lh + i] * rd[r] : 0.0;
+        }
+        warp_usolve_unit(Kc, m, x[0], x[1], x[2]);
+        const double f = 1.0 / sqrt(kap);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int r = lane + 32 * k;
+            if (r < m) a.coef[(size_t)slot * m + r] = x[k] * f;
+        }
+        if (lane == 0) a.omega[slot] = mu + 1.0 / kap;
+    }
+    if (rank == 0 && tid == 0) {
+        double kmin = 0.0, kmax = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double k = H[i * lh + i];
+            if (k < kmin) kmin = k;
+            if (k > kmax) kmax = k;
+        }
+        a.info[0] = (npos >= a.nwant) ? DEV_OK : DEV_FEWROOTS;
+        a.info[1] = mu;
+        a.info[2] = npos;
+        a.info[3] = kmax > 0.0 ? mu + 1.0 / kmax : 1e300;
+        a.info[4] = kmin < 0.0 ? mu + 1.0 / kmin : -1e300;
+        a.info[5] = sweeps;
+        if (a.prof) {
+            clk[5] = clock64();
+            printf("[rr-cl] m %d sweeps %d cycles: factor %lld solves %lld eig %lld (fp32 %lld to-G %lld oa %lld %lld) "
+                   "rank %lld ritz %lld\n",
+                   m, sweeps, clk[1] - clk[0], clk[2] - clk[1], clk[3] - clk[2], clk[6] - clk[2], clk[7] - clk[6],
+                   clk[8] - clk[7], clk[9] - clk[8], clk[4] - clk[3], clk[5] - clk[4]);
+            printf("[rr-cl] oa step 1: HG %lld S %lld R %lld E %lld G(I+E) %lld | HG loop %lld bar %lld csync %lld | S loop %lld sum3 %lld rest %lld\n",
+                   clk[10] - clk[7], clk[11] - clk[10], clk[12] - clk[11], clk[13] - clk[12], clk[14] - clk[13],
+                   clk[15] - clk[7], clk[16] - clk[15], clk[10] - clk[16], clk[17] - clk[10], clk[18] - clk[17], clk[11] - clk[18]);
+        }
+    }
+    cl_sync();  // no CTA leaves while a store into it could still be in flight
 }
 
 // Eigensolver of the one-CTA kernels (PPRPA_EIG): 4 (default) FP32 Jacobi refined in FP64 by
@@ -905,6 +1525,20 @@ int launch_rayleigh_ritz(const RRArgs& ain, cudaStream_t st) {
     a.tol32 = tv ? atof(tv) : (a.eig == 4 ? 1e-14 : 1e-10);
     const char* pv = getenv("PPRPA_RR_PROF");
     a.prof = pv ? atoi(pv) : 0;
+    const char* cv = getenv("PPRPA_RR_CLUSTER");
+    if (a.eig == 4 && a.m <= RRC_MAX && (cv ? atoi(cv) : 1) != 0) {
+        // clustered form: H, U (odd leading dimension), G, T, the packed Cholesky factor and its
+        // reciprocal pivots in each CTA's shared memory
+        const auto bytes = [&](int m) {
+            const int lh = rr_ld(m, a.pad);
+            return sizeof(double) * ((size_t)2 * m * lh + (size_t)2 * m * m + (size_t)m * (m + 1) / 2 + m);
+        };
+        cudaFuncSetAttribute(rr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(RRC_MAX));
+        rr_cluster_kernel<<<RRC_SIZE, RR_THREADS, bytes(a.m), st>>>(a);
+        // a cluster that cannot be placed is a launch error, not a sticky one: the one-CTA
+        // kernel below takes the call instead
+        if (cudaGetLastError() == cudaSuccess) return PPRPA_OK;
+    }
     const size_t smem = a.m <= RR_SMEM_MAX ? 2 * sizeof(double) * a.m * rr_ld(a.m, a.pad) : 0;
     // per device and cheap: set on every launch (several host threads may launch at once)
     cudaFuncSetAttribute(rayleigh_ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
