@@ -905,18 +905,20 @@ __device__ __forceinline__ void cl_bcast(double* p, double v) {
 __device__ __forceinline__ int lp(int i, int j) { return i * (i + 1) / 2 + j; }
 
 // In-place Cholesky of the packed lower triangle K (m x m); false on a pivot <= rel_tol * scale.
-// Right-looking: the trailing update gives a warp to each row and a lane to each column.
+// Right-looking.  The pivot takes one reciprocal square root (r = d rsqrt(d)), and the trailing
+// update walks the lower triangle of the trailing block as one flat index, so that the FP64
+// pipe (the scarce unit here) sees no idle lanes.
 __device__ bool chol_packed(double* K, int m, double rel_tol, double scale, int* flag, double* rpiv) {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = 0; j < m; ++j) {
         __syncthreads();
         if (tid == 0) {
             const double d = K[lp(j, j)];
             if (!(d > rel_tol * scale)) *flag = 1;
             else {
-                const double r = sqrt(d);
-                K[lp(j, j)] = r;
-                *rpiv = 1.0 / r;
+                const double ri = rsqrt(d);
+                K[lp(j, j)] = d * ri;
+                *rpiv = ri;
             }
         }
         __syncthreads();
@@ -924,9 +926,13 @@ __device__ bool chol_packed(double* K, int m, double rel_tol, double scale, int*
         const double ri = *rpiv;
         for (int i = j + 1 + tid; i < m; i += nt) K[lp(i, j)] *= ri;
         __syncthreads();
-        for (int i = j + 1 + w; i < m; i += nw) {
-            const double kij = K[lp(i, j)];
-            for (int l = j + 1 + lane; l <= i; l += 32) K[lp(i, l)] = fma(-kij, K[lp(l, j)], K[lp(i, l)]);
+        const int r = m - j - 1;
+        for (int t = tid; t < r * (r + 1) / 2; t += nt) {
+            int a = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (a * (a + 1) / 2 > t) --a;
+            while ((a + 1) * (a + 2) / 2 <= t) ++a;
+            const int i = j + 1 + a, l = j + 1 + t - a * (a + 1) / 2;  // j < l <= i
+            K[lp(i, l)] = fma(-K[lp(i, j)], K[lp(l, j)], K[lp(i, l)]);
         }
     }
     __syncthreads();
@@ -966,13 +972,40 @@ __device__ __forceinline__ void warp_usolve_unit(const double* Ls, int m, double
 }
 
 // FP32 parallel cyclic Jacobi with the pairing, rotations, fused 2 x 2 block update and
-// stopping rules of jacobi_sym_t, for the clustered kernel: U receives the rotations on its
-// rows [u0, u1) only (rows of U evolve independently), one thread per (pair, row).  btab lists
-// the blocks (a, b), a <= b, of a round (a << 8 | b); pq holds the pair (p | q << 16) and rot
-// its (c, s).  H is stored in full: the mirrored stores of a block hit distinct banks, where
-// an upper-triangle-only form mixes two address patterns within a warp and conflicts.
-__device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u0, int u1, float2* rot, int* pq,
-                           const unsigned short* btab, double* red, double tol2, int max_sweeps) {
+// stopping rules of jacobi_sym_t, for the clustered kernel.  The round is latency-bound (a few
+// warps, each a chain of dependent shared-memory accesses), so each thread keeps its work item
+// for the whole solve in registers: block (a, b), a <= b, of the pairing, or one (pair, row) of
+// the rows [u0, u1) of U that this CTA updates (rows of U evolve independently); the pairs of
+// a round are computed, not loaded.  rot holds the (c, s) of each pair of the current round.
+__device__ __forceinline__ void jac_pair(int s, int i, int me, int& p, int& q) {
+    if (i == 0) { p = me - 1; q = s; }
+    else {
+        p = s + i;
+        if (p >= me - 1) p -= me - 1;
+        q = s - i;
+        if (q < 0) q += me - 1;
+    }
+    if (p > q) { const int x = p; p = q; q = x; }
+}
+
+// work item t of a round: block (x, y) = (a, b), a <= b, for t < nblk (triangular order
+// t = b (b + 1) / 2 + a), else pair x and row y of U
+__device__ __forceinline__ void jac_item(int t, int nblk, int nu, int u0, int& x, int& y) {
+    if (t < nblk) {
+        int b = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while (b * (b + 1) / 2 > t) --b;
+        while ((b + 1) * (b + 2) / 2 <= t) ++b;
+        x = t - b * (b + 1) / 2;
+        y = b;
+    } else {
+        const int tu = t - nblk;
+        x = tu / nu;
+        y = u0 + tu - x * nu;
+    }
+}
+
+__device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u0, int u1, float2* rot,
+                                        double* red, double tol2, int max_sweeps) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nu = u1 - u0;
     for (int t = tid; t < nu * m; t += nt) {
@@ -982,6 +1015,10 @@ __device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u
     const int me = (m + 1) & ~1;
     const int half = me / 2;
     const int nblk = half * (half + 1) / 2;
+    const int nwork = nblk + half * nu;
+    // this thread's first work item, decoded once
+    int x0 = 0, y0 = 0;
+    if (tid < nwork) jac_item(tid, nblk, nu, u0, x0, y0);
     int sweep = 0;
     double prev_off = 0.0;
     for (; sweep < max_sweeps; ++sweep) {
@@ -1001,14 +1038,7 @@ __device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u
         for (int s = 0; s < me - 1; ++s) {
             for (int i = tid; i < half; i += nt) {
                 int p, q;
-                if (i == 0) { p = me - 1; q = s; }
-                else {
-                    p = s + i;
-                    if (p >= me - 1) p -= me - 1;
-                    q = s - i;
-                    if (q < 0) q += me - 1;
-                }
-                if (p > q) { const int x = p; p = q; q = x; }
+                jac_pair(s, i, me, p, q);
                 float c = 1.0f, sn = 0.0f;
                 if (q < m) {
                     const float apq = H[p * ld + q], app = H[p * ld + p], aqq = H[q * ld + q];
@@ -1023,29 +1053,28 @@ __device__ __noinline__ int jacobi32_cl(float* H, float* U, int m, int ld, int u
                         sn = tt * c;
                     }
                 }
-                pq[i] = p | (q << 16);
                 rot[i] = make_float2(c, sn);
             }
             __syncthreads();
-            // the 2 x 2 blocks of H, then (threads nblk.. of the same pass) U <- U J on rows
-            // [u0, u1), one (pair, row) each: H and U are disjoint
-            for (int t = tid; t < nblk + half * nu; t += nt) {
+            for (int t = tid; t < nwork; t += nt) {
+                int x, y;
+                if (t == tid) { x = x0; y = y0; }
+                else jac_item(t, nblk, nu, u0, x, y);
                 if (t >= nblk) {
-                    const int tu = t - nblk;
-                    const int i = tu / nu, row = u0 + tu - (tu / nu) * nu;
-                    const int pqi = pq[i];
-                    const int p = pqi & 0xffff, q = pqi >> 16;
+                    // U <- U J on this CTA's row y, pair x
+                    int p, q;
+                    jac_pair(s, x, me, p, q);
                     if (q >= m) continue;
-                    const float2 r = rot[i];
-                    const float up = U[row * ld + p], uq = U[row * ld + q];
-                    U[row * ld + p] = r.x * up - r.y * uq;
-                    U[row * ld + q] = r.y * up + r.x * uq;
+                    const float2 r = rot[x];
+                    const float up = U[y * ld + p], uq = U[y * ld + q];
+                    U[y * ld + p] = r.x * up - r.y * uq;
+                    U[y * ld + q] = r.y * up + r.x * uq;
                     continue;
                 }
-                const int v = btab[t];
-                const int aa = v >> 8, b = v & 255;
-                const int pqa = pq[aa], pqb = pq[b];
-                const int pa = pqa & 0xffff, qa = pqa >> 16, pb = pqb & 0xffff, qb = pqb >> 16;
+                const int aa = x, b = y;
+                int pa, qa, pb, qb;
+                jac_pair(s, aa, me, pa, qa);
+                jac_pair(s, b, me, pb, qb);
                 const bool va = qa < m, vb = qb < m;  // q = m marks the dummy player (odd m)
                 const float2 ra = rot[aa], rb = rot[b];
                 const float h00 = H[pa * ld + pb];
@@ -1105,9 +1134,6 @@ __device__ __noinline__ bool oa_refine_cl(const double* H, int ld, double*& G, d
         for (int k = 0; k < m; ++k) acc = fma(H[i * ld + k], G[k * m + j], acc);
         cl_bcast(&T[i * m + j], acc);
     }
-    if (tid == 0) pc[5] = clock64();
-    __syncthreads();
-    if (tid == 0) pc[6] = clock64();
     cl_sync();
     if (tid == 0) pc[0] = clock64();
     // W = S = G^T T, upper-triangle entries [t0, t1), mirrored; partial sum of the squares of
@@ -1126,9 +1152,7 @@ __device__ __noinline__ bool oa_refine_cl(const double* H, int ld, double*& G, d
             so = fma(2.0 * acc, acc, so);
         }
     }
-    if (tid == 0) pc[7] = clock64();
     block_sum3(so, z, z2, red);
-    if (tid == 0) pc[8] = clock64();
     if (tid == 0) cl_bcast(&part[0][rank], so);
     cl_sync();
     if (tid == 0) pc[1] = clock64();
@@ -1241,24 +1265,17 @@ __device__ __noinline__ bool oa_refine_cl(const double* H, int ld, double*& G, d
 // Clustered form of block_mixed_eig (same contract and return code).  G and T are m x m
 // shared-memory buffers at the same offsets in every CTA.
 __device__ int mixed_eig_cl(double* H, double* U, int m, int ld, double* G, double* T, double* rot, int* pq,
-                            unsigned short* btab, double* red, double tol32, long long* pclk) {
+                            double* red, double tol32, long long* pclk) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int rank = (int)cg::this_cluster().block_rank();
     const int u0 = rank * m / RRC_SIZE, u1 = (rank + 1) * m / RRC_SIZE;
     float* H32 = reinterpret_cast<float*>(U);  // two m x ld float matrices fill U's doubles
     float* U32 = H32 + (size_t)m * ld;
-    const int half = ((m + 1) & ~1) / 2;
-    for (int t = tid; t < half * (half + 1) / 2; t += nt) {
-        int b = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        while (b * (b + 1) / 2 > t) --b;
-        while ((b + 1) * (b + 2) / 2 <= t) ++b;
-        btab[t] = (unsigned short)(((t - b * (b + 1) / 2) << 8) | b);
-    }
     for (int t = tid; t < m * m; t += nt) {
         const int i = t / m, j = t % m;
         H32[i * ld + j] = (float)H[i * ld + j];
     }
-    const int s32 = jacobi32_cl(H32, U32, m, ld, u0, u1, reinterpret_cast<float2*>(rot), pq, btab, red, tol32, 16);
+    const int s32 = jacobi32_cl(H32, U32, m, ld, u0, u1, reinterpret_cast<float2*>(rot), red, tol32, 16);
     if (tid == 0) pclk[0] = clock64();
     // G = the FP32 eigenvectors: this CTA's rows, stored into every CTA
     for (int t = tid; t < (u1 - u0) * m; t += nt) {
@@ -1282,7 +1299,7 @@ __device__ int mixed_eig_cl(double* H, double* U, int m, int ld, double* G, doub
     bool ok = true;
     int steps = 0;
     while (steps < 2 && ok && corr > 1e-6) {
-        ok = oa_refine_cl(H, ld, G, T, U, m, lam, nh, red, part, flags, dE, scal, &corr, pclk + 4 + 10 * steps);
+        ok = oa_refine_cl(H, ld, G, T, U, m, lam, nh, red, part, flags, dE, scal, &corr, pclk + 4 + 5 * steps);
         ++steps;
         if (tid == 0) pclk[1 + steps] = clock64();
     }
@@ -1333,11 +1350,10 @@ __global__ void __cluster_dims__(RRC_SIZE, 1, 1) __launch_bounds__(RR_THREADS, 1
     __shared__ double rot[2 * 64 + 2];
     __shared__ int pq[2 * 64 + 2];
     __shared__ double red[104];
-    __shared__ unsigned short btab[(RRC_MAX / 2) * (RRC_MAX / 2 + 1) / 2 + 8];
     __shared__ int inv[RRC_MAX];
     __shared__ int flag, npos_sh;
     __shared__ double rpiv;
-    __shared__ long long clk[32];  // phase clocks of thread 0 of CTA 0 (PPRPA_RR_PROF)
+    __shared__ long long clk[20];  // phase clocks of thread 0 of CTA 0 (PPRPA_RR_PROF)
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
     const int rank = (int)cg::this_cluster().block_rank();
     const int m = a.m, ld = a.ld;
@@ -1430,7 +1446,7 @@ __global__ void __cluster_dims__(RRC_SIZE, 1, 1) __launch_bounds__(RR_THREADS, 1
     __syncthreads();
     if (tid == 0) clk[2] = clock64();
     if (tid == 0) clk[6] = clk[7] = clk[8] = clk[9] = clk[2];
-    const int sweeps = mixed_eig_cl(H, U, m, lh, G, T, rot, pq, btab, red, a.tol32, clk + 6);
+    const int sweeps = mixed_eig_cl(H, U, m, lh, G, T, rot, pq, red, a.tol32, clk + 6);
     if (tid == 0) clk[3] = clock64();
     // rank the positive kappas (descending) -> targets
     if (tid == 0) npos_sh = 0;
@@ -1489,9 +1505,8 @@ __global__ void __cluster_dims__(RRC_SIZE, 1, 1) __launch_bounds__(RR_THREADS, 1
                    "rank %lld ritz %lld\n",
                    m, sweeps, clk[1] - clk[0], clk[2] - clk[1], clk[3] - clk[2], clk[6] - clk[2], clk[7] - clk[6],
                    clk[8] - clk[7], clk[9] - clk[8], clk[4] - clk[3], clk[5] - clk[4]);
-            printf("[rr-cl] oa step 1: HG %lld S %lld R %lld E %lld G(I+E) %lld | HG loop %lld bar %lld csync %lld | S loop %lld sum3 %lld rest %lld\n",
-                   clk[10] - clk[7], clk[11] - clk[10], clk[12] - clk[11], clk[13] - clk[12], clk[14] - clk[13],
-                   clk[15] - clk[7], clk[16] - clk[15], clk[10] - clk[16], clk[17] - clk[10], clk[18] - clk[17], clk[11] - clk[18]);
+            printf("[rr-cl] oa step 1: HG %lld S %lld R %lld E %lld G(I+E) %lld\n", clk[10] - clk[7], clk[11] - clk[10],
+                   clk[12] - clk[11], clk[13] - clk[12], clk[14] - clk[13]);
         }
     }
     cl_sync();  // no CTA leaves while a store into it could still be in flight
