@@ -108,6 +108,71 @@ __global__ void __launch_bounds__(256) dgemm_kernel(Dgemm g) {
     }
 }
 
+// Small FP64 products: few outputs and a moderate K, like the Davidson projections and
+// combinations of a small problem.  FP64 runs at about two FMAs per clock per SM here, so a
+// product of a few hundred thousand FMAs on the handful of CTAs its 64 x 64 tiles give takes
+// tens of microseconds; these two kernels spread it over the GPU, without atomics.
+// C = alpha A B^T + beta C, A (M x K, lda), B (N x K, ldb): a warp per output, lanes over K.
+__global__ void __launch_bounds__(256) small_abt_kernel(Dgemm g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = (int64_t)g.M * g.N;
+    for (int64_t o = w; o < total; o += nw) {
+        const int64_t i = o / g.N, j = o % g.N;
+        const double* a = g.A + i * g.lda;
+        const double* b = g.B + j * g.ldb;
+        double s0 = 0.0, s1 = 0.0;
+        int k = lane;
+        for (; k + 32 < g.K; k += 64) {
+            s0 = fma(a[k], b[k], s0);
+            s1 = fma(a[k + 32], b[k + 32], s1);
+        }
+        if (k < g.K) s0 = fma(a[k], b[k], s0);
+        double acc = s0 + s1;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) {
+            double* c = g.C + i * g.ldc + j;
+            *c = g.beta == 0.0 ? g.alpha * acc : fma(g.beta, *c, g.alpha * acc);
+        }
+    }
+}
+
+// C = alpha op(A) B + beta C, op(A) (M x K) = A[i lda + k] or (transA) A[k lda + i], B (K x N,
+// ldb): a warp per row of C and 32 consecutive columns, a lane per column.
+__global__ void __launch_bounds__(256) small_ab_kernel(Dgemm g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nch = (g.N + 31) / 32;
+    const int64_t total = (int64_t)g.M * nch;
+    const int64_t as = g.transA ? g.lda : 1, ai = g.transA ? 1 : g.lda;  // strides of op(A) over k, i
+    for (int64_t o = w; o < total; o += nw) {
+        const int64_t i = o / nch, n = (o % nch) * 32 + lane;
+        const bool on = n < g.N;
+        const double* a = g.A + i * ai;
+        const double* b = g.B + n;
+        double s0 = 0.0, s1 = 0.0;
+        int k = 0;
+        for (; k + 1 < g.K; k += 2) {
+            const double a0 = a[k * as], a1 = a[(k + 1) * as];
+            if (on) {
+                s0 = fma(a0, b[(int64_t)k * g.ldb], s0);
+                s1 = fma(a1, b[(int64_t)(k + 1) * g.ldb], s1);
+            }
+        }
+        if (k < g.K) {
+            const double a0 = a[k * as];
+            if (on) s0 = fma(a0, b[(int64_t)k * g.ldb], s0);
+        }
+        if (on) {
+            double* c = g.C + i * g.ldc + n;
+            const double acc = s0 + s1;
+            *c = g.beta == 0.0 ? g.alpha * acc : fma(g.beta, *c, g.alpha * acc);
+        }
+    }
+}
+
 int auto_splitk(int M, int N, int K, int batches) {
     const int64_t tiles = ceil_div(M, DG_BM) * ceil_div(N, DG_BN) * (int64_t)batches;
     const int64_t target = 4 * 152;
@@ -136,6 +201,24 @@ __global__ void dgemm_scale_c_kernel(Dgemm g) {
 int dgemm(const Dgemm& gin, cudaStream_t st) {
     Dgemm g = gin;
     if (g.M <= 0 || g.N <= 0) return PPRPA_OK;
+    // a single small product (at most 64 Ki outputs, K <= 8192, 2^26 FMAs) goes to the
+    // small-product kernels; a split-K request of the caller means C += alpha op(A) op(B)
+    const int64_t outs = (int64_t)g.M * g.N;
+    if (g.nr == 1 && g.nb1 == 1 && g.nb2 == 1 && g.K > 0 && g.K <= 8192 && outs <= 65536 &&
+        outs * g.K <= ((int64_t)1 << 26) && !(g.transA && g.transB)) {
+        if (g.splitk > 1) g.beta = 1.0;
+        g.splitk = 1;
+        int64_t warps;
+        if (g.transB) {
+            warps = outs;
+            small_abt_kernel<<<(unsigned)std::min<int64_t>(ceil_div(warps, 8), 152 * 16), 256, 0, st>>>(g);
+        } else {
+            warps = g.M * ceil_div(g.N, 32);
+            small_ab_kernel<<<(unsigned)std::min<int64_t>(ceil_div(warps, 8), 152 * 16), 256, 0, st>>>(g);
+        }
+        PP_CHECK_LAUNCH();
+        return PPRPA_OK;
+    }
     // FP64 arithmetic is scarce on this GPU: a launch with few output tiles and a long
     // reduction over batches (sum_r A_r B_r) spreads that reduction over CTAs, which then add
     // their partial sums atomically into C after C has been scaled by beta
