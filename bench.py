@@ -222,11 +222,13 @@ def measured_traffic(spec, precision):
         return None, "no capture summary"
     kv = {}
     for line in text.splitlines():
-        if ":" in line and line.split(":", 1)[0].strip() in (
-                "traffic_bytes_per_launch", "traffic_naux", "orbital_space", "precision",
-                "kernel_source_sha256"):
-            k_, v = line.split(":", 1)
-            kv[k_.strip()] = v.strip().strip("`")
+        if ":" not in line:
+            continue
+        k_, v = line.split(":", 1)
+        k_ = k_.strip().lstrip("-*").strip()  # the summary lists them as bullets
+        if k_ in ("traffic_bytes_per_launch", "traffic_naux", "orbital_space", "precision",
+                  "kernel_source_sha256"):
+            kv[k_] = v.strip().strip("`")
     if kv.get("kernel_source_sha256") != src:
         return None, "kernel changed since the ncu capture (profiles/tc_gemm_c2-naux270_full.md)"
     if kv.get("precision") != precision or kv.get("orbital_space") != f"{spec.nocc_act} {spec.nvir_act}":
