@@ -267,10 +267,14 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     if (m_max < nguess + 1 && N > nguess) m_max = std::min(N, nguess + 1);
     int nkeep = std::max(nguess, std::max(4 * nroots, 40));
     nkeep = std::min(nkeep, std::max(1, m_max - std::max(nroots, 8)));
-    // automatic cap of a small problem (N < 8192 pairs) on the definite (shift-Cholesky) path:
-    // restart at 72, since there the one-CTA Rayleigh-Ritz step, O(m^3) FP64 on one SM,
-    // outweighs the few extra sigma products; the general path keeps the full cap
-    const int m_soft = (o->max_subspace > 0 || N >= 8192) ? m_max : std::min(m_max, std::max(72, nkeep + nroots));
+    // automatic cap on the definite (shift-Cholesky) path: restart at 72, the range of the
+    // clustered Rayleigh-Ritz kernel, while one sigma vector costs less than about one
+    // Rayleigh-Ritz call beyond it (PPRPA_SOFT_CAP_FLOPS, default 5e11 flop: a few ms of FP64
+    // work on one SM against a sigma vector of that size); the general path keeps the full cap
+    const double fsig = 3.0 * c->naux * c->n() * ((double)c->nv * c->nv + (double)c->no * c->no);
+    const double cap_flops = env_dbl("PPRPA_SOFT_CAP_FLOPS", 5e11);
+    const int m_soft = (o->max_subspace > 0 || fsig >= cap_flops) ? m_max
+                                                                    : std::min(m_max, std::max(72, nkeep + nroots));
     const int max_new = nroots;
     Timer t_all(st, c->blocking_sync), t_sig(st, c->blocking_sync);
     t_all.start();
