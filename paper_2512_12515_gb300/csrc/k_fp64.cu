@@ -122,14 +122,18 @@ __global__ void __launch_bounds__(256) small_abt_kernel(Dgemm g) {
         const int64_t i = o / g.N, j = o % g.N;
         const double* a = g.A + i * g.lda;
         const double* b = g.B + j * g.ldb;
-        double s0 = 0.0, s1 = 0.0;
+        double sa[4] = {0.0, 0.0, 0.0, 0.0};
         int k = lane;
-        for (; k + 32 < g.K; k += 64) {
-            s0 = fma(a[k], b[k], s0);
-            s1 = fma(a[k + 32], b[k + 32], s1);
+        for (; k + 96 < g.K; k += 128) {
+            const double a0 = a[k], a1 = a[k + 32], a2 = a[k + 64], a3 = a[k + 96];
+            const double b0 = b[k], b1 = b[k + 32], b2 = b[k + 64], b3 = b[k + 96];
+            sa[0] = fma(a0, b0, sa[0]);
+            sa[1] = fma(a1, b1, sa[1]);
+            sa[2] = fma(a2, b2, sa[2]);
+            sa[3] = fma(a3, b3, sa[3]);
         }
-        if (k < g.K) s0 = fma(a[k], b[k], s0);
-        double acc = s0 + s1;
+        for (; k < g.K; k += 32) sa[0] = fma(a[k], b[k], sa[0]);
+        double acc = (sa[0] + sa[1]) + (sa[2] + sa[3]);
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (lane == 0) {
             double* c = g.C + i * g.ldc + j;
@@ -152,22 +156,23 @@ __global__ void __launch_bounds__(256) small_ab_kernel(Dgemm g) {
         const bool on = n < g.N;
         const double* a = g.A + i * ai;
         const double* b = g.B + n;
-        double s0 = 0.0, s1 = 0.0;
+        // eight rows of B in flight per step: the loop is bound by the latency of these loads
+        double sa[4] = {0.0, 0.0, 0.0, 0.0};
         int k = 0;
-        for (; k + 1 < g.K; k += 2) {
-            const double a0 = a[k * as], a1 = a[(k + 1) * as];
-            if (on) {
-                s0 = fma(a0, b[(int64_t)k * g.ldb], s0);
-                s1 = fma(a1, b[(int64_t)(k + 1) * g.ldb], s1);
-            }
-        }
-        if (k < g.K) {
-            const double a0 = a[k * as];
-            if (on) s0 = fma(a0, b[(int64_t)k * g.ldb], s0);
-        }
         if (on) {
+            for (; k + 7 < g.K; k += 8) {
+                double av[8], bv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    av[u] = a[(k + u) * as];
+                    bv[u] = b[(int64_t)(k + u) * g.ldb];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sa[u & 3] = fma(av[u], bv[u], sa[u & 3]);
+            }
+            for (; k < g.K; ++k) sa[0] = fma(a[k * as], b[(int64_t)k * g.ldb], sa[0]);
             double* c = g.C + i * g.ldc + n;
-            const double acc = s0 + s1;
+            const double acc = (sa[0] + sa[1]) + (sa[2] + sa[3]);
             *c = g.beta == 0.0 ? g.alpha * acc : fma(g.beta, *c, g.alpha * acc);
         }
     }
@@ -208,14 +213,13 @@ int dgemm(const Dgemm& gin, cudaStream_t st) {
         outs * g.K <= ((int64_t)1 << 26) && !(g.transA && g.transB)) {
         if (g.splitk > 1) g.beta = 1.0;
         g.splitk = 1;
-        int64_t warps;
-        if (g.transB) {
-            warps = outs;
-            small_abt_kernel<<<(unsigned)std::min<int64_t>(ceil_div(warps, 8), 152 * 16), 256, 0, st>>>(g);
-        } else {
-            warps = g.M * ceil_div(g.N, 32);
-            small_ab_kernel<<<(unsigned)std::min<int64_t>(ceil_div(warps, 8), 152 * 16), 256, 0, st>>>(g);
-        }
+        // warps per block: as few as spread the warps over every SM (each SM's FP64 pipe is
+        // the scarce unit), at most 8
+        const int64_t warps = g.transB ? outs : g.M * ceil_div(g.N, 32);
+        const int wpb = (int)std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(warps, 152)));
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(warps, wpb), 152 * 16);
+        if (g.transB) small_abt_kernel<<<blocks, 32 * wpb, 0, st>>>(g);
+        else small_ab_kernel<<<blocks, 32 * wpb, 0, st>>>(g);
         PP_CHECK_LAUNCH();
         return PPRPA_OK;
     }
