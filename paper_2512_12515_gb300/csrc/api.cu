@@ -29,6 +29,21 @@ int ctx_sync(pprpa_ctx* c) {
     return PPRPA_OK;
 }
 
+int host_stage(pprpa_ctx* c, size_t bytes, void** out) {
+    if (c->hstage_bytes < bytes) {
+        if (c->hstage) {
+            PP_TRY(ctx_sync(c));  // no copy into the old buffer is still queued
+            PP_CUDA(cudaFreeHost(c->hstage));
+            c->hstage = nullptr;
+            c->hstage_bytes = 0;
+        }
+        PP_CUDA(cudaMallocHost(&c->hstage, bytes));
+        c->hstage_bytes = bytes;
+    }
+    *out = c->hstage;
+    return PPRPA_OK;
+}
+
 static int check_ctx(pprpa_ctx* c) {
     if (!c) return set_error(PPRPA_ERR_ARG, "null context");
     cudaError_t e = cudaSetDevice(c->device);
@@ -227,6 +242,7 @@ void pprpa_destroy(pprpa_ctx* c) {
     destroy_batch_plan(c->batch_plan);
     destroy_batch_plan(c->batch_plan3);
     if (c->sync_ev) cudaEventDestroy(c->sync_ev);
+    if (c->hstage) cudaFreeHost(c->hstage);
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

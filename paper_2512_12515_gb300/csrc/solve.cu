@@ -310,6 +310,21 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(ws_get(c, "dv_sel", sizeof(int) * m_max, (void**)&sel));
     PP_TRY(ws_get(c, "dv_idx", sizeof(int) * m_max, (void**)&idx));
     PP_TRY(ws_get(c, "dv_dom", sizeof(double) * m_max, (void**)&dom));
+    // pinned staging of the per-iteration readbacks and uploads (one wait per decision point):
+    // RR info (8), Ritz values (m_max), residual norms (m_max), norms before / after the
+    // orthogonalisation (nbuf each), shifts (32), then ints: selected roots (nbuf) and the
+    // keep flags of the two Cholesky-QR passes (2 nbuf)
+    void* hst;
+    PP_TRY(host_stage(c, sizeof(double) * (8 + 2 * (size_t)m_max + 2 * (size_t)nbuf + 32) +
+                             sizeof(int) * 3 * (size_t)nbuf, &hst));
+    double* hs_info = static_cast<double*>(hst);
+    double* hs_om = hs_info + 8;
+    double* hs_nrm = hs_om + m_max;
+    double* hs_nb = hs_nrm + m_max;
+    double* hs_na = hs_nb + nbuf;
+    double* hs_mus = hs_na + nbuf;
+    int* hs_sel = reinterpret_cast<int*>(hs_mus + 32);
+    int* hs_keep = hs_sel + nbuf;
 
     // a3: diagonal, then the initial guess
     if (o->mult == PPRPA_AB) PP_TRY(diag_ab(c, pt, D));
@@ -418,15 +433,19 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
                 cand.push_back(hi_est - 0.05 * t);
             }
             cand.resize(std::min<size_t>(cand.size(), 32));
-            PP_CUDA(cudaMemcpyAsync(mus, cand.data(), sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
+            std::copy(cand.begin(), cand.end(), hs_mus);
+            PP_CUDA(cudaMemcpyAsync(mus, hs_mus, sizeof(double) * cand.size(), cudaMemcpyHostToDevice, st));
             RRArgs a;
             a.G = G; a.Go = Go; a.S = S; a.ld = m_max; a.m = m;
             a.mus = mus; a.nmu = (int)cand.size();
             a.nwant = nroots; a.nkeep = nk_req;
             a.work = rwork; a.omega = om; a.coef = coef; a.info = rinfo;
             PP_TRY(launch_rayleigh_ritz(a, st));
-            PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+            // status and Ritz values in one wait (the values are used only when the call succeeded)
+            PP_CUDA(cudaMemcpyAsync(hs_info, rinfo, sizeof(double) * 6, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaMemcpyAsync(hs_om, om, sizeof(double) * std::min(nk_req, m), cudaMemcpyDeviceToHost, st));
             PP_TRY(ctx_sync(c));
+            std::copy(hs_info, hs_info + 6, hinfo);
             if ((int)hinfo[0] == DEV_NOTPD) {
                 if (o->require_definite) {
                     if (info) {
@@ -452,8 +471,10 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             g.nwant = nroots; g.nkeep = nk_req;
             g.work = rwork; g.omega = om; g.coef = coef; g.info = rinfo;
             PP_TRY(launch_rr_general(g, st));
-            PP_CUDA(cudaMemcpyAsync(hinfo, rinfo, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaMemcpyAsync(hs_info, rinfo, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+            PP_CUDA(cudaMemcpyAsync(hs_om, om, sizeof(double) * std::min(nk_req, m), cudaMemcpyDeviceToHost, st));
             PP_TRY(ctx_sync(c));
+            std::copy(hs_info, hs_info + 8, hinfo);
             if ((int)hinfo[0] == DEV_NOTPD)
                 return set_error(PPRPA_ERR_UNSTABLE, "Davidson: subspace eigenvalue iteration failed");
             npos = (int)hinfo[2];
@@ -461,8 +482,7 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         if (npos < 1)
             return set_error(PPRPA_ERR_UNSTABLE, "Davidson: the subspace holds no real addition root");
         const int ntg = std::min(npos, nroots);  // targets this iteration
-        PP_CUDA(cudaMemcpyAsync(h_om.data(), om, sizeof(double) * std::min(npos, nk_req), cudaMemcpyDeviceToHost, st));
-        PP_TRY(ctx_sync(c));
+        std::copy(hs_om, hs_om + std::min(npos, nk_req), h_om.begin());
         const int nk_avail = std::min(npos, nk_req);
         // complex Ritz values below the highest target: complex roots among the lowest
         if (general) max_imag_below = (hinfo[6] < h_om[ntg - 1]) ? hinfo[7] : 0.0;
@@ -471,8 +491,9 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         PP_TRY(combine(coef, m, ntg, m, Sg, N, SZ, 1.0, 0.0, st));
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * ntg, st));
         PP_TRY(launch_residual(SZ, Zr, om, ntg, N, nvv, R, nrm, st, ws));
-        PP_CUDA(cudaMemcpyAsync(h_nrm.data(), nrm, sizeof(double) * ntg, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaMemcpyAsync(hs_nrm, nrm, sizeof(double) * ntg, cudaMemcpyDeviceToHost, st));
         PP_TRY(ctx_sync(c));
+        std::copy(hs_nrm, hs_nrm + ntg, h_nrm.begin());
         double rmax = 0.0;
         std::vector<int> todo;
         for (int j = 0; j < ntg; ++j) {
@@ -536,17 +557,17 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         if (it == o->max_iter) break;
         // ---- correction vectors ----
         const int kn = (int)todo.size();
-        PP_CUDA(cudaMemcpyAsync(sel, todo.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, st));
+        std::copy(todo.begin(), todo.end(), hs_sel);
+        PP_CUDA(cudaMemcpyAsync(sel, hs_sel, sizeof(int) * kn, cudaMemcpyHostToDevice, st));
         PP_TRY(launch_correction(R, D, om, sel, kn, N, nvv, Dn, st, ws));
         if (m + kn > (general ? m_max : m_soft)) {
             PP_TRY(collapse(nk_avail, m, false));
             m = nk_avail;
         }
         // ---- orthogonalise against V (two passes of classical Gram-Schmidt) ----
-        std::vector<double> n_before(kn), n_after(kn);
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
         PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
-        PP_CUDA(cudaMemcpyAsync(n_before.data(), nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaMemcpyAsync(hs_nb, nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
         for (int pass = 0; pass < 2; ++pass) {
             PP_TRY(dots(V, N, m, Dn, N, kn, N, H, kn, 1.0, true, st));  // H = V Dn^T (m x kn)
             Dgemm g;  // Dn -= H^T V
@@ -559,11 +580,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         }
         PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
         PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
-        PP_CUDA(cudaMemcpyAsync(n_after.data(), nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
+        PP_CUDA(cudaMemcpyAsync(hs_na, nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
         PP_TRY(ctx_sync(c));
         std::vector<int> live;
         for (int t = 0; t < kn; ++t)
-            if (n_after[t] > 1e-20 * std::max(n_before[t], 1e-300)) live.push_back(t);
+            if (hs_na[t] > 1e-20 * std::max(hs_nb[t], 1e-300)) live.push_back(t);
         if (live.empty()) break;  // stagnation: no new directions
         // compact live rows into Dn2
         for (size_t t = 0; t < live.size(); ++t)
@@ -571,17 +592,18 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
                                     cudaMemcpyDeviceToDevice, st));
         int kl = (int)live.size();
         // ---- Cholesky-QR twice among the new vectors ----
-        std::vector<int> hkeep(kl, 1);
+        // (the second pass does not depend on the first one's flags: both are read in one wait;
+        // the copy of the first pass's flags is queued before the second pass overwrites them)
         for (int pass = 0; pass < 2; ++pass) {
             PP_TRY(dots(Dn2, N, kl, Dn2, N, kl, N, Gm, kl, 1.0, true, st));
             PP_TRY(launch_cholqr_small(Gm, kl, 1e-12, Tm, keep, cwork, st));
             PP_TRY(combine(Tm, kl, kl, kl, Dn2, N, Dn, 1.0, 0.0, st));
             PP_CUDA(cudaMemcpyAsync(Dn2, Dn, sizeof(double) * (size_t)kl * N, cudaMemcpyDeviceToDevice, st));
-            std::vector<int> kp(kl);
-            PP_CUDA(cudaMemcpyAsync(kp.data(), keep, sizeof(int) * kl, cudaMemcpyDeviceToHost, st));
-            PP_TRY(ctx_sync(c));
-            for (int t = 0; t < kl; ++t) hkeep[t] &= kp[t];
+            PP_CUDA(cudaMemcpyAsync(hs_keep + pass * nbuf, keep, sizeof(int) * kl, cudaMemcpyDeviceToHost, st));
         }
+        PP_TRY(ctx_sync(c));
+        std::vector<int> hkeep(kl);
+        for (int t = 0; t < kl; ++t) hkeep[t] = hs_keep[t] & hs_keep[nbuf + t];
         int added = 0;
         for (int t = 0; t < kl; ++t) {
             if (!hkeep[t]) continue;
