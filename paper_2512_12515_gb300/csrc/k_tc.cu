@@ -899,10 +899,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     float v[32];
                     tmem_ld32(tbase + c0, c0 + 16 < cend, v);
                     if (!rok) continue;
+                    // four columns per vector reduction (16-byte aligned: n_pad and the block
+                    // offsets are multiples of 8 floats), single ones at a ragged edge
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
+                    for (int e = 0; e < 32; e += 4) {
                         const int b = c.n0 + c0 + e;
-                        if (c0 + e < cend && b < n_valid) atomicAdd(Ob + b, v[e]);
+                        if (c0 + e + 3 < cend && b + 3 < n_valid) {
+                            atomicAdd(reinterpret_cast<float4*>(Ob + b), make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]));
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                if (c0 + e + u < cend && b + u < n_valid) atomicAdd(Ob + b + u, v[e + u]);
+                        }
                     }
                 }
             }

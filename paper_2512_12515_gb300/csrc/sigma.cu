@@ -475,7 +475,8 @@ static int tc_jobs(pprpa_ctx* c, const TcPrepared& pr, int P0, int npc, std::vec
         // accumulation loses accuracy over very long reductions (partial sums of the
         // slices are added in FP32 in L2)
         const int64_t base_items = (int64_t)p.ntiles * k;
-        int64_t ns = ceil_div(4LL * (pair2 ? c->num_sms / 2 : c->num_sms), base_items);
+        const int64_t waves = std::max(1, env_int("PPRPA_S2_WAVES", 4));
+        int64_t ns = ceil_div(waves * (pair2 ? c->num_sms / 2 : c->num_sms), base_items);
         ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max(1, p.kb_total / 8)));
         const int pcap = env_int(split ? "PPRPA_S2_PCAP_SPLIT" : "PPRPA_S2_PCAP", split ? 2 : 128);
         if (pcap > 0) ns = std::max<int64_t>(ns, ceil_div(npc, pcap));
