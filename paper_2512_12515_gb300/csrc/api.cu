@@ -29,18 +29,18 @@ int ctx_sync(pprpa_ctx* c) {
     return PPRPA_OK;
 }
 
-int host_stage(pprpa_ctx* c, size_t bytes, void** out) {
-    if (c->hstage_bytes < bytes) {
-        if (c->hstage) {
-            PP_TRY(ctx_sync(c));  // no copy into the old buffer is still queued
-            PP_CUDA(cudaFreeHost(c->hstage));
-            c->hstage = nullptr;
-            c->hstage_bytes = 0;
+int host_stage(pprpa_ctx* c, size_t bytes, void** out, int slot) {
+    if (c->hstage_bytes[slot] < bytes) {
+        if (c->hstage[slot]) {
+            PP_CUDA(cudaDeviceSynchronize());  // no copy from or into the old buffer is still queued
+            PP_CUDA(cudaFreeHost(c->hstage[slot]));
+            c->hstage[slot] = nullptr;
+            c->hstage_bytes[slot] = 0;
         }
-        PP_CUDA(cudaMallocHost(&c->hstage, bytes));
-        c->hstage_bytes = bytes;
+        PP_CUDA(cudaMallocHost(&c->hstage[slot], bytes));
+        c->hstage_bytes[slot] = bytes;
     }
-    *out = c->hstage;
+    *out = c->hstage[slot];
     return PPRPA_OK;
 }
 
@@ -242,7 +242,8 @@ void pprpa_destroy(pprpa_ctx* c) {
     destroy_batch_plan(c->batch_plan);
     destroy_batch_plan(c->batch_plan3);
     if (c->sync_ev) cudaEventDestroy(c->sync_ev);
-    if (c->hstage) cudaFreeHost(c->hstage);
+    for (void* h : c->hstage)
+        if (h) cudaFreeHost(h);
     if (c->d_status) cudaFree(c->d_status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -118,8 +118,9 @@ struct pprpa_ctx {
     // pinned host staging for the small per-iteration readbacks of a Davidson solve: a copy
     // into pageable memory waits for the stream by itself, a copy into this one does not, so
     // several readbacks share one wait
-    void* hstage = nullptr;
-    size_t hstage_bytes = 0;
+    // (slot 0: the Davidson readbacks; slot 1: the uploads of a batched-sigma plan)
+    void* hstage[2] = {nullptr, nullptr};
+    size_t hstage_bytes[2] = {0, 0};
 };
 
 namespace pprpa {
@@ -144,8 +145,8 @@ int autotune_tiles(pprpa_ctx* c, int mult, int k, int nterms, int* bn_out);
 int check_status(pprpa_ctx* c);
 // Waits for the context's stream (see pprpa_ctx::blocking_sync).
 int ctx_sync(pprpa_ctx* c);
-// Pinned host staging of at least `bytes` (pprpa_ctx::hstage), grown on demand.
-int host_stage(pprpa_ctx* c, size_t bytes, void** out);
+// Pinned host staging of at least `bytes` (pprpa_ctx::hstage, slot 0 or 1), grown on demand.
+int host_stage(pprpa_ctx* c, size_t bytes, void** out, int slot = 0);
 
 // Tensor-core sigma provider of a Davidson solve run among others (pprpa_solve_batch): the
 // solve hands its BF16 (nterms 1) or BF16x3 (nterms 3) products of k device vectors to it

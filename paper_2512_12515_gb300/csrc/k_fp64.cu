@@ -203,14 +203,19 @@ __global__ void dgemm_scale_c_kernel(Dgemm g) {
     }
 }
 
+bool dgemm_small(const Dgemm& g) {
+    const int64_t outs = (int64_t)g.M * g.N;
+    return g.M > 0 && g.N > 0 && g.nr == 1 && g.nb1 == 1 && g.nb2 == 1 && g.K > 0 && g.K <= 8192 &&
+           outs <= 65536 && outs * g.K <= ((int64_t)1 << 26) && !(g.transA && g.transB);
+}
+
 int dgemm(const Dgemm& gin, cudaStream_t st) {
     Dgemm g = gin;
     if (g.M <= 0 || g.N <= 0) return PPRPA_OK;
     // a single small product (at most 64 Ki outputs, K <= 8192, 2^26 FMAs) goes to the
     // small-product kernels; a split-K request of the caller means C += alpha op(A) op(B)
     const int64_t outs = (int64_t)g.M * g.N;
-    if (g.nr == 1 && g.nb1 == 1 && g.nb2 == 1 && g.K > 0 && g.K <= 8192 && outs <= 65536 &&
-        outs * g.K <= ((int64_t)1 << 26) && !(g.transA && g.transB)) {
+    if (dgemm_small(g)) {
         if (g.splitk > 1) g.beta = 1.0;
         g.splitk = 1;
         // warps per block: as few as spread the warps over every SM (each SM's FP64 pipe is
@@ -613,10 +618,55 @@ __global__ void row_norms2_kernel(const double* __restrict__ X, int N, double* _
     if (threadIdx.x == 0) atomicAdd(out + j, acc);
 }
 
+// out[j] = ||X_j||^2 written by one block per row (no prior zeroing)
+__global__ void row_norms2_set_kernel(const double* __restrict__ X, int N, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t i = threadIdx.x;
+    for (; i + blockDim.x < N; i += 2 * (int64_t)blockDim.x) {
+        const double x0 = X[(int64_t)j * N + i], x1 = X[(int64_t)j * N + i + blockDim.x];
+        a0 = fma(x0, x0, a0);
+        a1 = fma(x1, x1, a1);
+    }
+    if (i < N) {
+        const double x = X[(int64_t)j * N + i];
+        a0 = fma(x, x, a0);
+    }
+    const double acc = block_sum(a0 + a1, sh);
+    if (threadIdx.x == 0) out[j] = acc;
+}
+
 int launch_row_norms2(const double* X, int k, int N, double* out, cudaStream_t st) {
-    if (!k || !N) return PPRPA_OK;
+    if (!k) return PPRPA_OK;
+    if (N <= 65536) {
+        // a block per row writes its norm: one launch, no zeroing of out
+        row_norms2_set_kernel<<<k, 256, 0, st>>>(X, N, out);
+        PP_CHECK_LAUNCH();
+        return PPRPA_OK;
+    }
+    PP_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * k, st));
     dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 256), k);
     row_norms2_kernel<<<grid, 256, 0, st>>>(X, N, out);
+    PP_CHECK_LAUNCH();
+    return PPRPA_OK;
+}
+
+// dst row t = src row idx[t] (rows of N doubles), t < n
+__global__ void gather_rows_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                   const int* __restrict__ idx, int n, int64_t N) {
+    const int t = blockIdx.y;
+    if (t >= n) return;
+    const double* s = src + (int64_t)idx[t] * N;
+    double* d = dst + (int64_t)t * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = s[i];
+}
+
+int launch_gather_rows(double* dst, const double* src, const int* idx, int n, int64_t N, cudaStream_t st) {
+    if (n <= 0 || N <= 0) return PPRPA_OK;
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(N, 256), 64), (unsigned)n);
+    gather_rows_kernel<<<grid, 256, 0, st>>>(dst, src, idx, n, N);
     PP_CHECK_LAUNCH();
     return PPRPA_OK;
 }

@@ -28,6 +28,8 @@ struct Dgemm {
     int rsplit = 1;  // set by dgemm(): CTAs sharing the reduction over r (atomic accumulation)
 };
 int dgemm(const Dgemm& g, cudaStream_t st);
+// True when dgemm() gives g to the small-product kernels (one unbatched small product).
+bool dgemm_small(const Dgemm& g);
 // Picks a split-K factor for a GEMM whose output has few tiles.
 int auto_splitk(int M, int N, int K, int batches);
 
@@ -79,7 +81,10 @@ int launch_residual(const double* SZ, const double* Zr, const double* omega, int
                     int nvv, double* R, double* norms2, cudaStream_t st, double wsign = 1.0);
 int launch_correction(const double* R, const double* D, const double* omega, const int* sel,
                       int kn, int N, int nvv, double* out, cudaStream_t st, double wsign = 1.0);
+// out[j] = ||X_j||^2 for the k rows of X (k x N); out need not be zeroed
 int launch_row_norms2(const double* X, int k, int N, double* out, cudaStream_t st);
+// dst row t = src row idx[t] (rows of N doubles, idx on the device), t < n
+int launch_gather_rows(double* dst, const double* src, const int* idx, int n, int64_t N, cudaStream_t st);
 int launch_scatter_unit(double* V, int ld, const int* idx, int k, cudaStream_t st);
 int launch_build_matrix(const double* eri, int n, const int* pp, const int* pq, int N,
                         int nvv, const double* eps, int mult, double* M, cudaStream_t st);

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include <cstring>
+
 #include "ctx.h"
 
 namespace pprpa {
@@ -703,15 +705,24 @@ static int batch_persistent(int nmol, pprpa_ctx* const* ctxs, const int* mults, 
     PP_TRY(ws_get(owner, "batch_j2" + sfx, sizeof(TcJob) * std::max<size_t>(1, j2.size()), (void**)&bp->dj2));
     PP_TRY(ws_get(owner, "batch_i1" + sfx, sizeof(TcItem) * std::max<size_t>(1, i1.size()), (void**)&bp->di1));
     PP_TRY(ws_get(owner, "batch_i2" + sfx, sizeof(TcItem) * std::max<size_t>(1, i2.size()), (void**)&bp->di2));
-    if (!j1.empty()) {
-        PP_CUDA(cudaMemcpyAsync(bp->dj1, j1.data(), sizeof(TcJob) * j1.size(), cudaMemcpyHostToDevice, st));
-        PP_CUDA(cudaMemcpyAsync(bp->di1, i1.data(), sizeof(TcItem) * i1.size(), cudaMemcpyHostToDevice, st));
+    // the uploads go through pinned staging of the owner: a copy from pageable memory is
+    // staged by the driver at a few GB/s, and a solve rebuilds its plan nearly every round
+    {
+        const size_t b1 = sizeof(TcJob) * j1.size(), b2 = sizeof(TcItem) * i1.size();
+        const size_t b3 = sizeof(TcJob) * j2.size(), b4 = sizeof(TcItem) * i2.size();
+        void* hp;
+        PP_TRY(host_stage(owner, b1 + b2 + b3 + b4 + 64, &hp, 1));
+        char* h = static_cast<char*>(hp);
+        if (b1) std::memcpy(h, j1.data(), b1);
+        if (b2) std::memcpy(h + b1, i1.data(), b2);
+        if (b3) std::memcpy(h + b1 + b2, j2.data(), b3);
+        if (b4) std::memcpy(h + b1 + b2 + b3, i2.data(), b4);
+        if (b1) PP_CUDA(cudaMemcpyAsync(bp->dj1, h, b1, cudaMemcpyHostToDevice, st));
+        if (b2) PP_CUDA(cudaMemcpyAsync(bp->di1, h + b1, b2, cudaMemcpyHostToDevice, st));
+        if (b3) PP_CUDA(cudaMemcpyAsync(bp->dj2, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
+        if (b4) PP_CUDA(cudaMemcpyAsync(bp->di2, h + b1 + b2 + b3, b4, cudaMemcpyHostToDevice, st));
     }
-    if (!j2.empty()) {
-        PP_CUDA(cudaMemcpyAsync(bp->dj2, j2.data(), sizeof(TcJob) * j2.size(), cudaMemcpyHostToDevice, st));
-        PP_CUDA(cudaMemcpyAsync(bp->di2, i2.data(), sizeof(TcItem) * i2.size(), cudaMemcpyHostToDevice, st));
-    }
-    PP_CUDA(cudaStreamSynchronize(st));  // host vectors must outlive the copies
+    PP_CUDA(cudaStreamSynchronize(st));  // the staging is reused by the next plan
     // the pointers captured below are those of the contexts as they are now
     bp->epochs.resize(nmol);
     for (int m = 0; m < nmol; ++m) bp->epochs[m] = ctxs[m]->mem_epoch;

@@ -53,15 +53,20 @@ struct Timer {
 int dots(const double* A, int64_t lda, int na, const double* B, int64_t ldb, int nb, int K,
          double* C, int64_t ldc, double alpha, bool zero_first, cudaStream_t st) {
     if (na <= 0 || nb <= 0) return PPRPA_OK;
-    if (zero_first)
-        PP_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * nb, na, st));
-    if (K <= 0) return PPRPA_OK;
     Dgemm g;
     g.M = na; g.N = nb; g.K = K;
     g.A = A; g.lda = lda;
     g.B = B; g.ldb = ldb; g.transB = 1;
     g.C = C; g.ldc = ldc;
     g.alpha = alpha;
+    if (K > 0 && dgemm_small(g)) {
+        // a small product writes C (or adds to it) itself: no zeroing launch
+        g.beta = zero_first ? 0.0 : 1.0;
+        return dgemm(g, st);
+    }
+    if (zero_first)
+        PP_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * nb, na, st));
+    if (K <= 0) return PPRPA_OK;
     g.splitk = std::max(2, auto_splitk(na, nb, K, 1));
     return dgemm(g, st);
 }
@@ -312,11 +317,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     PP_TRY(ws_get(c, "dv_dom", sizeof(double) * m_max, (void**)&dom));
     // pinned staging of the per-iteration readbacks and uploads (one wait per decision point):
     // RR info (8), Ritz values (m_max), residual norms (m_max), norms before / after the
-    // orthogonalisation (nbuf each), shifts (32), then ints: selected roots (nbuf) and the
-    // keep flags of the two Cholesky-QR passes (2 nbuf)
+    // orthogonalisation (nbuf each), shifts (32), then ints: selected roots (nbuf), the keep
+    // flags of the two Cholesky-QR passes (2 nbuf) and the row lists of the two gathers (2 nbuf)
     void* hst;
     PP_TRY(host_stage(c, sizeof(double) * (8 + 2 * (size_t)m_max + 2 * (size_t)nbuf + 32) +
-                             sizeof(int) * 3 * (size_t)nbuf, &hst));
+                             sizeof(int) * 5 * (size_t)nbuf, &hst));
     double* hs_info = static_cast<double*>(hst);
     double* hs_om = hs_info + 8;
     double* hs_nrm = hs_om + m_max;
@@ -325,6 +330,8 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
     double* hs_mus = hs_na + nbuf;
     int* hs_sel = reinterpret_cast<int*>(hs_mus + 32);
     int* hs_keep = hs_sel + nbuf;
+    int* hs_live = hs_keep + 2 * nbuf;  // rows kept by the orthogonalisation, then by Cholesky-QR
+    int* hs_kept = hs_live + nbuf;
 
     // a3: diagonal, then the initial guess
     if (o->mult == PPRPA_AB) PP_TRY(diag_ab(c, pt, D));
@@ -565,7 +572,6 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             m = nk_avail;
         }
         // ---- orthogonalise against V (two passes of classical Gram-Schmidt) ----
-        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
         PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
         PP_CUDA(cudaMemcpyAsync(hs_nb, nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
         for (int pass = 0; pass < 2; ++pass) {
@@ -578,7 +584,6 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
             g.alpha = -1.0; g.beta = 1.0;
             PP_TRY(dgemm(g, st));
         }
-        PP_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * kn, st));
         PP_TRY(launch_row_norms2(Dn, kn, N, nrm, st));
         PP_CUDA(cudaMemcpyAsync(hs_na, nrm, sizeof(double) * kn, cudaMemcpyDeviceToHost, st));
         PP_TRY(ctx_sync(c));
@@ -586,11 +591,12 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         for (int t = 0; t < kn; ++t)
             if (hs_na[t] > 1e-20 * std::max(hs_nb[t], 1e-300)) live.push_back(t);
         if (live.empty()) break;  // stagnation: no new directions
-        // compact live rows into Dn2
-        for (size_t t = 0; t < live.size(); ++t)
-            PP_CUDA(cudaMemcpyAsync(Dn2 + t * N, Dn + (size_t)live[t] * N, sizeof(double) * N,
-                                    cudaMemcpyDeviceToDevice, st));
+        // compact live rows into Dn2 (one gather; the device row list reuses sel, whose last
+        // reader, the correction kernel, precedes it on the stream)
         int kl = (int)live.size();
+        std::copy(live.begin(), live.end(), hs_live);
+        PP_CUDA(cudaMemcpyAsync(sel, hs_live, sizeof(int) * kl, cudaMemcpyHostToDevice, st));
+        PP_TRY(launch_gather_rows(Dn2, Dn, sel, kl, N, st));
         // ---- Cholesky-QR twice among the new vectors ----
         // (the second pass does not depend on the first one's flags: both are read in one wait;
         // the copy of the first pass's flags is queued before the second pass overwrites them)
@@ -605,13 +611,11 @@ static int solve_davidson(pprpa_ctx* c, const pprpa_options* o, PairTable* pt, d
         std::vector<int> hkeep(kl);
         for (int t = 0; t < kl; ++t) hkeep[t] = hs_keep[t] & hs_keep[nbuf + t];
         int added = 0;
-        for (int t = 0; t < kl; ++t) {
-            if (!hkeep[t]) continue;
-            PP_CUDA(cudaMemcpyAsync(V + (size_t)(m + added) * N, Dn2 + (size_t)t * N, sizeof(double) * N,
-                                    cudaMemcpyDeviceToDevice, st));
-            ++added;
-        }
+        for (int t = 0; t < kl; ++t)
+            if (hkeep[t]) hs_kept[added++] = t;
         if (added == 0) break;
+        PP_CUDA(cudaMemcpyAsync(sel, hs_kept, sizeof(int) * added, cudaMemcpyHostToDevice, st));
+        PP_TRY(launch_gather_rows(V + (size_t)m * N, Dn2, sel, added, N, st));
         PP_TRY(run_sigma(added, V + (size_t)m * N, Sg + (size_t)m * N));
         PP_TRY(project_block(m, m + added));
         m += added;

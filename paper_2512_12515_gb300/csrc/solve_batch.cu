@@ -12,6 +12,8 @@
 // clustered launches for the large ones) on the batch's stream, and releases them.  A solve
 // that finishes leaves the rendezvous, so the others never wait for it.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstring>
@@ -90,6 +92,9 @@ class BatchSigma : public SigmaHook {
     }
 
     int rounds() const { return (int)round_; }
+    double sigma_seconds() const { return sigma_s_; }
+    double issue_seconds() const { return issue_s_; }
+    double tensor_flops() const { return flops_; }
 
   private:
     int index_of(pprpa_ctx* c) const {
@@ -117,10 +122,16 @@ class BatchSigma : public SigmaHook {
                 who.push_back((int)m);
             }
             if (cs.empty()) continue;
+            const auto t0 = std::chrono::steady_clock::now();
             int rc = sigma_tc_batch((int)cs.size(), cs.data(), mults.data(), ks.data(), zs.data(), ss.data(),
-                                    nterms, owner_->stream, owner_, true);
+                                    nterms, owner_->stream, owner_, use_graph_);
+            issue_s_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            for (size_t q = 0; q < cs.size(); ++q)
+                flops_ += (double)ks[q] * nterms * 3.0 * cs[q]->naux * cs[q]->n() *
+                          ((double)cs[q]->nv * cs[q]->nv + (double)cs[q]->no * cs[q]->no);
             if (rc == PPRPA_OK) rc = ctx_sync(owner_);
             if (rc == PPRPA_OK) rc = check_status(owner_);
+            sigma_s_ += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             for (int m : who) req_[m].rc = rc;
         }
         for (Request& r : req_) r.on = false;
@@ -131,6 +142,14 @@ class BatchSigma : public SigmaHook {
 
     std::vector<pprpa_ctx*> ctxs_;
     pprpa_ctx* owner_;
+    // the batch changes shape almost every round (molecules converge and leave, blocks
+    // shrink), so each round's graph runs once; PPRPA_SOLVE_BATCH_GRAPH=0 launches directly
+    // (measured the same)
+    bool use_graph_ = getenv("PPRPA_SOLVE_BATCH_GRAPH") ? atoi(getenv("PPRPA_SOLVE_BATCH_GRAPH")) != 0 : true;
+    // time in the batched sigma rounds, of it the part before the final wait (host work and
+    // the molecules that run on their own launches), and the tensor-core flop issued
+    // (printed with PPRPA_BATCH_LOG=1)
+    double sigma_s_ = 0.0, issue_s_ = 0.0, flops_ = 0.0;
     std::vector<Request> req_;
     int active_;
     int kcap_;
@@ -186,6 +205,9 @@ extern "C" int pprpa_solve_batch(int nmol, pprpa_ctx* const* ctxs, const pprpa_o
             });
         }
         for (auto& t : threads) t.join();
+        if (getenv("PPRPA_BATCH_LOG") && atoi(getenv("PPRPA_BATCH_LOG")))
+            fprintf(stderr, "[pprpa] solve_batch: %d rounds, %.3f s in the batched sigma (%.3f s issuing), %.3g tensor flop\n",
+                    hub.rounds(), hub.sigma_seconds(), hub.issue_seconds(), hub.tensor_flops());
     }
     pprpa_destroy(owner);
     for (int m = 0; m < nmol; ++m)
