@@ -82,7 +82,8 @@ typedef struct pprpa_options {
     double conv_tol;   /* residual 2-norm ||M z - omega W z|| for converged roots */
     int max_iter;      /* Davidson iteration cap */
     int max_subspace;  /* Davidson subspace cap (<= 128); 0 = automatic: 112, with restarts at 72
-                          below 8192 pairs while the shifted pencil is definite */
+                          while the shifted pencil is definite and one sigma vector costs under
+                          5e11 flop (3 naux n (nv^2 + no^2); PPRPA_SOFT_CAP_FLOPS) */
     int want_ec;       /* also return the correlation energy: FULL, or Davidson asked for every
                           root of its channel (nroots = nvv for pp, noo for hh) */
     int require_definite; /* Davidson: 1 = return PPRPA_ERR_UNSTABLE as soon as the subspace
